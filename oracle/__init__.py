@@ -1,0 +1,166 @@
+"""FP64 CPU oracle for tensorized NEAT evaluation (Sec. 3.1-3.3).
+
+TEST INFRASTRUCTURE ONLY: tests, the smoke check and the benchmark's CPU
+baseline / reference legs use it; the CUDA library never does.  The arithmetic
+lives in ``neat_oracle.c`` (plain C, double precision); this module compiles it
+with gcc and marshals numpy arrays through ctypes.
+
+Parity status of each function (what pins it, in tests/test_oracle_*.py):
+  transform  -- XOR worked example, brute force over all topological orders of
+                tiny DAGs, longest-path layers, relabelling invariants, status
+                bits of malformed genomes.
+  forward    -- XOR closed form, single-path chains per activation, closed forms
+                of two-input aggregations, layered-MLP special case vs numpy,
+                invariants (disabled/padding rows, genome and row permutations).
+  bound      -- checked empirically against independent fp32 evaluations.
+  backward   -- central finite differences of the forward; MLP special case
+                against numpy back-propagation.
+  hyperneat  -- single-node CPPNs with closed forms over the grid.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "neat_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+# status bits (the oracle's own copy; the CUDA library defines its own)
+CYCLE, DANGLING_KEY, DUP_KEY, DUP_EDGE, EDGE_INTO_INPUT, BAD_ATTR, IO_ROW_INVALID = (
+    1, 2, 4, 8, 16, 32, 64)
+
+
+def build(force: bool = False) -> str:
+    """Compile neat_oracle.c into liboracle.so next to it (gcc -O2, IEEE math)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-Wall",
+                               "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            P = ctypes.c_void_p
+            i32, i64, dbl = ctypes.c_int, ctypes.c_int64, ctypes.c_double
+            lib.or_transform.argtypes = [i32, i32, i32, i32, i32, P, P, P, P, P, P]
+            lib.or_forward.argtypes = [i32, i32, i32, i32, i32, P, P, P, i64, i32, P, P, P]
+            lib.or_backward.argtypes = [i32, i32, i32, i32, i32, P, P, P, i64, i32, P, P, P, P, P]
+            lib.or_hyperneat.argtypes = [i32, i32, i32, P, P, i32, dbl, P, i64, P, P, P]
+            for f in (lib.or_transform, lib.or_forward, lib.or_backward, lib.or_hyperneat):
+                f.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a):
+    """The oracle reads double arrays; float32 data converts exactly."""
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _shapes(nodes, conns):
+    P, N, k = nodes.shape
+    P2, C, k2 = conns.shape
+    assert k == 5 and k2 == 4 and P == P2
+    return P, N, C
+
+
+def transform(nodes, conns, I, O):
+    """(order [P,N] i32, layer [P,N] i32, n_layers [P] i32, status [P] u32)."""
+    nodes, conns = _f64(nodes), _f64(conns)
+    P, N, C = _shapes(nodes, conns)
+    order = np.empty((P, N), np.int32)
+    layer = np.empty((P, N), np.int32)
+    nl = np.empty(P, np.int32)
+    st = np.empty(P, np.uint32)
+    rc = _load().or_transform(P, N, C, I, O, _ptr(nodes), _ptr(conns), _ptr(order), _ptr(layer),
+                              _ptr(nl), _ptr(st))
+    assert rc == 0, rc
+    return order, layer, nl, st
+
+
+def _inputs(inputs, P, I):
+    inputs = _f64(inputs)
+    assert inputs.ndim == 3 and inputs.shape[2] == I
+    if inputs.shape[0] == 1 and P != 1:
+        stride = 0
+    else:
+        assert inputs.shape[0] == P
+        stride = inputs.shape[1] * I
+    return inputs, stride, inputs.shape[1]
+
+
+def forward(nodes, conns, inputs, I, O, with_bound=False, with_values=False):
+    """outputs [P,S,O] f64 (and bound [P,S,O], values [P,S,N] when asked).
+    inputs is [P,S,I] or [1,S,I] (shared by every genome)."""
+    nodes, conns = _f64(nodes), _f64(conns)
+    P, N, C = _shapes(nodes, conns)
+    inputs, stride, S = _inputs(inputs, P, I)
+    out = np.empty((P, S, O), np.float64)
+    bnd = np.empty((P, S, O), np.float64) if with_bound else None
+    vals = np.empty((P, S, N), np.float64) if with_values else None
+    rc = _load().or_forward(P, N, C, I, O, _ptr(nodes), _ptr(conns), _ptr(inputs), stride, S,
+                            _ptr(out), _ptr(bnd), _ptr(vals))
+    assert rc == 0, rc
+    res = [out]
+    if with_bound:
+        res.append(bnd)
+    if with_values:
+        res.append(vals)
+    return res[0] if len(res) == 1 else tuple(res)
+
+
+def backward(nodes, conns, inputs, I, O, grad_out, want_inputs=True):
+    """(grad_w [P,C], grad_b [P,N], grad_r [P,N], grad_in [P,S,I] or None), all f64."""
+    nodes, conns = _f64(nodes), _f64(conns)
+    P, N, C = _shapes(nodes, conns)
+    inputs, stride, S = _inputs(inputs, P, I)
+    go = np.ascontiguousarray(grad_out, dtype=np.float64)
+    assert go.shape == (P, S, O)
+    gw = np.empty((P, C), np.float64)
+    gb = np.empty((P, N), np.float64)
+    gr = np.empty((P, N), np.float64)
+    gi = np.empty((P, S, I), np.float64) if want_inputs else None
+    rc = _load().or_backward(P, N, C, I, O, _ptr(nodes), _ptr(conns), _ptr(inputs), stride, S,
+                             _ptr(go), _ptr(gw), _ptr(gb), _ptr(gr), _ptr(gi))
+    assert rc == 0, rc
+    return gw, gb, gr, gi
+
+
+def hyperneat(nodes, conns, grid=32, thresh=0.2, qidx=None, with_raw=False, with_bound=False):
+    """Thresholded substrate weights [P, nq] (nq = grid^4 when qidx is None)."""
+    nodes, conns = _f64(nodes), _f64(conns)
+    P, N, C = _shapes(nodes, conns)
+    if qidx is not None:
+        qidx = np.ascontiguousarray(qidx, dtype=np.int64)
+        nq = qidx.size
+    else:
+        nq = grid ** 4
+    out = np.empty((P, nq), np.float64)
+    raw = np.empty((P, nq), np.float64) if with_raw else None
+    bnd = np.empty((P, nq), np.float64) if with_bound else None
+    rc = _load().or_hyperneat(P, N, C, _ptr(nodes), _ptr(conns), grid, thresh, _ptr(qidx),
+                              nq if qidx is not None else 0, _ptr(out), _ptr(raw), _ptr(bnd))
+    assert rc == 0, rc
+    res = [out]
+    if with_raw:
+        res.append(raw)
+    if with_bound:
+        res.append(bnd)
+    return res[0] if len(res) == 1 else tuple(res)
