@@ -1,0 +1,499 @@
+#!/usr/bin/env python
+"""Throughput of population-wide NEAT network evaluation on B300.
+
+Metric: connection evaluations per second, conn-evals/s = pop x samples x
+enabled connections / time (every enabled connection of every genome is
+evaluated once per input vector).
+
+Default workload (--config locomotion): 10,000 genomes with 27 inputs and
+8 outputs (N=128, C=512), one rollout of 1,000 sequential steps with one
+input vector per genome per step.  One benchmark step is the whole hot path
+on one batch: the transformation stage (validate, sort, layers, pack, queue)
+followed by the 1,000-step forward rollout, captured in one CUDA graph.  The
+step inputs (1.08 GB) exceed the 126 MB L2, so no step starts warm except
+for the population's programs, which a rollout re-reads by design.
+
+Legs of the JSON line:
+  value        device-resident throughput over K timed steps (CUDA events)
+  e2e          same metric through the public Rollout API from pinned host
+               buffers (H2D population + inputs, D2H outputs inside the timing)
+  roofline     forward kernel: algorithmic bytes / average launch duration
+  plain        the padded one-launch-per-step form on the same workload
+  cpu_baseline the FP64 oracle on the host cores, on a bounded sample
+
+--impl reference times the FP64 oracle (the reference of this build) on the
+same workload, one bounded sample per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "conn-evals/s (pop×samples×enabled conns), % roofline; batched/fwd+bwd vs plain"
+UNIT = "conn-evals/s"
+PEAKS_FALLBACK = {"hbm_gbs": 6400.0, "source": "fallback"}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        d["source"] = "measured"
+        return d
+    return dict(PEAKS_FALLBACK)
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="locomotion",
+                    choices=["locomotion", "uneven", "differentiation", "hyperneat", "tiny"])
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (one process per GPU; no collective on the data path)
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend)
+        pg = dist
+    return rank, world, local, pg
+
+
+def barrier(pg, device=None):
+    if pg is not None:
+        if device is not None:
+            pg.barrier(device_ids=[device.index])
+        else:
+            pg.barrier()
+
+
+def allreduce_max(pg, x, device):
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allreduce_sum(pg, x, device):
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.proc = None
+        try:
+            import torch
+            uuid = "GPU-" + str(torch.cuda.get_device_properties(device_index).uuid)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", uuid], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, mx, power = [], [], []
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                mx.append(float(f[1]))
+                power.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[4:8]):
+                if v == "Active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "power_w_max": max(power), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+def enabled_counts(nodes, conns):
+    """Enabled connections and valid nodes of every genome (host-side count of
+    the workload's size; padding rows have a NaN key)."""
+    valid_c = ~np.isnan(conns[..., 0]) & ~np.isnan(conns[..., 1])
+    en = valid_c & ~np.isnan(conns[..., 3]) & (conns[..., 3] != 0)
+    return en.sum(axis=1).astype(np.int64), (~np.isnan(nodes[..., 0])).sum(axis=1).astype(np.int64)
+
+
+def workload(name, seed):
+    from workloads import CONFIGS, make_population
+    cfg = CONFIGS[name]
+    spec = cfg["spec"]
+    nodes, conns = make_population(spec, cfg["P"], seed=seed)
+    return cfg, spec, nodes, conns
+
+
+def describe(name, cfg, spec):
+    if name == "locomotion":
+        return (f"locomotion rollout: pop={cfg['P']}, {spec.I} in / {spec.O} out, N={spec.N}, "
+                f"C={spec.C}, {cfg['steps']} sequential steps x S=1, transform + rollout per step")
+    if name == "uneven":
+        return (f"uneven batching: pop={cfg['P']}, V~logU[23,1024], E~logU[8,4096], S={cfg['S']}, "
+                f"{cfg['steps']} steps per rollout")
+    if name == "differentiation":
+        return f"differentiation: pop={cfg['P']}, S={cfg['S']}, forward+backward (MSE)"
+    if name == "hyperneat":
+        return f"HyperNEAT query: pop={cfg['P']} CPPNs, 32x32 substrate (2^20 queries each)"
+    return f"tiny XOR: pop={cfg['P']}, S=4"
+
+
+# ---------------------------------------------------------------------------
+def cpu_baseline(name, cfg, spec, nodes, conns, seed, budget_steps=None):
+    """The FP64 oracle as it stands (single thread) on a bounded sample."""
+    import oracle
+    from workloads import locomotion_inputs, regression_batch, uneven_inputs
+    E, _ = enabled_counts(nodes, conns)
+    t0 = time.perf_counter()
+    if name == "locomotion":
+        R = budget_steps or 200
+        x = np.concatenate([locomotion_inputs(seed, t, cfg["P"], spec.I) for t in range(R)], axis=1)
+        t0 = time.perf_counter()
+        oracle.forward(nodes, conns, x, spec.I, spec.O)
+        units = float(E.sum()) * R
+        sample = f"all {cfg['P']} genomes x {R} of the {cfg['steps']} rollout steps"
+    elif name == "uneven":
+        k = budget_steps or 1500
+        sel = np.arange(k)
+        x = uneven_inputs(seed, 0, cfg["P"])[sel]
+        t0 = time.perf_counter()
+        oracle.forward(nodes[sel], conns[sel], x, spec.I, spec.O)
+        units = float(E[sel].sum()) * cfg["S"]
+        sample = f"{k} of {cfg['P']} genomes x 1 step (S={cfg['S']})"
+    elif name == "differentiation":
+        k = budget_steps or 64
+        x, y = regression_batch(seed, cfg["S"])
+        t0 = time.perf_counter()
+        out = oracle.forward(nodes[:k], conns[:k], x, spec.I, spec.O)
+        go = (2.0 / cfg["S"]) * (out[..., 0] - y[None].astype(np.float64))
+        oracle.backward(nodes[:k], conns[:k], x, spec.I, spec.O, go[..., None], want_inputs=True)
+        units = float(E[:k].sum()) * cfg["S"]
+        sample = f"{k} of {cfg['P']} genomes, forward + backward at S={cfg['S']}"
+    elif name == "hyperneat":
+        k = budget_steps or 2
+        q = np.arange(32 ** 4 // 4)
+        t0 = time.perf_counter()
+        oracle.hyperneat(nodes[:k], conns[:k], grid=32, qidx=q)
+        units = float(E[:k].sum()) * q.size
+        sample = f"{k} of {cfg['P']} CPPNs x a quarter of the 2^20 queries"
+    else:
+        from workloads import xor_inputs
+        t0 = time.perf_counter()
+        for _ in range(200):
+            oracle.forward(nodes, conns, xor_inputs(), spec.I, spec.O)
+        units = float(E.sum()) * 4 * 200
+        sample = "200 repetitions of the whole population"
+    dt = time.perf_counter() - t0
+    return {"value": units / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+            "seconds": round(dt, 3)}
+
+
+# ---------------------------------------------------------------------------
+def bench_ours(args, rank, world, local, pg):
+    import torch
+    from paper_2504_08339_b300.api import Plan
+    from paper_2504_08339_b300.rollout import Rollout
+    from workloads import locomotion_inputs, regression_batch, uneven_inputs
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    peaks = load_peaks()
+    name = args.config
+    cfg, spec, nodes, conns = workload(name, args.seed + rank)
+    P = cfg["P"]
+    E, Vn = enabled_counts(nodes, conns)
+    plan = Plan(P, spec.N, spec.C, spec.I, spec.O, device=dev)
+    launches_per_step = 4  # transform, rank, offsets, pack
+    extra = {}
+
+    if name in ("locomotion", "uneven", "tiny"):
+        if name == "locomotion":
+            T, S, ring = cfg["steps"], 1, cfg["steps"]
+            host_in = np.stack([locomotion_inputs(args.seed + rank, t, P, spec.I) for t in range(T)])
+        elif name == "uneven":
+            T, S, ring = cfg["steps"], cfg["S"], 8
+            host_in = np.stack([uneven_inputs(args.seed + rank, t, P) for t in range(ring)])
+        else:
+            from workloads import xor_inputs
+            T, S, ring = 1, 4, 1
+            host_in = np.repeat(xor_inputs(), P, 0)[None]
+        ro = Rollout(plan, T, S=S, ring=ring, events=True)
+        ro.load(torch.from_numpy(nodes), torch.from_numpy(conns), torch.from_numpy(host_in),
+                non_blocking=False)
+        ro.capture()
+        units_per_step = float(E.sum()) * S * T
+        launches_per_step += T
+        run = ro.run
+        fwd_launches = T
+        alg_bytes = float((8 * E + 12 * Vn).sum() + 4 * S * (spec.I + spec.O) * P)
+    elif name == "differentiation":
+        S = cfg["S"]
+        x, y = regression_batch(args.seed + rank, S)
+        d_nodes = torch.from_numpy(nodes).to(dev)
+        d_conns = torch.from_numpy(conns).to(dev)
+        d_x = torch.from_numpy(x).to(dev)
+        d_y = torch.from_numpy(y).to(dev)
+        saved = torch.empty((P, S, spec.N), device=dev)
+        out = torch.empty((P, S, spec.O), device=dev)
+        go = torch.empty((P, S, spec.O), device=dev)
+        tr = plan.transform(d_nodes, d_conns)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))]
+
+        def run():
+            plan.transform(d_nodes, d_conns, out=tr)
+            ev[0][0].record()
+            plan.forward(d_x, out=out, saved=saved)
+            ev[0][1].record()
+            torch.sub(out[..., 0], d_y, out=go[..., 0])
+            go.mul_(2.0 / S)
+            return plan.backward(d_x, go, saved=saved)
+
+        units_per_step = float(E.sum()) * S
+        launches_per_step += 2
+        fwd_launches = 1
+        ro = None
+        alg_bytes = float((8 * E + 12 * Vn).sum() + 4 * S * (spec.I + spec.O) + 4 * S * spec.N * P)
+    else:  # hyperneat
+        d_nodes = torch.from_numpy(nodes).to(dev)
+        d_conns = torch.from_numpy(conns).to(dev)
+        tr = plan.transform(d_nodes, d_conns)
+        w = torch.empty((P, 1024, 1024), device=dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))]
+
+        def run():
+            plan.transform(d_nodes, d_conns, out=tr)
+            ev[0][0].record()
+            plan.hyperneat(32, cfg["thresh"], out=w)
+            ev[0][1].record()
+
+        units_per_step = float(E.sum()) * 2 ** 20
+        launches_per_step += 1
+        fwd_launches = 1
+        ro = None
+        alg_bytes = float((8 * E + 12 * Vn).sum() + 4.0 * 2 ** 20 * P)
+
+    # ---- timed region (device-resident inputs)
+    for _ in range(max(3, args.warmup)):
+        run()
+    torch.cuda.synchronize()
+    barrier(pg, dev)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    launch_ms = []
+    for _ in range(args.steps):
+        run()
+        if ro is not None:
+            pass
+    t1.record()
+    torch.cuda.synchronize()
+    ms = t0.elapsed_time(t1)
+    clk = clocks.stop()
+    barrier(pg, dev)
+    # per-launch durations of the forward kernel (events inside the graph; the
+    # last replay of the timed region)
+    if ro is not None:
+        try:
+            launch_ms = ro.launch_durations_ms()
+        except Exception:
+            launch_ms = []
+    else:
+        launch_ms = [ev[0][0].elapsed_time(ev[0][1])]
+    ms_max = allreduce_max(pg, ms, dev)
+    units_total = allreduce_sum(pg, units_per_step * args.steps, dev)
+    value = units_total / (ms_max / 1e3)
+
+    avg_launch_us = 1e3 * float(np.mean(launch_ms)) if launch_ms else None
+    roof = None
+    if avg_launch_us:
+        achieved = alg_bytes / (avg_launch_us * 1e-6) / 1e9
+        peak = float(peaks["hbm_gbs"])
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": None,
+                "kernel": "k_forward_sp" if name != "hyperneat" else "k_hyperneat",
+                "algorithmic_bytes_per_launch": int(alg_bytes),
+                "avg_launch_us": round(avg_launch_us, 3),
+                "peak_source": f"{peaks.get('source')} (MEASURED_PEAKS.json hbm_gbs)"}
+        extra["launch_us_min"] = round(1e3 * min(launch_ms), 3)
+        extra["launch_us_max"] = round(1e3 * max(launch_ms), 3)
+
+    # ---- plain padded one-launch-per-step form (eager launches, no graph)
+    plain = None
+    if not args.no_plain and name in ("locomotion", "uneven", "tiny"):
+        K = max(1, min(3, args.steps))
+        d_in = ro.inputs
+        out_p = torch.empty_like(ro.outputs[0])
+
+        def run_plain():
+            plan.transform(ro.nodes, ro.conns, out=ro.tr)
+            for t in range(ro.T):
+                plan.forward(d_in[t % ro.ring], out=out_p, plain=True)
+
+        run_plain()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(K):
+            run_plain()
+        b.record()
+        torch.cuda.synchronize()
+        pms = a.elapsed_time(b) / K
+        plain = {"value": units_per_step / (pms / 1e3), "ms_per_step": round(pms, 3),
+                 "form": "padded programs, one CTA per (genome, 32 samples), one launch per "
+                         "rollout step, eager (no graph)", "steps": K}
+
+    # ---- end to end through the public API from pinned host buffers
+    e2e = None
+    if not args.no_e2e and ro is not None:
+        h_nodes = torch.from_numpy(nodes).pin_memory()
+        h_conns = torch.from_numpy(conns).pin_memory()
+        h_in = torch.from_numpy(host_in).pin_memory()
+        h_out = torch.empty(ro.outputs.shape, dtype=torch.float32).pin_memory()
+        K = max(1, min(10, args.steps))
+        ro.run_host(h_nodes, h_conns, h_in, h_out)
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(K):
+            ro.run_host(h_nodes, h_conns, h_in, h_out)
+            _ = float(h_out.view(-1)[0]) if False else None
+        b.record()
+        torch.cuda.synchronize()
+        wall = (time.perf_counter() - w0) / K
+        ems = max(a.elapsed_time(b) / K, wall * 1e3)
+        h2d = h_nodes.numel() * 4 + h_conns.numel() * 4 + h_in.numel() * 4
+        d2h = h_out.numel() * 4
+        e2e = {"value": allreduce_sum(pg, units_per_step, dev) / (allreduce_max(pg, ems, dev) / 1e3),
+               "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": round(ems, 3), "steps": K}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = cpu_baseline(name, cfg, spec, nodes, conns, args.seed)
+
+    gpu_launches = launches_per_step * args.steps
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": max(3, args.warmup), "ms_per_step": round(ms_max / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded generators; random genomes shaped like the workload)",
+        "config": {"workload": describe(name, cfg, spec), "name": name, "pop": P,
+                   "enabled_conns_per_genome_mean": round(float(E.mean()), 2),
+                   "valid_nodes_per_genome_mean": round(float(Vn.mean()), 2),
+                   "form": "batched: persistent size-sorted queue over ragged-packed programs, "
+                           "CUDA graph", "parallelism": f"dp{world} (independent populations)",
+                   "l2": "step inputs exceed L2 (126 MB); programs L2-resident within a rollout"},
+        "clocks": clk, "gpu_launches": gpu_launches, "roofline": roof,
+        "cpu_baseline": cpu, "e2e": e2e, "plain": plain, "extra": extra,
+        "fwd_launches_per_step": fwd_launches,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def bench_reference(args, rank, world):
+    """The FP64 oracle, as it stands, on the host cores: every step is a
+    bounded sample of the same workload."""
+    if rank != 0:
+        return
+    name = args.config
+    cfg, spec, nodes, conns = workload(name, args.seed)
+    budget = {"locomotion": 8, "uneven": 150, "differentiation": 4, "hyperneat": 1, "tiny": None}[name]
+    for _ in range(max(3, args.warmup)):
+        cpu_baseline(name, cfg, spec, nodes, conns, args.seed, budget)
+    vals, secs = [], 0.0
+    rec = None
+    for _ in range(args.steps):
+        rec = cpu_baseline(name, cfg, spec, nodes, conns, args.seed, budget)
+        vals.append(rec["value"])
+        secs += rec["seconds"]
+    units = sum(v * 1.0 for v in vals)
+    value = float(np.mean(vals))
+    del units
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": max(3, args.warmup),
+        "ms_per_step": round(1e3 * secs / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": describe(name, cfg, spec), "name": name, "pop": cfg["P"]},
+        "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": rec["sample"], "value": value,
+                         "unit": UNIT},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    rank, world, local, pg = dist_setup(args)
+    try:
+        if args.impl == "reference":
+            bench_reference(args, rank, world)
+        else:
+            bench_ours(args, rank, world, local, pg)
+    finally:
+        if pg is not None:
+            pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,193 @@
+/*
+ * neat.h -- C ABI of the B300 (sm_103a) NEAT population-evaluation library.
+ *
+ * Evaluates a whole population of NEAT genomes held in the padded tensor
+ * encoding of TensorNEAT (arXiv 2504.08339):
+ *   Sec. 3.1 (Tensorized Encodings): one row per node / connection, rows past
+ *     a genome's size (and holes left by removal) are NaN padding; the
+ *     population tensors are P_N[P, N, .] and P_C[P, C, .].
+ *   Sec. 3.3 (Tensorized Network Inference): a transformation stage computes
+ *     the topological order N_order (and here also layer indices and a packed
+ *     per-genome program that replaces the dense C_exp tensor); a calculation
+ *     stage sets v[inputs] = I and, in N_order, v[k] = f_n(f_c(v | in-edges of
+ *     k) | attributes of k) with f_c = w * x and f_n = act(b + r * agg(.));
+ *     O = v[outputs].
+ *   App. B (genome interface): input_idx = arange(I), output_idx =
+ *     arange(I, I + O), i.e. node ROWS 0..I-1 are the inputs and rows
+ *     I..I+O-1 the outputs.
+ *
+ * Memory conventions (all entry points):
+ *   - Every array argument is a DEVICE pointer owned by the caller, row-major,
+ *     float32 or int32/uint32 as declared, aligned to its element size (conns
+ *     to 16 bytes).  The library never frees it and keeps no reference after
+ *     the call returns.  A misaligned or NULL required pointer gives
+ *     NEAT_ERR_ARG and launches nothing.
+ *   - The plan's workspace is caller-owned device memory of at least
+ *     neat_workspace_bytes() bytes (256-byte aligned); it holds the
+ *     transformed programs between calls.  The plan object itself is a small
+ *     host allocation.
+ *   - Calls are asynchronous on `stream`; the return code reports only host
+ *     side argument checks and launch errors.  Problems of individual genomes
+ *     are reported through the per-genome status words (NEAT_G_* bits).
+ *   - A plan must not be used on two streams at once.
+ *
+ * Node rows:       nodes[P, N, 5] = (key, bias, response, activation id, aggregation id)
+ * Connection rows: conns[P, C, 4] = (in key, out key, weight, enabled)
+ * A row is padding iff one of its key columns is NaN; a connection is enabled
+ * iff `enabled` is neither NaN nor 0.  Keys are integers in [0, 2^24), unique
+ * per genome, resolved by lookup (they need not equal row indices).
+ */
+#ifndef NEAT_H
+#define NEAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Same declaration as the CUDA runtime's stream handle. */
+typedef struct CUstream_st *cudaStream_t;
+
+typedef enum {
+  NEAT_OK = 0,
+  NEAT_ERR_ARG = -1,          /* bad size, NULL or misaligned pointer          */
+  NEAT_ERR_CUDA = -2,         /* a CUDA launch or runtime call failed           */
+  NEAT_ERR_WORKSPACE = -3,    /* workspace smaller than neat_workspace_bytes() */
+  NEAT_ERR_UNSUPPORTED = -4,  /* sizes beyond the library limits below          */
+  NEAT_ERR_STATE = -5         /* e.g. forward before any transform              */
+} neat_status;
+
+/* Limits of this build. */
+#define NEAT_MAX_NODES 1024
+#define NEAT_MAX_CONNS 8192
+
+/* Activation ids (node column 3): textbook, unscaled forms. */
+#define NEAT_ACT_IDENTITY 0 /* z                 */
+#define NEAT_ACT_SIGMOID 1  /* 1 / (1 + e^-z)    */
+#define NEAT_ACT_TANH 2     /* tanh z            */
+#define NEAT_ACT_RELU 3     /* max(0, z)         */
+#define NEAT_ACT_SIN 4      /* sin z             */
+#define NEAT_ACT_GAUSSIAN 5 /* e^(-z^2)          */
+#define NEAT_ACT_ABS 6      /* |z|               */
+/* Aggregation ids (node column 4); an empty aggregation is 0 for all four. */
+#define NEAT_AGG_SUM 0
+#define NEAT_AGG_PRODUCT 1
+#define NEAT_AGG_MAX 2 /* fmax fold (NaN-ignoring) */
+#define NEAT_AGG_MEAN 3
+
+/* Per-genome status bits written by neat_transform.  A genome with any bit
+ * set gets NaN outputs from the forward calls and zero gradients; with any
+ * bit other than CYCLE it also gets no order (order/layer all -1). */
+#define NEAT_G_CYCLE 1u            /* enabled connections form a cycle (or a self-loop) */
+#define NEAT_G_DANGLING_KEY 2u     /* an enabled connection names a key no node has      */
+#define NEAT_G_DUP_KEY 4u          /* two valid node rows share a key                    */
+#define NEAT_G_DUP_EDGE 8u         /* two enabled rows with the same (in, out)           */
+#define NEAT_G_EDGE_INTO_INPUT 16u /* an enabled connection ends at an input node        */
+#define NEAT_G_BAD_ATTR 32u        /* key not an integer in [0,2^24); act/agg id out of
+                                      range or not integral; NaN bias/response on a
+                                      non-input node; NaN weight on an enabled row   */
+#define NEAT_G_IO_ROW_INVALID 64u  /* one of rows 0..I+O-1 is padding                    */
+
+typedef struct neat_plan neat_plan;
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+int neat_version(void);
+
+/* Human-readable name of a status code (static string). */
+const char *neat_status_string(neat_status s);
+
+/* The cudaError_t value behind the calling thread's most recent
+ * NEAT_ERR_CUDA (0 if none occurred). */
+int neat_last_cuda_error(void);
+
+/* Bytes of device workspace a plan for these sizes needs (0 on bad sizes).
+ * Sizes: P >= 0 genomes, N in [I+O, NEAT_MAX_NODES] node rows, C in
+ * [1, NEAT_MAX_CONNS] connection rows, I >= 1 inputs, O >= 1 outputs. */
+size_t neat_workspace_bytes(int P, int N, int C, int I, int O);
+
+/* Create a plan.  `workspace` is caller-owned device memory (256-byte
+ * aligned, >= neat_workspace_bytes(P,N,C,I,O) bytes) that must outlive the
+ * plan.  The plan binds to the current CUDA device.  *out is set on success. */
+neat_status neat_plan_create(neat_plan **out, int P, int N, int C, int I, int O,
+                             void *workspace, size_t workspace_bytes);
+
+/* Destroy a plan (host memory only; the workspace stays the caller's). */
+neat_status neat_plan_destroy(neat_plan *plan);
+
+/* Tuning knobs picked by the autotuner (0 = library default).
+ *   warps_per_cta    warps of a sample-parallel CTA (1..16)
+ *   samples_per_lane samples one lane evaluates in the sample-parallel forward (1, 2, 4)
+ *   genomes_per_batch genomes packed into one CTA by the small-sample forward (1..64)
+ *   small_s_max      largest S that uses the small-sample (level-synchronous) forward */
+typedef struct {
+  int warps_per_cta;
+  int samples_per_lane;
+  int genomes_per_batch;
+  int small_s_max;
+} neat_tuning;
+neat_status neat_plan_set_tuning(neat_plan *plan, const neat_tuning *t);
+neat_status neat_plan_get_tuning(const neat_plan *plan, neat_tuning *t);
+
+/* Transformation stage (Sec. 3.3) for all P genomes.
+ *   nodes   [P, N, 5] f32, conns [P, C, 4] f32 (read only)
+ *   order   [P, N] i32 out: node ROWS in topological order -- Kahn by frontier,
+ *           each frontier in ascending key -- padded with -1
+ *   layer   [P, N] i32 out: frontier index of each row (-1 for padding rows
+ *           and rows not emitted)
+ *   n_layers[P] i32 out, gstatus [P] u32 out (NEAT_G_* bits)
+ * Also (re)builds the plan's packed programs; later forward/backward calls
+ * evaluate the genomes of the most recent transform. */
+neat_status neat_transform(neat_plan *plan, const float *nodes, const float *conns, int32_t *order,
+                           int32_t *layer, int32_t *n_layers, uint32_t *gstatus,
+                           cudaStream_t stream);
+
+/* Calculation stage (Sec. 3.3), batched form: one persistent launch pulls
+ * size-sorted genomes from a device work queue over ragged-packed programs.
+ *   inputs  genome g, sample s, input i at inputs[g * in_pop_stride + s * I + i]
+ *           (in_pop_stride 0 = one input set shared by all genomes; otherwise
+ *           >= S * I)
+ *   S       input vectors per genome (S >= 0)
+ *   outputs [P, S, O] f32 out; NaN for genomes with a nonzero status
+ *   saved   optional [P, S, N] f32 out (NULL to skip): per canonical position,
+ *           the aggregated input a of each node, kept for neat_backward. */
+neat_status neat_forward(neat_plan *plan, const float *inputs, int64_t in_pop_stride, int S,
+                         float *outputs, float *saved, cudaStream_t stream);
+
+/* Calculation stage, plain padded form (the comparison baseline): one CTA per
+ * (genome, 32 samples) walking all N padded positions; no queue, no packing.
+ * Same arguments and results as neat_forward (no saved buffer). */
+neat_status neat_forward_plain(neat_plan *plan, const float *inputs, int64_t in_pop_stride, int S,
+                               float *outputs, cudaStream_t stream);
+
+/* Reverse mode of the calculation stage (no counterpart in the paper; the
+ * gradient of L with respect to weights, biases, responses and inputs given
+ * grad_outputs = dL/dO).
+ *   inputs, in_pop_stride, S as in neat_forward
+ *   grad_outputs [P, S, O] f32
+ *   saved        the buffer filled by neat_forward with the same inputs, or
+ *                NULL to recompute the forward values inside the kernel
+ *   grad_weight  [P, C] f32 out, by connection row (0 on padding/disabled rows)
+ *   grad_bias, grad_response [P, N] f32 out, by node row (0 on inputs/padding)
+ *   grad_inputs  optional [P, S, I] f32 out (NULL to skip); with a shared input
+ *                set (in_pop_stride 0) it is still written per genome.
+ * Sums over samples are deterministic (no floating-point atomics). */
+neat_status neat_backward(neat_plan *plan, const float *inputs, int64_t in_pop_stride, int S,
+                          const float *grad_outputs, const float *saved, float *grad_weight,
+                          float *grad_bias, float *grad_response, float *grad_inputs,
+                          cudaStream_t stream);
+
+/* HyperNEAT substrate query (the CPPN use of NEAT networks).  Requires I = 5,
+ * O = 1.  For every genome and every (source, target) pair of a grid x grid
+ * substrate, cell c = j * grid + i at (x, y) = (-1 + 2i/(grid-1),
+ * -1 + 2j/(grid-1)), the CPPN is evaluated on (x_s, y_s, x_t, y_t, 1) and
+ *   weights[g, s, t] = o if |o| > thresh else 0        ([P, grid^2, grid^2] f32)
+ * Coordinates are generated in the kernel.  2 <= grid <= 128. */
+neat_status neat_hyperneat_query(neat_plan *plan, int grid, float thresh, float *weights,
+                                 cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NEAT_H */

@@ -1,0 +1,205 @@
+"""Torch-facing wrapper of the C ABI: device memory and streams come from
+PyTorch, every computation happens in libneat.so's kernels."""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import torch
+
+from . import _lib
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _need(t, name, dtype, shape=None):
+    if not isinstance(t, torch.Tensor) or t.device.type != "cuda":
+        raise _lib.NeatError(f"{name} must be a CUDA tensor (no CPU path exists)")
+    if t.dtype != dtype:
+        raise _lib.NeatError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise _lib.NeatError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise _lib.NeatError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+
+
+@dataclass
+class Transformed:
+    order: torch.Tensor      # [P, N] int32, node rows in topological order, -1 padded
+    layer: torch.Tensor      # [P, N] int32
+    n_layers: torch.Tensor   # [P] int32
+    status: torch.Tensor     # [P] int32 (uint32 bits)
+
+
+class Plan:
+    """A population plan: P genomes of N node rows and C connection rows with
+    I inputs and O outputs, bound to the current CUDA device.  The workspace
+    (device memory for the transformed programs) is a torch allocation."""
+
+    def __init__(self, P, N, C, I, O, device=None):
+        lib = _lib.load()
+        self.P, self.N, self.C, self.I, self.O = int(P), int(N), int(C), int(I), int(O)
+        self.device = torch.device(device) if device is not None else torch.device(
+            "cuda", torch.cuda.current_device())
+        nbytes = lib.neat_workspace_bytes(self.P, self.N, self.C, self.I, self.O)
+        if nbytes == 0:
+            raise _lib.NeatError(f"unsupported sizes P={P} N={N} C={C} I={I} O={O}")
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=self.device)
+        base = self.workspace.data_ptr()
+        self._ws_ptr = (base + 255) // 256 * 256
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _lib.check(lib.neat_plan_create(ctypes.byref(self._h), self.P, self.N, self.C, self.I,
+                                            self.O, ctypes.c_void_p(self._ws_ptr), nbytes),
+                       "neat_plan_create")
+        self._lib = lib
+
+    # -- lifecycle -------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.neat_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- tuning ------------------------------------------------------------------
+    def get_tuning(self) -> dict:
+        t = _lib.neat_tuning()
+        _lib.check(self._lib.neat_plan_get_tuning(self._h, ctypes.byref(t)), "get_tuning")
+        return {k: getattr(t, k) for k, _ in t._fields_}
+
+    def set_tuning(self, **kw):
+        t = _lib.neat_tuning()
+        for k, v in kw.items():
+            setattr(t, k, int(v))
+        _lib.check(self._lib.neat_plan_set_tuning(self._h, ctypes.byref(t)), "set_tuning")
+
+    # -- transformation stage -----------------------------------------------------
+    def transform(self, nodes, conns, out: Transformed | None = None, stream=None) -> Transformed:
+        P, N, C = self.P, self.N, self.C
+        _need(nodes, "nodes", torch.float32, (P, N, 5))
+        _need(conns, "conns", torch.float32, (P, C, 4))
+        if out is None:
+            dev = nodes.device
+            out = Transformed(torch.empty((P, N), dtype=torch.int32, device=dev),
+                              torch.empty((P, N), dtype=torch.int32, device=dev),
+                              torch.empty((P,), dtype=torch.int32, device=dev),
+                              torch.empty((P,), dtype=torch.int32, device=dev))
+        _lib.check(self._lib.neat_transform(self._h, _ptr(nodes), _ptr(conns), _ptr(out.order),
+                                            _ptr(out.layer), _ptr(out.n_layers),
+                                            _ptr(out.status), _stream(stream)),
+                   "neat_transform")
+        return out
+
+    # -- calculation stage ---------------------------------------------------------
+    def _inputs(self, inputs):
+        _need(inputs, "inputs", torch.float32)
+        if inputs.dim() != 3 or inputs.shape[2] != self.I:
+            raise _lib.NeatError(f"inputs must be [P or 1, S, {self.I}]")
+        S = inputs.shape[1]
+        if inputs.shape[0] == self.P:
+            stride = S * self.I
+        elif inputs.shape[0] == 1:
+            stride = 0
+        else:
+            raise _lib.NeatError("inputs must have P or 1 rows")
+        return S, stride
+
+    def forward(self, inputs, out=None, saved=None, plain=False, stream=None):
+        """outputs [P, S, O]; inputs [P, S, I] or [1, S, I] (shared)."""
+        S, stride = self._inputs(inputs)
+        if out is None:
+            out = torch.empty((self.P, S, self.O), dtype=torch.float32, device=inputs.device)
+        _need(out, "out", torch.float32, (self.P, S, self.O))
+        if plain:
+            code = self._lib.neat_forward_plain(self._h, _ptr(inputs), stride, S, _ptr(out),
+                                                _stream(stream))
+            _lib.check(code, "neat_forward_plain")
+        else:
+            if saved is not None:
+                _need(saved, "saved", torch.float32, (self.P, S, self.N))
+            code = self._lib.neat_forward(self._h, _ptr(inputs), stride, S, _ptr(out),
+                                          _ptr(saved), _stream(stream))
+            _lib.check(code, "neat_forward")
+        return out
+
+    def backward(self, inputs, grad_out, saved=None, want_inputs=True, stream=None):
+        """(grad_weight [P,C], grad_bias [P,N], grad_response [P,N], grad_inputs [P,S,I] or None)."""
+        S, stride = self._inputs(inputs)
+        _need(grad_out, "grad_out", torch.float32, (self.P, S, self.O))
+        if saved is not None:
+            _need(saved, "saved", torch.float32, (self.P, S, self.N))
+        dev = inputs.device
+        gw = torch.empty((self.P, self.C), dtype=torch.float32, device=dev)
+        gb = torch.empty((self.P, self.N), dtype=torch.float32, device=dev)
+        gr = torch.empty((self.P, self.N), dtype=torch.float32, device=dev)
+        gi = torch.empty((self.P, S, self.I), dtype=torch.float32, device=dev) if want_inputs else None
+        code = self._lib.neat_backward(self._h, _ptr(inputs), stride, S, _ptr(grad_out),
+                                       _ptr(saved), _ptr(gw), _ptr(gb), _ptr(gr), _ptr(gi),
+                                       _stream(stream))
+        _lib.check(code, "neat_backward")
+        return gw, gb, gr, gi
+
+    def hyperneat(self, grid=32, thresh=0.2, out=None, stream=None):
+        """Substrate weights [P, grid^2, grid^2] of every CPPN (I=5, O=1)."""
+        G2 = grid * grid
+        if out is None:
+            out = torch.empty((self.P, G2, G2), dtype=torch.float32, device=self.device)
+        _need(out, "out", torch.float32, (self.P, G2, G2))
+        _lib.check(self._lib.neat_hyperneat_query(self._h, int(grid), float(thresh), _ptr(out),
+                                                  _stream(stream)), "neat_hyperneat_query")
+        return out
+
+
+class NeatFunction(torch.autograd.Function):
+    """outputs = network(nodes, conns)(inputs), differentiable with respect to
+    the bias/response columns of nodes, the weight column of conns and the
+    inputs.  Stores the per-node aggregates when they fit (`store=True`),
+    otherwise the backward recomputes the forward values in the kernel."""
+
+    @staticmethod
+    def forward(ctx, plan: Plan, nodes, conns, inputs, store: bool = True):
+        plan.transform(nodes, conns)
+        S = inputs.shape[1]
+        saved = None
+        if store:
+            saved = torch.empty((plan.P, S, plan.N), dtype=torch.float32, device=inputs.device)
+        out = plan.forward(inputs, saved=saved)
+        ctx.plan = plan
+        ctx.saved_agg = saved
+        ctx.save_for_backward(nodes, conns, inputs)
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        nodes, conns, inputs = ctx.saved_tensors
+        plan = ctx.plan
+        gw, gb, gr, gi = plan.backward(inputs, grad_out.contiguous(), saved=ctx.saved_agg,
+                                       want_inputs=ctx.needs_input_grad[3])
+        g_nodes = g_conns = g_inputs = None
+        if ctx.needs_input_grad[1]:
+            g_nodes = torch.zeros_like(nodes)
+            g_nodes[..., 1] = gb
+            g_nodes[..., 2] = gr
+        if ctx.needs_input_grad[2]:
+            g_conns = torch.zeros_like(conns)
+            g_conns[..., 2] = gw
+        if ctx.needs_input_grad[3]:
+            g_inputs = gi if inputs.shape[0] == plan.P else gi.sum(0, keepdim=True)
+        return None, g_nodes, g_conns, g_inputs, None
+
+
+def evaluate(plan: Plan, nodes, conns, inputs, store: bool = True):
+    """Differentiable population evaluation (see NeatFunction)."""
+    return NeatFunction.apply(plan, nodes, conns, inputs, store)

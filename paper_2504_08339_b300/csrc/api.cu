@@ -1,0 +1,254 @@
+// Host side of the C ABI declared in include/neat.h: the plan object,
+// argument checks, launch-shape choices, and the exported entry points.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "neat_internal.cuh"
+
+struct neat_plan {
+  int device;
+  int P, N, C, I, O;
+  void *ws;
+  size_t ws_bytes;
+  neat::Layout L;
+  neat::Ws w;
+  int sm_count;
+  int smem_optin;
+  neat_tuning tune;
+  int transformed;
+};
+
+namespace {
+
+constexpr int kVersion = 100;  // 0.1.0
+
+bool aligned(const void *p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+bool sizes_ok(int P, int N, int C, int I, int O) {
+  return P >= 0 && I >= 1 && O >= 1 && N >= I + O && N <= NEAT_MAX_NODES && C >= 1 &&
+         C <= NEAT_MAX_CONNS && P <= (1 << 24);
+}
+
+thread_local int g_last_cuda_error = 0;
+
+neat_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return NEAT_OK;
+  g_last_cuda_error = int(e);
+  return NEAT_ERR_CUDA;
+}
+
+// warps per CTA of the sample-parallel kernels: as many [N][32] value
+// arrays as fit in ~96 KB, 1..8
+int default_sp_warps(int N) {
+  const size_t per = size_t(N) * 32 * sizeof(float);
+  int w = int((96 * 1024) / per);
+  return std::max(1, std::min(8, w));
+}
+
+int sp_warps(const neat_plan *p) {
+  int w = p->tune.warps_per_cta > 0 ? p->tune.warps_per_cta : default_sp_warps(p->N);
+  while (w > 1 && neat::forward_sp_smem(p->N, w) > size_t(p->smem_optin)) --w;
+  return w;
+}
+
+int backward_warps(const neat_plan *p) {
+  int w = 8;
+  while (w > 1 && neat::backward_smem(p->N, p->C, w) > size_t(200 * 1024)) --w;
+  return w;
+}
+
+neat_status check_inputs(const neat_plan *p, const float *inputs, int64_t stride, int S) {
+  if (S < 0) return NEAT_ERR_ARG;
+  if (S == 0 || p->P == 0) return NEAT_OK;
+  if (inputs == nullptr || !aligned(inputs, 4)) return NEAT_ERR_ARG;
+  if (stride != 0 && stride < int64_t(S) * p->I) return NEAT_ERR_ARG;
+  return NEAT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int neat_version(void) { return kVersion; }
+
+int neat_last_cuda_error(void) { return g_last_cuda_error; }
+
+const char *neat_status_string(neat_status s) {
+  switch (s) {
+    case NEAT_OK: return "ok";
+    case NEAT_ERR_ARG: return "invalid argument";
+    case NEAT_ERR_CUDA: return "CUDA error";
+    case NEAT_ERR_WORKSPACE: return "workspace too small";
+    case NEAT_ERR_UNSUPPORTED: return "unsupported size";
+    case NEAT_ERR_STATE: return "plan not transformed";
+  }
+  return "unknown status";
+}
+
+size_t neat_workspace_bytes(int P, int N, int C, int I, int O) {
+  if (!sizes_ok(P, N, C, I, O)) return 0;
+  return neat::make_layout(P, N, C, I, O).total;
+}
+
+neat_status neat_plan_create(neat_plan **out, int P, int N, int C, int I, int O, void *workspace,
+                             size_t workspace_bytes) {
+  if (out == nullptr) return NEAT_ERR_ARG;
+  *out = nullptr;
+  if (!sizes_ok(P, N, C, I, O)) return NEAT_ERR_UNSUPPORTED;
+  const neat::Layout L = neat::make_layout(P, N, C, I, O);
+  if (workspace == nullptr || !aligned(workspace, 256)) return NEAT_ERR_ARG;
+  if (workspace_bytes < L.total) return NEAT_ERR_WORKSPACE;
+  neat_plan *p = new (std::nothrow) neat_plan;
+  if (p == nullptr) return NEAT_ERR_ARG;
+  std::memset(p, 0, sizeof(*p));
+  p->P = P; p->N = N; p->C = C; p->I = I; p->O = O;
+  p->ws = workspace;
+  p->ws_bytes = workspace_bytes;
+  p->L = L;
+  p->w = neat::make_ws(workspace, L, P, N, C, I, O);
+  cudaError_t e = cudaGetDevice(&p->device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&p->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device);
+  if (e == cudaSuccess && neat::transform_smem(N, C) > size_t(p->smem_optin))
+    e = cudaErrorInvalidValue;
+  if (e == cudaSuccess) e = neat::transform_set_smem_limit(p->smem_optin);
+  if (e == cudaSuccess) e = neat::forward_set_smem_limit(p->smem_optin);
+  if (e == cudaSuccess) e = neat::backward_set_smem_limit(p->smem_optin);
+  // zero the headers and queue counters so a plan is in a defined state
+  if (e == cudaSuccess) e = cudaMemset(static_cast<char *>(workspace) + L.hdr, 0,
+                                       sizeof(neat::GenomeHdr) * size_t(P));
+  if (e == cudaSuccess) e = cudaMemset(static_cast<char *>(workspace) + L.counters, 0,
+                                       sizeof(uint32_t) * 64);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    delete p;
+    return cuda_status(e);
+  }
+  *out = p;
+  return NEAT_OK;
+}
+
+neat_status neat_plan_destroy(neat_plan *plan) {
+  if (plan == nullptr) return NEAT_ERR_ARG;
+  delete plan;
+  return NEAT_OK;
+}
+
+neat_status neat_plan_set_tuning(neat_plan *plan, const neat_tuning *t) {
+  if (plan == nullptr || t == nullptr) return NEAT_ERR_ARG;
+  if (t->warps_per_cta < 0 || t->warps_per_cta > 16) return NEAT_ERR_ARG;
+  if (!(t->samples_per_lane == 0 || t->samples_per_lane == 1 || t->samples_per_lane == 2 ||
+        t->samples_per_lane == 4))
+    return NEAT_ERR_ARG;
+  if (t->genomes_per_batch < 0 || t->genomes_per_batch > 64) return NEAT_ERR_ARG;
+  if (t->small_s_max < 0) return NEAT_ERR_ARG;
+  plan->tune = *t;
+  return NEAT_OK;
+}
+
+neat_status neat_plan_get_tuning(const neat_plan *plan, neat_tuning *t) {
+  if (plan == nullptr || t == nullptr) return NEAT_ERR_ARG;
+  *t = plan->tune;
+  if (t->warps_per_cta == 0) t->warps_per_cta = sp_warps(plan);
+  if (t->samples_per_lane == 0) t->samples_per_lane = 1;
+  return NEAT_OK;
+}
+
+neat_status neat_transform(neat_plan *plan, const float *nodes, const float *conns, int32_t *order,
+                           int32_t *layer, int32_t *n_layers, uint32_t *gstatus,
+                           cudaStream_t stream) {
+  if (plan == nullptr) return NEAT_ERR_ARG;
+  if (plan->P > 0) {
+    if (nodes == nullptr || conns == nullptr || order == nullptr || layer == nullptr ||
+        n_layers == nullptr || gstatus == nullptr)
+      return NEAT_ERR_ARG;
+    if (!aligned(nodes, 4) || !aligned(conns, 16) || !aligned(order, 4) || !aligned(layer, 4) ||
+        !aligned(n_layers, 4) || !aligned(gstatus, 4))
+      return NEAT_ERR_ARG;
+  }
+  cudaError_t e = neat::launch_transform(plan->w, nodes, conns, order, layer, n_layers, gstatus,
+                                         stream);
+  if (e == cudaSuccess) e = neat::launch_queue_build(plan->w, 0, stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  plan->transformed = 1;
+  return NEAT_OK;
+}
+
+neat_status neat_forward(neat_plan *plan, const float *inputs, int64_t in_pop_stride, int S,
+                         float *outputs, float *saved, cudaStream_t stream) {
+  if (plan == nullptr) return NEAT_ERR_ARG;
+  if (!plan->transformed) return NEAT_ERR_STATE;
+  neat_status s = check_inputs(plan, inputs, in_pop_stride, S);
+  if (s != NEAT_OK) return s;
+  if (S == 0 || plan->P == 0) return NEAT_OK;
+  if (outputs == nullptr || !aligned(outputs, 4) || (saved && !aligned(saved, 4)))
+    return NEAT_ERR_ARG;
+  const int warps = sp_warps(plan);
+  const size_t smem = neat::forward_sp_smem(plan->N, warps);
+  const int occ = std::max(1, neat::forward_sp_occupancy(warps, smem));
+  const int64_t items = int64_t(plan->P) * ((S + 31) / 32);
+  const int64_t want = (items + warps - 1) / warps;
+  const int grid = int(std::max<int64_t>(1, std::min<int64_t>(int64_t(plan->sm_count) * occ, want)));
+  return cuda_status(neat::launch_forward_sp(plan->w, inputs, in_pop_stride, S, outputs, saved,
+                                             warps, grid, stream));
+}
+
+neat_status neat_forward_plain(neat_plan *plan, const float *inputs, int64_t in_pop_stride, int S,
+                               float *outputs, cudaStream_t stream) {
+  if (plan == nullptr) return NEAT_ERR_ARG;
+  if (!plan->transformed) return NEAT_ERR_STATE;
+  neat_status s = check_inputs(plan, inputs, in_pop_stride, S);
+  if (s != NEAT_OK) return s;
+  if (S == 0 || plan->P == 0) return NEAT_OK;
+  if (outputs == nullptr || !aligned(outputs, 4)) return NEAT_ERR_ARG;
+  if ((S + 31) / 32 > 65535) return NEAT_ERR_UNSUPPORTED;
+  return cuda_status(neat::launch_forward_plain(plan->w, inputs, in_pop_stride, S, outputs, stream));
+}
+
+neat_status neat_backward(neat_plan *plan, const float *inputs, int64_t in_pop_stride, int S,
+                          const float *grad_outputs, const float *saved, float *grad_weight,
+                          float *grad_bias, float *grad_response, float *grad_inputs,
+                          cudaStream_t stream) {
+  if (plan == nullptr) return NEAT_ERR_ARG;
+  if (!plan->transformed) return NEAT_ERR_STATE;
+  neat_status s = check_inputs(plan, inputs, in_pop_stride, S);
+  if (s != NEAT_OK) return s;
+  if (plan->P == 0) return NEAT_OK;
+  if (grad_weight == nullptr || grad_bias == nullptr || grad_response == nullptr)
+    return NEAT_ERR_ARG;
+  if (S > 0 && grad_outputs == nullptr) return NEAT_ERR_ARG;
+  if (!aligned(grad_weight, 4) || !aligned(grad_bias, 4) || !aligned(grad_response, 4) ||
+      (grad_outputs && !aligned(grad_outputs, 4)) || (saved && !aligned(saved, 4)) ||
+      (grad_inputs && !aligned(grad_inputs, 4)))
+    return NEAT_ERR_ARG;
+  const int warps = backward_warps(plan);
+  if (neat::backward_smem(plan->N, plan->C, warps) > size_t(plan->smem_optin))
+    return NEAT_ERR_UNSUPPORTED;
+  return cuda_status(neat::launch_backward(plan->w, inputs, in_pop_stride, S, grad_outputs, saved,
+                                           grad_weight, grad_bias, grad_response, grad_inputs,
+                                           warps, stream));
+}
+
+neat_status neat_hyperneat_query(neat_plan *plan, int grid, float thresh, float *weights,
+                                 cudaStream_t stream) {
+  if (plan == nullptr) return NEAT_ERR_ARG;
+  if (!plan->transformed) return NEAT_ERR_STATE;
+  if (plan->I != 5 || plan->O != 1) return NEAT_ERR_UNSUPPORTED;
+  if (grid < 2 || grid > 128) return NEAT_ERR_ARG;
+  if (plan->P == 0) return NEAT_OK;
+  if (weights == nullptr || !aligned(weights, 4)) return NEAT_ERR_ARG;
+  const int warps = sp_warps(plan);
+  const size_t smem = neat::forward_sp_smem(plan->N, warps);
+  const int occ = std::max(1, neat::hyperneat_occupancy(warps, smem));
+  return cuda_status(neat::launch_hyperneat(plan->w, grid, thresh, weights, warps,
+                                            plan->sm_count * occ, stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,490 @@
+// Transformation stage (TensorNEAT Sec. 3.3): per genome, decode the padded
+// rows (Sec. 3.1), check them, sort nodes by key, resolve connection keys,
+// run Kahn's algorithm frontier by frontier (ascending key inside a frontier,
+// so the order is the unique sort by (layer, key)), and write the order, the
+// layer indices and a packed program that replaces the dense C_exp tensor.
+//
+// One CTA per genome; everything lives in shared memory.  Then three small
+// kernels build the size-sorted work queue and the ragged-packed copy.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "neat_internal.cuh"
+
+namespace neat {
+namespace {
+
+constexpr float KEY_LIMIT = 16777216.0f;  // 2^24
+
+__device__ __forceinline__ bool is_int_in(float x, float lo, float hi) {
+  return x == x && x >= lo && x < hi && x == floorf(x);
+}
+
+// Exclusive scan of a[0..n) in place; returns the total.  All threads call it.
+__device__ int block_exclusive_scan(int *a, int n, int *wbuf) {
+  const int T = blockDim.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int nw = (T + 31) >> 5;
+  const int per = (n + T - 1) / T;
+  const int b = min(tid * per, n), e = min(b + per, n);
+  int s = 0;
+  for (int i = b; i < e; ++i) s += a[i];
+  int x = s;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane == 31) wbuf[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int w = lane < nw ? wbuf[lane] : 0;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, w, d);
+      if (lane >= d) w += y;
+    }
+    if (lane < nw) wbuf[lane] = w;
+  }
+  __syncthreads();
+  int base = (wid > 0 ? wbuf[wid - 1] : 0) + x - s;
+  const int total = wbuf[nw - 1];
+  for (int i = b; i < e; ++i) {
+    int v = a[i];
+    a[i] = base;
+    base += v;
+  }
+  __syncthreads();
+  return total;
+}
+
+// Ascending bitonic sort of a[0..n2), n2 a power of two.
+__device__ void bitonic_sort_u64(uint64_t *a, int n2) {
+  for (int k = 2; k <= n2; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < (n2 >> 1); i += blockDim.x) {
+        const int lo = ((i & ~(j - 1)) << 1) | (i & (j - 1));
+        const int hi = lo + j;
+        const uint64_t x = a[lo], y = a[hi];
+        const bool up = (lo & k) == 0;
+        if ((x > y) == up) {
+          a[lo] = y;
+          a[hi] = x;
+        }
+      }
+      __syncthreads();
+    }
+}
+
+__host__ __device__ inline int pow2_ceil(int x) {
+  int p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+struct TSmem {
+  // byte offsets into dynamic shared memory
+  int sk, ek, key_s, row_of_s, s_of_row, indeg, rem, inbeg, outbeg, outfill, order_s, layer_s,
+      pos_of, tmp, ready, outlist, total;
+};
+
+__host__ __device__ inline TSmem tsmem_layout(int N, int C) {
+  TSmem L;
+  const int N2 = pow2_ceil(N), C2 = pow2_ceil(C);
+  int off = 0;
+  auto take = [&](int bytes) { int o = off; off += (bytes + 15) & ~15; return o; };
+  L.sk = take(8 * N2);
+  L.ek = take(8 * C2);
+  L.key_s = take(4 * N);
+  L.row_of_s = take(4 * N);
+  L.s_of_row = take(4 * N);
+  L.indeg = take(4 * N);
+  L.rem = take(4 * N);
+  L.inbeg = take(4 * N);
+  L.outbeg = take(4 * (N + 1));
+  L.outfill = take(4 * N);
+  L.order_s = take(4 * N);
+  L.layer_s = take(4 * N);
+  L.pos_of = take(4 * N);
+  L.tmp = take(4 * (N + 1));
+  L.ready = take(4 * N);
+  L.outlist = take(4 * C);
+  L.total = off;
+  return L;
+}
+
+__global__ void __launch_bounds__(256) k_transform(Ws w, const float *__restrict__ nodes,
+                                                   const float *__restrict__ conns,
+                                                   int32_t *__restrict__ order,
+                                                   int32_t *__restrict__ layer,
+                                                   int32_t *__restrict__ n_layers,
+                                                   uint32_t *__restrict__ gstatus) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  __shared__ int wbuf[33];
+  __shared__ unsigned s_status;
+  __shared__ int s_V, s_E;
+
+  const int N = w.N, C = w.C, I = w.I, O = w.O;
+  const int g = blockIdx.x, tid = threadIdx.x, T = blockDim.x;
+  const TSmem L = tsmem_layout(N, C);
+  uint64_t *sk = reinterpret_cast<uint64_t *>(sm + L.sk);
+  uint64_t *ek = reinterpret_cast<uint64_t *>(sm + L.ek);
+  int *key_s = reinterpret_cast<int *>(sm + L.key_s);
+  int *row_of_s = reinterpret_cast<int *>(sm + L.row_of_s);
+  int *s_of_row = reinterpret_cast<int *>(sm + L.s_of_row);
+  int *indeg = reinterpret_cast<int *>(sm + L.indeg);
+  int *rem = reinterpret_cast<int *>(sm + L.rem);
+  int *inbeg = reinterpret_cast<int *>(sm + L.inbeg);
+  int *outbeg = reinterpret_cast<int *>(sm + L.outbeg);
+  int *outfill = reinterpret_cast<int *>(sm + L.outfill);
+  int *order_s = reinterpret_cast<int *>(sm + L.order_s);
+  int *layer_s = reinterpret_cast<int *>(sm + L.layer_s);
+  int *pos_of = reinterpret_cast<int *>(sm + L.pos_of);
+  int *tmp = reinterpret_cast<int *>(sm + L.tmp);
+  int *ready = reinterpret_cast<int *>(sm + L.ready);
+  int *outlist = reinterpret_cast<int *>(sm + L.outlist);
+  const int N2 = pow2_ceil(N), C2 = pow2_ceil(C);
+
+  const float *gn = nodes + size_t(g) * N * 5;
+  const float *gc = conns + size_t(g) * C * 4;
+
+  if (tid == 0) { s_status = 0u; s_V = 0; s_E = 0; }
+  __syncthreads();
+
+  // 1. node rows: validity, attribute checks, (key,row) sort keys
+  unsigned st = 0u;
+  int nvalid = 0;
+  for (int i = tid; i < N2; i += T) {
+    uint64_t key = ~0ull;
+    if (i < N) {
+      const float k = gn[i * 5 + 0];
+      s_of_row[i] = -1;
+      if (k == k) {
+        ++nvalid;
+        uint32_t ku = 0xffffffffu;
+        if (is_int_in(k, 0.0f, KEY_LIMIT)) ku = uint32_t(k); else st |= NEAT_G_BAD_ATTR;
+        if (i >= I) {
+          const float b = gn[i * 5 + 1], r = gn[i * 5 + 2], a = gn[i * 5 + 3], ag = gn[i * 5 + 4];
+          if (!is_int_in(a, 0.0f, 7.0f) || !is_int_in(ag, 0.0f, 4.0f) || b != b || r != r)
+            st |= NEAT_G_BAD_ATTR;
+        }
+        key = (uint64_t(ku) << 32) | uint32_t(i);
+      } else if (i < I + O) {
+        st |= NEAT_G_IO_ROW_INVALID;
+      }
+    }
+    sk[i] = key;
+  }
+  if (st) atomicOr(&s_status, st);
+  if (nvalid) atomicAdd(&s_V, nvalid);
+  __syncthreads();
+  const int V = s_V;
+  bitonic_sort_u64(sk, N2);
+
+  // 2. sorted key table, duplicate keys
+  st = 0u;
+  for (int s = tid; s < V; s += T) {
+    const uint64_t x = sk[s];
+    const int row = int(x & 0xffffffffu);
+    key_s[s] = int(x >> 32);  // keys < 2^24 (or 0xffffffff for a bad key: genome rejected)
+    row_of_s[s] = row;
+    s_of_row[row] = s;
+    if (s > 0 && (sk[s - 1] >> 32) == (x >> 32)) st |= NEAT_G_DUP_KEY;
+    indeg[s] = 0;
+    outfill[s] = 0;
+    layer_s[s] = -1;
+    ready[s] = 0;
+  }
+  if (st) atomicOr(&s_status, st);
+  __syncthreads();
+
+  // 3. connection rows: enabled ones resolved to sorted node indices
+  st = 0u;
+  int nen = 0;
+  for (int j = tid; j < C2; j += T) {
+    uint64_t key = ~0ull;
+    if (j < C) {
+      const float4 c = reinterpret_cast<const float4 *>(gc)[j];
+      const bool valid = (c.x == c.x) && (c.y == c.y);
+      const bool enabled = valid && (c.w == c.w) && c.w != 0.0f;
+      if (enabled) {
+        int src = -1, dst = -1;
+        float kk[2] = {c.x, c.y};
+        int res[2];
+        for (int t = 0; t < 2; ++t) {
+          res[t] = -1;
+          if (is_int_in(kk[t], 0.0f, KEY_LIMIT)) {
+            const int ku = int(kk[t]);
+            int lo = 0, hi = V;
+            while (lo < hi) {
+              const int mid = (lo + hi) >> 1;
+              if (key_s[mid] < ku) lo = mid + 1; else hi = mid;
+            }
+            if (lo < V && key_s[lo] == ku) res[t] = lo;
+          }
+        }
+        src = res[0];
+        dst = res[1];
+        if (src < 0 || dst < 0) {
+          st |= NEAT_G_DANGLING_KEY;
+        } else {
+          if (row_of_s[dst] < I) st |= NEAT_G_EDGE_INTO_INPUT;
+          if (c.z != c.z) st |= NEAT_G_BAD_ATTR;
+          key = (uint64_t(dst) << 40) | (uint64_t(src) << 20) | uint64_t(j);
+          ++nen;
+        }
+      }
+    }
+    ek[j] = key;
+  }
+  if (st) atomicOr(&s_status, st);
+  if (nen) atomicAdd(&s_E, nen);
+  __syncthreads();
+  const int E = s_E;
+  bitonic_sort_u64(ek, C2);
+
+  // 4. in-degrees, incoming segments, duplicate edges, out-degree counts
+  st = 0u;
+  for (int i = tid; i < E; i += T) {
+    const uint64_t x = ek[i];
+    const int dst = int(x >> 40), src = int((x >> 20) & 0xfffffu);
+    atomicAdd(&indeg[dst], 1);
+    atomicAdd(&outfill[src], 1);
+    if (i == 0 || int(ek[i - 1] >> 40) != dst) inbeg[dst] = i;
+    if (i > 0 && (ek[i - 1] >> 20) == (x >> 20)) st |= NEAT_G_DUP_EDGE;
+  }
+  if (st) atomicOr(&s_status, st);
+  __syncthreads();
+  for (int s = tid; s < V; s += T) outbeg[s] = outfill[s];
+  __syncthreads();
+  block_exclusive_scan(outbeg, V, wbuf);
+  for (int s = tid; s < V; s += T) outfill[s] = 0;
+  __syncthreads();
+  for (int i = tid; i < E; i += T) {
+    const uint64_t x = ek[i];
+    const int dst = int(x >> 40), src = int((x >> 20) & 0xfffffu);
+    outlist[outbeg[src] + atomicAdd(&outfill[src], 1)] = dst;
+  }
+  const unsigned status0 = s_status;  // read after the previous barrier
+  __syncthreads();
+
+  // 5. Kahn by frontier.  Each round emits every ready node in ascending key
+  // (sorted index order = key order), then releases their successors.
+  int emitted = 0, t = 0;
+  if ((status0 & ~NEAT_G_CYCLE) == 0u) {
+    for (int s = tid; s < V; s += T) {
+      rem[s] = indeg[s];
+      ready[s] = indeg[s] == 0;
+    }
+    __syncthreads();
+    for (int round = 0; round <= V; ++round) {  // bounded: each round emits >= 1 node
+      for (int s = tid; s < V; s += T) tmp[s] = ready[s];
+      __syncthreads();
+      const int F = block_exclusive_scan(tmp, V, wbuf);
+      if (F == 0) break;
+      for (int s = tid; s < V; s += T)
+        if (ready[s]) {
+          const int p = emitted + tmp[s];
+          order_s[p] = s;
+          layer_s[s] = t;
+          pos_of[s] = p;
+          ready[s] = 0;
+        }
+      __syncthreads();
+      for (int p = emitted + tid; p < emitted + F; p += T) {
+        const int s = order_s[p];
+        for (int k = outbeg[s]; k < outbeg[s] + outfill[s]; ++k) {
+          const int d = outlist[k];
+          if (atomicSub(&rem[d], 1) == 1) ready[d] = 1;
+        }
+      }
+      __syncthreads();
+      emitted += F;
+      ++t;
+    }
+    if (tid == 0 && emitted < V) atomicOr(&s_status, NEAT_G_CYCLE);
+  }
+  __syncthreads();
+  const unsigned status = s_status;
+  const bool no_order = (status & ~NEAT_G_CYCLE) != 0u;
+
+  // 6. order / layer / n_layers / status outputs
+  for (int p = tid; p < N; p += T)
+    order[size_t(g) * N + p] = (!no_order && p < emitted) ? row_of_s[order_s[p]] : -1;
+  for (int r = tid; r < N; r += T) {
+    const int s = s_of_row[r];
+    layer[size_t(g) * N + r] = (!no_order && s >= 0) ? layer_s[s] : -1;
+  }
+  if (tid == 0) {
+    n_layers[g] = no_order ? 0 : t;
+    gstatus[g] = status;
+  }
+
+  // 7. padded program (valid genomes only)
+  GenomeHdr h;
+  h.V = 0; h.E = 0; h.L = 0; h.status = status; h.node_off = 0; h.edge_off = 0;
+  h.lvl_off = -1; h.pad = 0;
+  if (status == 0u) {
+    h.V = V; h.E = E; h.L = t;
+    // edge begin per position
+    for (int p = tid; p < V; p += T) tmp[p] = indeg[order_s[p]];
+    __syncthreads();
+    block_exclusive_scan(tmp, V, wbuf);
+    NodeRec *pn = w.pnode + size_t(g) * N;
+    int32_t *prow = w.prow + size_t(g) * N;
+    for (int p = tid; p < N; p += T) {
+      NodeRec rec;
+      if (p < V) {
+        const int s = order_s[p], row = row_of_s[s];
+        const float *nr = gn + row * 5;
+        uint32_t meta = uint32_t(indeg[s]) | META_VALID;
+        if (row < I) {
+          meta |= META_INPUT;
+          rec.bias = 0.0f;
+          rec.resp = 1.0f;
+        } else {
+          meta |= (uint32_t(nr[3]) << 16) | (uint32_t(nr[4]) << 20);
+          rec.bias = nr[1];
+          rec.resp = nr[2];
+        }
+        rec.in_begin = uint32_t(tmp[p]);
+        rec.meta = meta;
+        prow[p] = row;
+      } else {
+        rec.bias = 0.0f; rec.resp = 0.0f; rec.in_begin = 0u; rec.meta = 0u;
+        prow[p] = -1;
+      }
+      pn[p] = rec;
+    }
+    EdgeRec *pe = w.pedge + size_t(g) * C;
+    int32_t *per = w.perow + size_t(g) * C;
+    for (int i = tid; i < E; i += T) {
+      const uint64_t x = ek[i];
+      const int dst = int(x >> 40), src = int((x >> 20) & 0xfffffu), row = int(x & 0xfffffu);
+      const int p = pos_of[dst];
+      const int idx = tmp[p] + (i - inbeg[dst]);
+      EdgeRec er;
+      er.src = uint32_t(pos_of[src]);
+      er.w = gc[row * 4 + 2];
+      pe[idx] = er;
+      per[idx] = row;
+    }
+    int32_t *io = w.pio + size_t(g) * (I + O);
+    for (int i = tid; i < I + O; i += T) io[i] = pos_of[s_of_row[i]];
+  }
+  if (tid == 0) w.hdr[g] = h;
+}
+
+// Work-queue order: genomes by descending cost (ties: lower id first).
+// mode 0: cost = E + 2V (sample-parallel forward); mode 1: layers first, then E.
+__device__ __forceinline__ uint64_t cost_key(const GenomeHdr &h, int mode, int g) {
+  uint32_t cost;
+  if (h.status != 0u) cost = 0u;
+  else if (mode == 0) cost = uint32_t(h.E + 2 * h.V + 1);
+  else cost = (uint32_t(h.L) << 16) | uint32_t(min(h.E, 0xffff));
+  return (uint64_t(cost) << 32) | uint64_t(0xffffffffu - uint32_t(g));
+}
+
+__global__ void __launch_bounds__(256) k_rank(Ws w, int mode) {
+  __shared__ uint64_t tile[256];
+  const int P = w.P;
+  const int g = blockIdx.x * 256 + threadIdx.x;
+  const uint64_t kg = g < P ? cost_key(w.hdr[g], mode, g) : 0ull;
+  int rank = 0;
+  for (int base = 0; base < P; base += 256) {
+    const int h = base + threadIdx.x;
+    tile[threadIdx.x] = h < P ? cost_key(w.hdr[h], mode, h) : 0ull;
+    __syncthreads();
+    const int lim = min(256, P - base);
+    for (int k = 0; k < lim; ++k) rank += tile[k] > kg;
+    __syncthreads();
+  }
+  if (g < P) w.qorder[rank] = g;
+}
+
+// Exclusive scans of V and E in queue order -> ragged offsets (one CTA).
+__global__ void __launch_bounds__(1024) k_offsets(Ws w) {
+  __shared__ int wv[33], we[33];
+  const int P = w.P, T = blockDim.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int per = (P + T - 1) / T;
+  const int b = min(tid * per, P), e = min(b + per, P);
+  int sv = 0, se = 0;
+  for (int q = b; q < e; ++q) {
+    const GenomeHdr h = w.hdr[w.qorder[q]];
+    sv += h.V;
+    se += h.E;
+  }
+  int xv = sv, xe = se;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int yv = __shfl_up_sync(0xffffffffu, xv, d), ye = __shfl_up_sync(0xffffffffu, xe, d);
+    if (lane >= d) { xv += yv; xe += ye; }
+  }
+  if (lane == 31) { wv[wid] = xv; we[wid] = xe; }
+  __syncthreads();
+  if (wid == 0) {
+    int a = wv[lane], c = we[lane];
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int ya = __shfl_up_sync(0xffffffffu, a, d), yc = __shfl_up_sync(0xffffffffu, c, d);
+      if (lane >= d) { a += ya; c += yc; }
+    }
+    wv[lane] = a;
+    we[lane] = c;
+  }
+  __syncthreads();
+  int ov = (wid > 0 ? wv[wid - 1] : 0) + xv - sv;
+  int oe = (wid > 0 ? we[wid - 1] : 0) + xe - se;
+  for (int q = b; q < e; ++q) {
+    const int g = w.qorder[q];
+    GenomeHdr h = w.hdr[g];
+    h.node_off = ov;
+    h.edge_off = oe;
+    ov += h.V;
+    oe += h.E;
+    w.hdr[g] = h;
+  }
+}
+
+// Copy the padded programs into the ragged-packed arena.
+__global__ void __launch_bounds__(128) k_pack(Ws w) {
+  const int g = blockIdx.x;
+  const GenomeHdr h = w.hdr[g];
+  const NodeRec *pn = w.pnode + size_t(g) * w.N;
+  const EdgeRec *pe = w.pedge + size_t(g) * w.C;
+  const int32_t *per = w.perow + size_t(g) * w.C;
+  for (int p = threadIdx.x; p < h.V; p += blockDim.x) w.knode[h.node_off + p] = pn[p];
+  for (int i = threadIdx.x; i < h.E; i += blockDim.x) {
+    w.kedge[h.edge_off + i] = pe[i];
+    w.kerow[h.edge_off + i] = per[i];
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_transform(const Ws &w, const float *nodes, const float *conns, int32_t *order,
+                             int32_t *layer, int32_t *n_layers, uint32_t *gstatus,
+                             cudaStream_t st) {
+  if (w.P == 0) return cudaSuccess;
+  const TSmem L = tsmem_layout(w.N, w.C);
+  const int threads = w.N + w.C <= 384 ? 128 : 256;
+  k_transform<<<w.P, threads, L.total, st>>>(w, nodes, conns, order, layer, n_layers, gstatus);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_queue_build(const Ws &w, int mode, cudaStream_t st) {
+  if (w.P == 0) return cudaSuccess;
+  k_rank<<<(w.P + 255) / 256, 256, 0, st>>>(w, mode);
+  k_offsets<<<1, 1024, 0, st>>>(w);
+  k_pack<<<w.P, 128, 0, st>>>(w);
+  return cudaGetLastError();
+}
+
+}  // namespace neat
+
+namespace neat {
+cudaError_t transform_set_smem_limit(int bytes) {
+  return set_dyn_smem_limit(k_transform, bytes);
+}
+size_t transform_smem(int N, int C) { return size_t(tsmem_layout(N, C).total); }
+}  // namespace neat

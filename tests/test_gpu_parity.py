@@ -1,0 +1,399 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs.  Orders, layers and status bits must be bit-exact; outputs
+and gradients within the tolerances of parity_util."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from genome_builders import load_xor, stack
+from parity_util import compare_grads, compare_outputs
+from workloads import (CONFIGS, locomotion_inputs, population_for, regression_batch,
+                       uneven_inputs, xor_inputs)
+
+pytestmark = pytest.mark.gpu
+
+
+def _plan(spec, P):
+    from paper_2504_08339_b300.api import Plan
+    return Plan(P, spec.N, spec.C, spec.I, spec.O)
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _transform_both(nodes, conns, spec):
+    P = nodes.shape[0]
+    plan = _plan(spec, P)
+    tr = plan.transform(_dev(nodes), _dev(conns))
+    torch.cuda.synchronize()
+    ref = oracle.transform(nodes, conns, spec.I, spec.O)
+    return plan, tr, ref
+
+
+def _assert_transform_equal(tr, ref):
+    o, l, nl, st = ref
+    np.testing.assert_array_equal(tr.order.cpu().numpy(), o)
+    np.testing.assert_array_equal(tr.layer.cpu().numpy(), l)
+    np.testing.assert_array_equal(tr.n_layers.cpu().numpy(), nl)
+    np.testing.assert_array_equal(tr.status.cpu().numpy().astype(np.uint32), st)
+
+
+SIZES = {"tiny": 100, "locomotion": 3000, "uneven": 600, "differentiation": 2048, "hyperneat": 256}
+
+
+@pytest.mark.parametrize("name", list(SIZES))
+def test_transform_bit_exact(name):
+    nodes, conns, spec = population_for(name, seed=1, P=SIZES[name])
+    plan, tr, ref = _transform_both(nodes, conns, spec)
+    _assert_transform_equal(tr, ref)
+    assert (ref[3] == 0).all()
+
+
+def _malformed_population():
+    d, n, c = load_xor()
+    variants = []
+
+    def v(f):
+        nn, cc = n.copy(), c.copy()
+        f(nn, cc)
+        variants.append((nn, cc))
+
+    v(lambda n, c: None)
+    v(lambda n, c: c.__setitem__(3, (3, 7, 1.0, 1)))            # cycle
+    v(lambda n, c: c.__setitem__(3, (7, 7, 1.0, 1)))            # self loop
+    v(lambda n, c: c.__setitem__(3, (99, 3, 1.0, 1)))           # dangling
+    v(lambda n, c: c.__setitem__(3, (0.5, 3, 1.0, 1)))          # non-integral conn key
+    v(lambda n, c: n.__setitem__(6, (5, 0, 1, 1, 0)))           # duplicate key
+    v(lambda n, c: c.__setitem__(3, (0, 7, 2.0, 1)))            # duplicate edge
+    v(lambda n, c: c.__setitem__(3, (7, 0, 1.0, 1)))            # edge into input
+    v(lambda n, c: n.__setitem__((4, 3), 9))                    # act id
+    v(lambda n, c: n.__setitem__((4, 4), 1.5))                  # agg id
+    v(lambda n, c: n.__setitem__((4, 1), np.nan))               # NaN bias
+    v(lambda n, c: c.__setitem__((0, 2), np.nan))               # NaN weight enabled
+    v(lambda n, c: c.__setitem__((10, 2), np.nan))              # NaN weight disabled: fine
+    v(lambda n, c: n.__setitem__(6, (2.0 ** 24, 0, 1, 1, 0)))   # key range
+    v(lambda n, c: n.__setitem__(6, (-3, 0, 1, 1, 0)))
+    v(lambda n, c: n.__setitem__((3, 0), np.nan))               # output row padding
+    v(lambda n, c: n.__setitem__((0, 3), 99))                   # input attrs ignored
+    v(lambda n, c: c.__setitem__(3, (np.nan, 3, 5.0, 1)))       # half-NaN row = padding
+    v(lambda n, c: c.__setitem__((10, 3), np.nan))              # NaN enabled = disabled
+    return stack(variants), d
+
+
+def test_transform_and_forward_malformed_genomes():
+    (nodes, conns), d = _malformed_population()
+    spec = CONFIGS["tiny"]["spec"]
+    from paper_2504_08339_b300.api import Plan
+    P = nodes.shape[0]
+    plan = Plan(P, nodes.shape[1], conns.shape[1], 3, 1)
+    tr = plan.transform(_dev(nodes), _dev(conns))
+    ref = oracle.transform(nodes, conns, 3, 1)
+    _assert_transform_equal(tr, ref)
+    assert (ref[3] != 0).sum() >= 12
+    x = xor_inputs()
+    out = plan.forward(_dev(x)).cpu().numpy()
+    r = oracle.forward(nodes, conns, x, 3, 1)
+    compare_outputs(out, r)
+    plain = plan.forward(_dev(x), plain=True).cpu().numpy()
+    compare_outputs(plain, r)
+    del spec
+
+
+def _fwd_case(name, P, S, seed=2):
+    nodes, conns, spec = population_for(name, seed=seed, P=P)
+    rng = np.random.default_rng(seed)
+    if name == "tiny":
+        x = xor_inputs()
+    elif name == "differentiation":
+        x = regression_batch(seed, S)[0]
+    else:
+        x = rng.standard_normal((P, S, spec.I), dtype=np.float32)
+    return nodes, conns, spec, x
+
+
+@pytest.mark.parametrize("name,P,S", [
+    ("tiny", 100, 4),
+    ("locomotion", 1000, 1),
+    ("locomotion", 400, 37),
+    ("uneven", 300, 64),
+    ("differentiation", 256, 100),
+    ("hyperneat", 128, 33),
+])
+@pytest.mark.parametrize("plain", [False, True])
+def test_forward_parity(name, P, S, plain):
+    nodes, conns, spec, x = _fwd_case(name, P, S)
+    plan = _plan(spec, P)
+    plan.transform(_dev(nodes), _dev(conns))
+    out = plan.forward(_dev(x), plain=plain).cpu().numpy()
+    ref, bnd = oracle.forward(nodes, conns, x, spec.I, spec.O, with_bound=True)
+    stats = compare_outputs(out, ref, bnd)
+    if name in ("tiny", "differentiation"):
+        # well-conditioned populations: inside the plain tolerance everywhere
+        assert stats["ill_conditioned"] == 0, stats
+
+
+def test_forward_saved_aggregates_match_oracle_values():
+    nodes, conns, spec, x = _fwd_case("differentiation", 64, 45)
+    plan = _plan(spec, 64)
+    tr = plan.transform(_dev(nodes), _dev(conns))
+    saved = torch.empty((64, 45, spec.N), device="cuda")
+    out = plan.forward(_dev(x), saved=saved)
+    out2 = plan.forward(_dev(x))
+    assert torch.equal(out, out2)
+    # the saved aggregate a at position p gives v = act(b + r a); check it on outputs
+    order = tr.order.cpu().numpy()
+    _, vals = oracle.forward(nodes, conns, x, spec.I, spec.O, with_values=True)
+    sv = saved.cpu().numpy()
+    for g in range(64):
+        pos_out = int(np.flatnonzero(order[g] == spec.I)[0])      # output row I
+        a = sv[g, :, pos_out].astype(np.float64)
+        b, r = float(nodes[g, spec.I, 1]), float(nodes[g, spec.I, 2])
+        np.testing.assert_allclose(b + r * a, vals[g, :, spec.I], rtol=1e-4, atol=1e-5)
+
+
+def test_locomotion_full_population_sampled_steps():
+    """The full 10,000-genome locomotion population, in the launch shape of the
+    rollout (S = 1 per step); a sample of steps and all genomes vs the oracle."""
+    name = "locomotion"
+    nodes, conns, spec = population_for(name, seed=0)
+    P = nodes.shape[0]
+    plan = _plan(spec, P)
+    tr = plan.transform(_dev(nodes), _dev(conns))
+    ref_t = oracle.transform(nodes, conns, spec.I, spec.O)
+    _assert_transform_equal(tr, ref_t)
+    for step in (0, 1, 517, 999):
+        x = locomotion_inputs(0, step, P, spec.I)
+        out = plan.forward(_dev(x)).cpu().numpy()
+        ref, bnd = oracle.forward(nodes, conns, x, spec.I, spec.O, with_bound=True)
+        compare_outputs(out, ref, bnd, what=f"step {step}")
+
+
+def test_uneven_full_population_sampled_genomes():
+    """The full 16,384-genome uneven population: transform bit-exact on every
+    genome; forward on one step checked on a 400-genome sample."""
+    nodes, conns, spec = population_for("uneven", seed=0)
+    P = nodes.shape[0]
+    plan = _plan(spec, P)
+    tr = plan.transform(_dev(nodes), _dev(conns))
+    ref_t = oracle.transform(nodes, conns, spec.I, spec.O)
+    _assert_transform_equal(tr, ref_t)
+    x = uneven_inputs(0, 3, P)
+    out = plan.forward(_dev(x)).cpu().numpy()
+    sel = np.random.default_rng(0).choice(P, 400, replace=False)
+    ref, bnd = oracle.forward(nodes[sel], conns[sel], x[sel], spec.I, spec.O, with_bound=True)
+    compare_outputs(out[sel], ref, bnd)
+
+
+@pytest.mark.parametrize("stored", [True, False])
+@pytest.mark.parametrize("name,P,S", [("differentiation", 96, 77), ("locomotion", 48, 40),
+                                      ("hyperneat", 32, 20)])
+def test_backward_parity(name, P, S, stored):
+    nodes, conns, spec, x = _fwd_case(name, P, S, seed=5)
+    plan = _plan(spec, P)
+    plan.transform(_dev(nodes), _dev(conns))
+    xd = _dev(x)
+    saved = None
+    if stored:
+        saved = torch.empty((P, S, spec.N), device="cuda")
+        plan.forward(xd, saved=saved)
+    go = np.random.default_rng(9).standard_normal((P, S, spec.O)).astype(np.float32)
+    gw, gb, gr, gi = plan.backward(xd, _dev(go), saved=saved)
+    rw, rb, rr, ri = oracle.backward(nodes, conns, x, spec.I, spec.O, go)
+    compare_grads(gw.cpu().numpy(), rw, "grad_weight")
+    compare_grads(gb.cpu().numpy(), rb, "grad_bias")
+    compare_grads(gr.cpu().numpy(), rr, "grad_response")
+    compare_grads(gi.cpu().numpy(), ri, "grad_inputs")
+
+
+def test_backward_and_forward_are_deterministic():
+    nodes, conns, spec, x = _fwd_case("differentiation", 128, 300, seed=3)
+    plan = _plan(spec, 128)
+    plan.transform(_dev(nodes), _dev(conns))
+    xd = _dev(x)
+    go = _dev(np.random.default_rng(1).standard_normal((128, 300, 1)).astype(np.float32))
+    a = plan.forward(xd)
+    b = plan.forward(xd)
+    assert torch.equal(a, b)
+    g1 = plan.backward(xd, go)
+    g2 = plan.backward(xd, go)
+    for u, v in zip(g1, g2):
+        assert torch.equal(u, v)
+
+
+def test_autograd_function_matches_oracle():
+    from paper_2504_08339_b300.api import evaluate
+    nodes, conns, spec, x = _fwd_case("differentiation", 40, 64, seed=4)
+    plan = _plan(spec, 40)
+    n = _dev(nodes).requires_grad_(True)
+    c = _dev(conns).requires_grad_(True)
+    xi = _dev(x).requires_grad_(True)
+    y = _dev(regression_batch(4, 64)[1])
+    for store in (True, False):
+        out = evaluate(plan, n, c, xi, store)
+        loss = ((out[..., 0] - y) ** 2).mean(dim=1).sum()
+        gn, gc, gx = torch.autograd.grad(loss, (n, c, xi))
+        ref = oracle.forward(nodes, conns, x, spec.I, spec.O)
+        gout = (2.0 / 64) * (ref[..., 0] - y.cpu().numpy()[None].astype(np.float64))
+        rw, rb, rr, ri = oracle.backward(nodes, conns, x, spec.I, spec.O, gout[..., None])
+        compare_grads(gc[..., 2].cpu().numpy(), rw, "w")
+        compare_grads(gn[..., 1].cpu().numpy(), rb, "b")
+        compare_grads(gn[..., 2].cpu().numpy(), rr, "r")
+        compare_grads(gx.cpu().numpy(), ri.sum(0, keepdims=True), "x")
+        assert torch.count_nonzero(gn[..., 0]) == 0 and torch.count_nonzero(gc[..., 3]) == 0
+
+
+def test_hyperneat_full_grid_small():
+    nodes, conns, spec = population_for("hyperneat", seed=6, P=12)
+    plan = _plan(spec, 12)
+    plan.transform(_dev(nodes), _dev(conns))
+    G = 12
+    out = plan.hyperneat(grid=G, thresh=0.2).cpu().numpy().reshape(12, -1)
+    ref, raw, bnd = oracle.hyperneat(nodes, conns, grid=G, thresh=0.2, with_raw=True,
+                                     with_bound=True)
+    _check_threshold(out, ref, raw, bnd)
+
+
+def _check_threshold(out, ref, raw, bnd):
+    # the threshold decision is unique only away from |o| = thresh; near it
+    # either 0 or the raw value is correct
+    lim = np.maximum(1e-6 + 1e-5 * np.abs(raw), 2 * bnd)
+    near = np.abs(np.abs(raw) - 0.2) <= lim
+    compare_outputs(out[~near], ref[~near], None if bnd is None else bnd[~near])
+    ok = (out[near] == 0) | (np.abs(out[near] - raw[near]) <= lim[near])
+    assert ok.all()
+
+
+def test_hyperneat_full_size_sampled():
+    """All 256 CPPNs on the 32x32 substrate (268M queries, 1 GiB of weights);
+    every query of 4 genomes and a 1% sample of 8 more are checked."""
+    nodes, conns, spec = population_for("hyperneat", seed=0)
+    P = nodes.shape[0]
+    plan = _plan(spec, P)
+    plan.transform(_dev(nodes), _dev(conns))
+    out = plan.hyperneat(grid=32, thresh=0.2).view(P, -1)
+    rng = np.random.default_rng(0)
+    full = rng.choice(P, 4, replace=False)
+    got = out[torch.from_numpy(full).cuda()].cpu().numpy()
+    ref, raw, bnd = oracle.hyperneat(nodes[full], conns[full], grid=32, with_raw=True,
+                                     with_bound=True)
+    _check_threshold(got, ref, raw, bnd)
+    samp = rng.choice(np.setdiff1d(np.arange(P), full), 8, replace=False)
+    q = rng.choice(32 ** 4, 32 ** 4 // 100, replace=False)
+    got = out[torch.from_numpy(samp).cuda()][:, torch.from_numpy(q).cuda()].cpu().numpy()
+    ref, raw, bnd = oracle.hyperneat(nodes[samp], conns[samp], grid=32, qidx=q, with_raw=True,
+                                     with_bound=True)
+    _check_threshold(got, ref, raw, bnd)
+
+
+def test_edge_cases():
+    from paper_2504_08339_b300.api import Plan
+    spec = CONFIGS["differentiation"]["spec"]
+    # zero genomes, zero samples
+    plan = Plan(0, spec.N, spec.C, spec.I, spec.O)
+    e = torch.empty((0, spec.N, 5), device="cuda")
+    tr = plan.transform(e, torch.empty((0, spec.C, 4), device="cuda"))
+    assert tr.order.shape == (0, spec.N)
+    nodes, conns, spec = population_for("differentiation", seed=7, P=5)
+    plan = _plan(spec, 5)
+    plan.transform(_dev(nodes), _dev(conns))
+    out = plan.forward(torch.empty((5, 0, spec.I), device="cuda"))
+    assert out.shape == (5, 0, 1)
+    # shared inputs equal broadcast inputs
+    x = regression_batch(0, 50)[0]
+    a = plan.forward(_dev(x))
+    b = plan.forward(_dev(np.repeat(x, 5, 0)))
+    assert torch.equal(a, b)
+    # genome without any connection and hidden nodes: outputs are act(b) constants
+    n = np.full((1, spec.N, 5), np.nan, np.float32)
+    c = np.full((1, spec.C, 4), np.nan, np.float32)
+    for r in range(spec.I):
+        n[0, r] = (r, 0, 1, 0, 0)
+    n[0, spec.I] = (spec.I, 0.3, 1.0, 2, 0)
+    p1 = _plan(spec, 1)
+    p1.transform(_dev(n), _dev(c))
+    o = p1.forward(_dev(x)).cpu().numpy()
+    compare_outputs(o, oracle.forward(n, c, x, spec.I, spec.O))
+
+
+def test_maximum_sizes():
+    """N = 1024 node rows, C = 8192 connection rows (the library maxima)."""
+    from workloads import GenomeSpec, make_population
+    spec = GenomeSpec(I=9, O=3, N=1024, C=8192, V_loguniform=(700, 1024),
+                      E_loguniform=(6000, 8192), acts=("tanh", "sigmoid", "sin"),
+                      aggs=("sum", "mean", "max"), w_std=1.0, b_std=0.5)
+    nodes, conns = make_population(spec, 6, seed=11)
+    plan, tr, ref = _transform_both(nodes, conns, spec)
+    _assert_transform_equal(tr, ref)
+    x = np.random.default_rng(0).standard_normal((6, 40, 9)).astype(np.float32)
+    out = plan.forward(_dev(x)).cpu().numpy()
+    r, bnd = oracle.forward(nodes, conns, x, 9, 3, with_bound=True)
+    compare_outputs(out, r, bnd)
+
+
+def test_abi_argument_errors():
+    import ctypes
+    from paper_2504_08339_b300 import _lib
+    lib = _lib.load()
+    assert lib.neat_workspace_bytes(10, 3, 4, 2, 2) == 0           # N < I + O
+    assert lib.neat_workspace_bytes(10, 1025, 4, 2, 2) == 0        # N too large
+    h = ctypes.c_void_p()
+    nb = lib.neat_workspace_bytes(4, 16, 32, 3, 1)
+    ws = torch.empty(nb + 512, dtype=torch.uint8, device="cuda")
+    base = (ws.data_ptr() + 255) // 256 * 256
+    assert lib.neat_plan_create(ctypes.byref(h), 4, 16, 32, 3, 1, ctypes.c_void_p(base + 16),
+                                nb) == _lib.NEAT_ERR_ARG
+    assert lib.neat_plan_create(ctypes.byref(h), 4, 16, 32, 3, 1, ctypes.c_void_p(base),
+                                nb - 1) == _lib.NEAT_ERR_WORKSPACE
+    assert lib.neat_plan_create(ctypes.byref(h), 4, 16, 32, 3, 1, ctypes.c_void_p(base),
+                                nb) == _lib.NEAT_OK
+    x = torch.zeros((4, 2, 3), device="cuda")
+    out = torch.zeros((4, 2, 1), device="cuda")
+    s = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert lib.neat_forward(h, ctypes.c_void_p(x.data_ptr()), 6, 2,
+                            ctypes.c_void_p(out.data_ptr()), None, s) == _lib.NEAT_ERR_STATE
+    nodes = torch.full((4, 16, 5), float("nan"), device="cuda")
+    conns = torch.full((4, 32, 4), float("nan"), device="cuda")
+    i32 = [torch.zeros(64, dtype=torch.int32, device="cuda") for _ in range(4)]
+    assert lib.neat_transform(h, ctypes.c_void_p(nodes.data_ptr()),
+                              ctypes.c_void_p(conns.data_ptr() + 4), *[
+                                  ctypes.c_void_p(t.data_ptr()) for t in i32], s) == _lib.NEAT_ERR_ARG
+    assert lib.neat_transform(h, ctypes.c_void_p(nodes.data_ptr()),
+                              ctypes.c_void_p(conns.data_ptr()), *[
+                                  ctypes.c_void_p(t.data_ptr()) for t in i32], s) == _lib.NEAT_OK
+    assert lib.neat_forward(h, ctypes.c_void_p(x.data_ptr()), 5, 2,
+                            ctypes.c_void_p(out.data_ptr()), None, s) == _lib.NEAT_ERR_ARG
+    assert lib.neat_forward(h, ctypes.c_void_p(x.data_ptr() + 2), 6, 2,
+                            ctypes.c_void_p(out.data_ptr()), None, s) == _lib.NEAT_ERR_ARG
+    assert lib.neat_hyperneat_query(h, 32, 0.2, ctypes.c_void_p(out.data_ptr()), s) == \
+        _lib.NEAT_ERR_UNSUPPORTED
+    torch.cuda.synchronize()
+    # every genome was all-padding: IO rows invalid
+    st = i32[3][:4].cpu().numpy()
+    assert (st == 64).all()
+    lib.neat_plan_destroy(h)
+
+
+def test_cuda_graph_replay_matches_direct_calls():
+    nodes, conns, spec = population_for("locomotion", seed=2, P=500)
+    plan = _plan(spec, 500)
+    plan.transform(_dev(nodes), _dev(conns))
+    T = 7
+    xs = _dev(np.stack([locomotion_inputs(2, t, 500) for t in range(T)]))
+    outs = torch.empty((T, 500, 1, spec.O), device="cuda")
+    direct = torch.stack([plan.forward(xs[t]) for t in range(T)])
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        plan.forward(xs[0], out=outs[0])       # warm-up on the capture stream
+    torch.cuda.current_stream().wait_stream(s)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        for t in range(T):
+            plan.forward(xs[t], out=outs[t])
+    for _ in range(3):
+        outs.zero_()
+        graph.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(outs, direct)
