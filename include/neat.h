@@ -119,12 +119,16 @@ neat_status neat_plan_destroy(neat_plan *plan);
 /* Tuning knobs picked by the autotuner (0 = library default).
  *   warps_per_cta    warps of a sample-parallel CTA (1..16)
  *   samples_per_lane samples one lane evaluates in the sample-parallel forward (1, 2, 4)
- *   genomes_per_batch genomes packed into one CTA by the small-sample forward (1..64)
- *   small_s_max      largest S that uses the small-sample (level-synchronous) forward */
+ *   lvl_threads      threads of a level-synchronous (small-sample) CTA: 32..256,
+ *                    a multiple of 32
+ *   small_s_max      largest S that uses the level-synchronous forward (1..64,
+ *                    -1 = never; default 8); larger S, calls that ask for the
+ *                    saved aggregates, and batches that do not fit in shared
+ *                    memory use the sample-parallel forward */
 typedef struct {
   int warps_per_cta;
   int samples_per_lane;
-  int genomes_per_batch;
+  int lvl_threads;
   int small_s_max;
 } neat_tuning;
 neat_status neat_plan_set_tuning(neat_plan *plan, const neat_tuning *t);

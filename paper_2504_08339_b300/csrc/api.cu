@@ -56,6 +56,16 @@ int sp_warps(const neat_plan *p) {
   return w;
 }
 
+int lvl_threads(const neat_plan *p) { return p->tune.lvl_threads > 0 ? p->tune.lvl_threads : 256; }
+
+int small_s_max(const neat_plan *p) {
+  return p->tune.small_s_max != 0 ? p->tune.small_s_max : 8;  // -1: never
+}
+
+bool lvl_fits(const neat_plan *p, int S) {
+  return neat::forward_lvl_smem(p->w, neat::lvl_tile(S)) <= size_t(p->smem_optin);
+}
+
 int backward_warps(const neat_plan *p) {
   int w = 8;
   while (w > 1 && neat::backward_smem(p->N, p->C, w) > size_t(200 * 1024)) --w;
@@ -121,6 +131,7 @@ neat_status neat_plan_create(neat_plan **out, int P, int N, int C, int I, int O,
   if (e == cudaSuccess) e = neat::transform_set_smem_limit(p->smem_optin);
   if (e == cudaSuccess) e = neat::forward_set_smem_limit(p->smem_optin);
   if (e == cudaSuccess) e = neat::backward_set_smem_limit(p->smem_optin);
+  if (e == cudaSuccess) e = neat::lvl_set_smem_limit(p->smem_optin);
   // zero the headers and queue counters so a plan is in a defined state
   if (e == cudaSuccess) e = cudaMemset(static_cast<char *>(workspace) + L.hdr, 0,
                                        sizeof(neat::GenomeHdr) * size_t(P));
@@ -147,8 +158,9 @@ neat_status neat_plan_set_tuning(neat_plan *plan, const neat_tuning *t) {
   if (!(t->samples_per_lane == 0 || t->samples_per_lane == 1 || t->samples_per_lane == 2 ||
         t->samples_per_lane == 4))
     return NEAT_ERR_ARG;
-  if (t->genomes_per_batch < 0 || t->genomes_per_batch > 64) return NEAT_ERR_ARG;
-  if (t->small_s_max < 0) return NEAT_ERR_ARG;
+  if (t->lvl_threads < 0 || t->lvl_threads > 256 || (t->lvl_threads % 32) != 0)
+    return NEAT_ERR_ARG;
+  if (t->small_s_max < -1 || t->small_s_max > 64) return NEAT_ERR_ARG;
   plan->tune = *t;
   return NEAT_OK;
 }
@@ -158,6 +170,8 @@ neat_status neat_plan_get_tuning(const neat_plan *plan, neat_tuning *t) {
   *t = plan->tune;
   if (t->warps_per_cta == 0) t->warps_per_cta = sp_warps(plan);
   if (t->samples_per_lane == 0) t->samples_per_lane = 1;
+  if (t->lvl_threads == 0) t->lvl_threads = lvl_threads(plan);
+  if (t->small_s_max == 0) t->small_s_max = small_s_max(plan);
   return NEAT_OK;
 }
 
@@ -176,6 +190,7 @@ neat_status neat_transform(neat_plan *plan, const float *nodes, const float *con
   cudaError_t e = neat::launch_transform(plan->w, nodes, conns, order, layer, n_layers, gstatus,
                                          stream);
   if (e == cudaSuccess) e = neat::launch_queue_build(plan->w, 0, stream);
+  if (e == cudaSuccess) e = neat::launch_lvl_build(plan->w, stream);
   if (e != cudaSuccess) return cuda_status(e);
   plan->transformed = 1;
   return NEAT_OK;
@@ -190,6 +205,16 @@ neat_status neat_forward(neat_plan *plan, const float *inputs, int64_t in_pop_st
   if (S == 0 || plan->P == 0) return NEAT_OK;
   if (outputs == nullptr || !aligned(outputs, 4) || (saved && !aligned(saved, 4)))
     return NEAT_ERR_ARG;
+  if (saved == nullptr && S <= small_s_max(plan) && lvl_fits(plan, S)) {
+    // few samples per genome: level-synchronous batches of genomes
+    const int threads = lvl_threads(plan);
+    const int st = neat::lvl_tile(S);
+    const size_t smem = neat::forward_lvl_smem(plan->w, st);
+    const int occ = std::max(1, neat::forward_lvl_occupancy(threads, smem, st));
+    const int grid = std::max(1, std::min(plan->sm_count * occ, plan->w.lvl_max_batches));
+    return cuda_status(neat::launch_forward_lvl(plan->w, inputs, in_pop_stride, S, outputs,
+                                                threads, grid, stream));
+  }
   const int warps = sp_warps(plan);
   const size_t smem = neat::forward_sp_smem(plan->N, warps);
   const int occ = std::max(1, neat::forward_sp_occupancy(warps, smem));

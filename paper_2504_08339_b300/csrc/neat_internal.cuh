@@ -45,36 +45,100 @@ struct __align__(16) GenomeHdr {
   uint32_t status;
   int node_off;  // ragged-packed offsets (queue order)
   int edge_off;
-  int lvl_off;   // level-synchronous schedule (small-S form): batch of this genome
+  int lvl_off;   // unused (reserved)
+  int nch;       // 4-edge chunks of the level-synchronous form: sum of ceil(indeg/4)
+};
+
+// -- level-synchronous batches (small-S form) --------------------------------------
+// Consecutive genomes of a layer-sorted queue are packed into batches.  A batch
+// program lives in the level arena as one contiguous, 16-byte aligned block:
+//   BatchHead (48 B)
+//   gio       int32[n_genomes*(1+I+O)] genome id, input slots, output slots
+//   rounds    int2[n_rounds + 1]       (first task, first chunk) of each round
+//   --- off_task: the head part above is staged first, the rest after it
+//   tasks     TaskRec[n_tasks]         non-input nodes, by (layer, act, -cnt)
+//   eslot     uint16[4 * n_chunks]     source value slot of each edge (0xffff: pad)
+//   ew        float[4 * n_chunks]      weight of each edge
+// Every task's incoming edges are padded to whole 4-edge chunks.  A round
+// holds tasks of one layer only and at most LVL_PCAP chunks (a layer may span
+// several rounds).  Value slot of position p of the k-th genome of the batch
+// = slot_base(k) + p.
+struct __align__(16) BatchHead {
+  int n_genomes, n_slots, n_rounds, n_tasks;
+  int n_chunks, off_round, off_task, off_eslot;
+  int off_gio, prog_bytes, off_ew, pad;
+};
+constexpr int LVL_PCAP = 256;  // chunks per round (>= the chunks of any one node)
+// where a batch program sits in the arena
+struct __align__(16) BatchLoc {
+  int off;    // byte offset in the arena
+  int bytes;  // program bytes (multiple of 16)
+  int head;   // bytes of the head part (= off_task, multiple of 16)
   int pad;
 };
 
-// -- level-synchronous batch header (small-S form) -------------------------------
-struct __align__(16) BatchHdr {
-  int n_genomes;   // genomes in the batch
-  int n_slots;     // node-value slots used by the batch
-  int n_rounds;    // level rounds
-  int n_tasks;     // node tasks over all rounds
-  int n_edges;     // edge records over all tasks
-  int prog_off;    // byte offset of the batch program in the schedule arena
-  int prog_bytes;  // bytes of the batch program (multiple of 16)
-  int first_q;     // queue index of the batch's first genome
-};
-
-// Task record of the level-synchronous form (16 B).
+// Task record (16 B).  meta: [0,14) in-degree, [14,17) activation,
+// [17,19) aggregation, [19,31) destination slot.
 struct __align__(16) TaskRec {
   float bias;
   float resp;
-  uint32_t ebeg;   // first edge (batch-relative)
-  uint32_t meta;   // cnt | act << 16 | agg << 20 | dst slot << ... (see below)
+  uint32_t chunk;  // first 4-edge chunk, batch-relative
+  uint32_t meta;
 };
-// TaskRec.meta: [0,12) count, [12,16) act, [16,20) agg ... slot stored apart.
+constexpr int LVL_SLOT_BITS = 12;
+constexpr int LVL_MAX_SLOTS = 1 << LVL_SLOT_BITS;  // 4096 value slots per batch
+constexpr int LVL_MAX_GENOMES = 64;                // genomes per batch (hard cap)
+constexpr int LVL_GENOME_BUDGET = 48;
+// value slots a batch may fill before its last genome (a batch then holds
+// fewer than slot_budget + N slots)
+__host__ __device__ inline int lvl_slot_budget(int N) { return N <= 256 ? 1024 : 3072; }
+__host__ __device__ inline uint32_t task_meta(int cnt, int act, int agg, int slot) {
+  return uint32_t(cnt) | (uint32_t(act) << 14) | (uint32_t(agg) << 17) | (uint32_t(slot) << 19);
+}
+__host__ __device__ inline int task_cnt(uint32_t m) { return int(m & 0x3fffu); }
+__host__ __device__ inline int task_act(uint32_t m) { return int((m >> 14) & 7u); }
+__host__ __device__ inline int task_agg(uint32_t m) { return int((m >> 17) & 3u); }
+__host__ __device__ inline int task_slot(uint32_t m) { return int(m >> 19); }
+
+// Bytes a genome contributes to a batch program (upper bound incl. alignment):
+// task records, padded edges (24 B per chunk), I/O slots, and round-table
+// entries (one per layer plus one per task, bounding the chunk-cap splits).
+__host__ __device__ inline int lvl_genome_bytes(int V, int nch, int L, int I, int O, bool ok) {
+  const int tasks = ok ? (V - I) : 0;
+  const int b = 24 * tasks + 24 * (ok ? nch : 0) + 4 * (1 + I + O) + 8 * ((ok ? L : 0) + 2) + 160;
+  return (b + 15) & ~15;
+}
+// largest chunk count of a genome with N node rows and C connection rows
+inline int lvl_max_chunks(int N, int C) { return C / 4 + N; }
+// Batch-assignment weight: program bytes, or the genome's share of the slot /
+// genome-count budgets, whichever is larger (all scaled to bytes).
+__host__ __device__ inline int lvl_genome_weight(int pb, int V, int budget, int slot_budget) {
+  const int ws = int((long long)V * budget / slot_budget);
+  const int wg = budget / LVL_GENOME_BUDGET;
+  const int m = ws > wg ? ws : wg;
+  return pb > m ? pb : m;
+}
+// Byte budget of a batch (a batch holds the genomes whose weight prefix falls
+// in [b * budget, (b+1) * budget), so its program is < budget + max weight).
+inline int lvl_pb_max(int N, int C, int I, int O) {
+  return lvl_genome_bytes(N, lvl_max_chunks(N, C), N, I, O, true);
+}
+inline int lvl_budget(int N, int C, int I, int O) {
+  const int pbmax = lvl_pb_max(N, C, I, O);
+  int b = 32 * 1024;
+  while (b < 2 * pbmax && b < 96 * 1024) b *= 2;
+  return b;
+}
+inline int lvl_max_weight(int N, int C, int I, int O, int budget) {
+  return lvl_genome_weight(lvl_pb_max(N, C, I, O), N, budget, lvl_slot_budget(N));
+}
 
 // -- workspace layout ------------------------------------------------------------
 struct Layout {
-  size_t hdr, pnode, pedge, perow, prow, pio, qorder, knode, kedge, kerow, counters;
-  size_t lvl_bhdr, lvl_arena, lvl_io;   // small-S schedule
+  size_t hdr, pnode, pedge, perow, prow, player, pio, qorder, knode, kedge, kerow, counters;
+  size_t qlvl, lvl_goff, lvl_first, lvl_loc, lvl_arena;  // small-S schedule
   size_t lvl_arena_bytes;
+  int lvl_max_batches;
   size_t total;
 };
 
@@ -90,18 +154,23 @@ inline Layout make_layout(int P, int N, int C, int I, int O) {
   L.pedge = take(sizeof(EdgeRec) * p * C);
   L.perow = take(sizeof(int32_t) * p * C);
   L.prow = take(sizeof(int32_t) * p * N);
+  L.player = take(sizeof(int32_t) * p * N);
   L.pio = take(sizeof(int32_t) * p * (I + O));
   L.qorder = take(sizeof(int32_t) * (p + 1));
   L.knode = take(sizeof(NodeRec) * p * N);
   L.kedge = take(sizeof(EdgeRec) * p * C);
   L.kerow = take(sizeof(int32_t) * p * C);
   L.counters = take(sizeof(uint32_t) * 64);
-  // small-S schedule: one batch per genome at most; per task 16 B + slot 2 B,
-  // per edge 6 B, per round 4 B, plus alignment slack per batch.
-  L.lvl_bhdr = take(sizeof(BatchHdr) * (p + 1));
-  L.lvl_arena_bytes = p * (size_t(N) * 20 + size_t(C) * 8 + size_t(N) * 8 + 256);
+  // small-S schedule
+  const int budget = lvl_budget(N, C, I, O);
+  const int wmax = lvl_max_weight(N, C, I, O, budget);
+  L.lvl_max_batches = int(p * size_t(wmax) / size_t(budget)) + 2;
+  L.qlvl = take(sizeof(int32_t) * (p + 1));
+  L.lvl_goff = take(sizeof(int32_t) * (p + 1));
+  L.lvl_first = take(sizeof(int32_t) * (size_t(L.lvl_max_batches) + 2));
+  L.lvl_loc = take(sizeof(BatchLoc) * (size_t(L.lvl_max_batches) + 1));
+  L.lvl_arena_bytes = p * size_t(lvl_pb_max(N, C, I, O)) + 256;
   L.lvl_arena = take(L.lvl_arena_bytes);
-  L.lvl_io = take(sizeof(int32_t) * p * (I + O));
   L.total = off;
   return L;
 }
@@ -119,9 +188,13 @@ struct Ws {
   EdgeRec *kedge;
   int32_t *kerow;
   uint32_t *counters;
-  BatchHdr *lvl_bhdr;
+  int32_t *player;
+  int32_t *qlvl;
+  int32_t *lvl_goff;
+  int32_t *lvl_first;
+  BatchLoc *lvl_loc;
   unsigned char *lvl_arena;
-  int32_t *lvl_io;
+  int lvl_budget, lvl_max_batches;
   int P, N, C, I, O;
 };
 
@@ -139,16 +212,23 @@ inline Ws make_ws(void *base, const Layout &L, int P, int N, int C, int I, int O
   w.kedge = reinterpret_cast<EdgeRec *>(b + L.kedge);
   w.kerow = reinterpret_cast<int32_t *>(b + L.kerow);
   w.counters = reinterpret_cast<uint32_t *>(b + L.counters);
-  w.lvl_bhdr = reinterpret_cast<BatchHdr *>(b + L.lvl_bhdr);
+  w.player = reinterpret_cast<int32_t *>(b + L.player);
+  w.qlvl = reinterpret_cast<int32_t *>(b + L.qlvl);
+  w.lvl_goff = reinterpret_cast<int32_t *>(b + L.lvl_goff);
+  w.lvl_first = reinterpret_cast<int32_t *>(b + L.lvl_first);
+  w.lvl_loc = reinterpret_cast<BatchLoc *>(b + L.lvl_loc);
   w.lvl_arena = reinterpret_cast<unsigned char *>(b + L.lvl_arena);
-  w.lvl_io = reinterpret_cast<int32_t *>(b + L.lvl_io);
+  w.lvl_budget = lvl_budget(N, C, I, O);
+  w.lvl_max_batches = L.lvl_max_batches;
   w.P = P; w.N = N; w.C = C; w.I = I; w.O = O;
   return w;
 }
 
 // counters[] slots
 constexpr int CTR_FWD_ITEM = 0, CTR_FWD_DONE = 1, CTR_HN_ITEM = 2, CTR_HN_DONE = 3,
-              CTR_LVL_ITEM = 4, CTR_LVL_DONE = 5, CTR_NBATCH = 8;
+              CTR_LVL_ITEM = 4, CTR_LVL_DONE = 5, CTR_NBATCH = 8, CTR_ERR = 9;
+// error bits in counters[CTR_ERR]
+constexpr uint32_t ERR_TMA_TIMEOUT = 1u;
 
 // -- activations (textbook forms; accurate libm-style device functions) -----------
 __device__ __forceinline__ float act_apply(int a, float z) {
@@ -204,6 +284,14 @@ cudaError_t forward_set_smem_limit(int bytes);
 cudaError_t backward_set_smem_limit(int bytes);
 int forward_sp_occupancy(int warps, size_t smem);
 int hyperneat_occupancy(int warps, size_t smem);
+// level-synchronous small-S form
+cudaError_t launch_lvl_build(const Ws &w, cudaStream_t st);
+size_t forward_lvl_smem(const Ws &w, int st_samples);
+cudaError_t launch_forward_lvl(const Ws &w, const float *inputs, int64_t stride, int S,
+                               float *outputs, int threads, int grid, cudaStream_t st);
+cudaError_t lvl_set_smem_limit(int bytes);
+int forward_lvl_occupancy(int threads, size_t smem, int st_samples);
+int lvl_tile(int S);
 
 }  // namespace neat
 

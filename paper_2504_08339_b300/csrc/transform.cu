@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(256) k_transform(Ws w, const float *__restrict
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ int wbuf[33];
   __shared__ unsigned s_status;
-  __shared__ int s_V, s_E;
+  __shared__ int s_V, s_E, s_nch;
 
   const int N = w.N, C = w.C, I = w.I, O = w.O;
   const int g = blockIdx.x, tid = threadIdx.x, T = blockDim.x;
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(256) k_transform(Ws w, const float *__restrict
   const float *gn = nodes + size_t(g) * N * 5;
   const float *gc = conns + size_t(g) * C * 4;
 
-  if (tid == 0) { s_status = 0u; s_V = 0; s_E = 0; }
+  if (tid == 0) { s_status = 0u; s_V = 0; s_E = 0; s_nch = 0; }
   __syncthreads();
 
   // 1. node rows: validity, attribute checks, (key,row) sort keys
@@ -323,17 +323,25 @@ __global__ void __launch_bounds__(256) k_transform(Ws w, const float *__restrict
   // 7. padded program (valid genomes only)
   GenomeHdr h;
   h.V = 0; h.E = 0; h.L = 0; h.status = status; h.node_off = 0; h.edge_off = 0;
-  h.lvl_off = -1; h.pad = 0;
+  h.lvl_off = -1; h.nch = 0;
   if (status == 0u) {
     h.V = V; h.E = E; h.L = t;
-    // edge begin per position
-    for (int p = tid; p < V; p += T) tmp[p] = indeg[order_s[p]];
+    // edge begin per position; 4-edge chunk count of the level-synchronous form
+    int my_nch = 0;
+    for (int p = tid; p < V; p += T) {
+      tmp[p] = indeg[order_s[p]];
+      my_nch += (tmp[p] + 3) >> 2;
+    }
+    if (my_nch) atomicAdd(&s_nch, my_nch);
     __syncthreads();
+    h.nch = s_nch;
     block_exclusive_scan(tmp, V, wbuf);
     NodeRec *pn = w.pnode + size_t(g) * N;
     int32_t *prow = w.prow + size_t(g) * N;
+    int32_t *play = w.player + size_t(g) * N;
     for (int p = tid; p < N; p += T) {
       NodeRec rec;
+      play[p] = p < V ? layer_s[order_s[p]] : -1;
       if (p < V) {
         const int s = order_s[p], row = row_of_s[s];
         const float *nr = gn + row * 5;
@@ -385,7 +393,7 @@ __device__ __forceinline__ uint64_t cost_key(const GenomeHdr &h, int mode, int g
   return (uint64_t(cost) << 32) | uint64_t(0xffffffffu - uint32_t(g));
 }
 
-__global__ void __launch_bounds__(256) k_rank(Ws w, int mode) {
+__global__ void __launch_bounds__(256) k_rank(Ws w, int mode, int32_t *__restrict__ qout) {
   __shared__ uint64_t tile[256];
   const int P = w.P;
   const int g = blockIdx.x * 256 + threadIdx.x;
@@ -399,7 +407,7 @@ __global__ void __launch_bounds__(256) k_rank(Ws w, int mode) {
     for (int k = 0; k < lim; ++k) rank += tile[k] > kg;
     __syncthreads();
   }
-  if (g < P) w.qorder[rank] = g;
+  if (g < P) qout[rank] = g;
 }
 
 // Exclusive scans of V and E in queue order -> ragged offsets (one CTA).
@@ -474,7 +482,11 @@ cudaError_t launch_transform(const Ws &w, const float *nodes, const float *conns
 
 cudaError_t launch_queue_build(const Ws &w, int mode, cudaStream_t st) {
   if (w.P == 0) return cudaSuccess;
-  k_rank<<<(w.P + 255) / 256, 256, 0, st>>>(w, mode);
+  (void)mode;
+  // size-sorted queue (sample-parallel forms, packing order) and
+  // layer-sorted queue (level-synchronous batches)
+  k_rank<<<(w.P + 255) / 256, 256, 0, st>>>(w, 0, w.qorder);
+  k_rank<<<(w.P + 255) / 256, 256, 0, st>>>(w, 1, w.qlvl);
   k_offsets<<<1, 1024, 0, st>>>(w);
   k_pack<<<w.P, 128, 0, st>>>(w);
   return cudaGetLastError();

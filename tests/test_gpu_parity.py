@@ -121,12 +121,16 @@ def _fwd_case(name, P, S, seed=2):
     ("differentiation", 256, 100),
     ("hyperneat", 128, 33),
 ])
-@pytest.mark.parametrize("plain", [False, True])
-def test_forward_parity(name, P, S, plain):
+@pytest.mark.parametrize("path", ["auto", "level", "sample", "plain"])
+def test_forward_parity(name, P, S, path):
     nodes, conns, spec, x = _fwd_case(name, P, S)
     plan = _plan(spec, P)
+    if path == "level":
+        plan.set_tuning(small_s_max=64)
+    elif path == "sample":
+        plan.set_tuning(small_s_max=-1)
     plan.transform(_dev(nodes), _dev(conns))
-    out = plan.forward(_dev(x), plain=plain).cpu().numpy()
+    out = plan.forward(_dev(x), plain=path == "plain").cpu().numpy()
     ref, bnd = oracle.forward(nodes, conns, x, spec.I, spec.O, with_bound=True)
     stats = compare_outputs(out, ref, bnd)
     if name in ("tiny", "differentiation"):
