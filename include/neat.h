@@ -124,12 +124,15 @@ neat_status neat_plan_destroy(neat_plan *plan);
  *   small_s_max      largest S that uses the level-synchronous forward (1..64,
  *                    -1 = never; default 8); larger S, calls that ask for the
  *                    saved aggregates, and batches that do not fit in shared
- *                    memory use the sample-parallel forward */
+ *                    memory use the sample-parallel forward
+ *   lvl_budget_kb    program bytes (KiB, 8..160) per level-synchronous batch;
+ *                    applied by the next neat_transform */
 typedef struct {
   int warps_per_cta;
   int samples_per_lane;
   int lvl_threads;
   int small_s_max;
+  int lvl_budget_kb;
 } neat_tuning;
 neat_status neat_plan_set_tuning(neat_plan *plan, const neat_tuning *t);
 neat_status neat_plan_get_tuning(const neat_plan *plan, neat_tuning *t);

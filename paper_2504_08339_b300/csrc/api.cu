@@ -161,6 +161,9 @@ neat_status neat_plan_set_tuning(neat_plan *plan, const neat_tuning *t) {
   if (t->lvl_threads < 0 || t->lvl_threads > 256 || (t->lvl_threads % 32) != 0)
     return NEAT_ERR_ARG;
   if (t->small_s_max < -1 || t->small_s_max > 64) return NEAT_ERR_ARG;
+  if (t->lvl_budget_kb != 0 && (t->lvl_budget_kb * 1024 < neat::LVL_MIN_BUDGET ||
+                                t->lvl_budget_kb * 1024 > neat::LVL_MAX_BUDGET))
+    return NEAT_ERR_ARG;
   plan->tune = *t;
   return NEAT_OK;
 }
@@ -172,6 +175,7 @@ neat_status neat_plan_get_tuning(const neat_plan *plan, neat_tuning *t) {
   if (t->samples_per_lane == 0) t->samples_per_lane = 1;
   if (t->lvl_threads == 0) t->lvl_threads = lvl_threads(plan);
   if (t->small_s_max == 0) t->small_s_max = small_s_max(plan);
+  if (t->lvl_budget_kb == 0) t->lvl_budget_kb = plan->w.lvl_budget / 1024;
   return NEAT_OK;
 }
 
@@ -187,6 +191,10 @@ neat_status neat_transform(neat_plan *plan, const float *nodes, const float *con
         !aligned(n_layers, 4) || !aligned(gstatus, 4))
       return NEAT_ERR_ARG;
   }
+  // the batch budget is fixed by the transform that builds the batches
+  plan->w.lvl_budget = plan->tune.lvl_budget_kb > 0
+                           ? plan->tune.lvl_budget_kb * 1024
+                           : neat::lvl_budget(plan->N, plan->C, plan->I, plan->O);
   cudaError_t e = neat::launch_transform(plan->w, nodes, conns, order, layer, n_layers, gstatus,
                                          stream);
   if (e == cudaSuccess) e = neat::launch_queue_build(plan->w, 0, stream);

@@ -390,13 +390,20 @@ __device__ __forceinline__ void run_round(const TaskRec *__restrict__ tasks,
     const int c0 = int(tk.chunk) - lo.y, nc = (cnt + 3) >> 2;
     float a = 0.0f;
     if (nc > 0) {
-      float4 p = part[c0 * ST + s];
-      float sum = p.x, prod = p.y, mx = p.z;
-      for (int k = 1; k < nc; ++k) {
-        p = part[(c0 + k) * ST + s];
-        sum += p.x;
-        prod *= p.y;
-        mx = fmaxf(mx, p.z);
+      // partials four at a time: the loads of a group are independent, so
+      // they are in flight together
+      float sum = 0.0f, prod = 1.0f, mx = qnan();
+      for (int k = 0; k < nc; k += 4) {
+        float4 p[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          p[u] = k + u < nc ? part[(c0 + k + u) * ST + s] : make_float4(0.0f, 1.0f, qnan(), 0.0f);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          sum += p[u].x;
+          prod *= p[u].y;
+          mx = fmaxf(mx, p[u].z);
+        }
       }
       a = agg == NEAT_AGG_SUM ? sum
         : agg == NEAT_AGG_MEAN ? sum / float(cnt)

@@ -123,6 +123,8 @@ __host__ __device__ inline int lvl_genome_weight(int pb, int V, int budget, int 
 inline int lvl_pb_max(int N, int C, int I, int O) {
   return lvl_genome_bytes(N, lvl_max_chunks(N, C), N, I, O, true);
 }
+constexpr int LVL_MIN_BUDGET = 8 * 1024;
+constexpr int LVL_MAX_BUDGET = 160 * 1024;
 inline int lvl_budget(int N, int C, int I, int O) {
   const int pbmax = lvl_pb_max(N, C, I, O);
   int b = 32 * 1024;
@@ -162,9 +164,10 @@ inline Layout make_layout(int P, int N, int C, int I, int O) {
   L.kerow = take(sizeof(int32_t) * p * C);
   L.counters = take(sizeof(uint32_t) * 64);
   // small-S schedule
-  const int budget = lvl_budget(N, C, I, O);
-  const int wmax = lvl_max_weight(N, C, I, O, budget);
-  L.lvl_max_batches = int(p * size_t(wmax) / size_t(budget)) + 2;
+  // batches for any budget >= LVL_MIN_BUDGET: sum of weights / budget + 1,
+  // with weight <= pb + V * budget / slot_budget + budget / 48
+  L.lvl_max_batches = int(p * size_t(lvl_pb_max(N, C, I, O)) / LVL_MIN_BUDGET +
+                          p * size_t(N) / size_t(lvl_slot_budget(N)) + p / LVL_GENOME_BUDGET) + 3;
   L.qlvl = take(sizeof(int32_t) * (p + 1));
   L.lvl_goff = take(sizeof(int32_t) * (p + 1));
   L.lvl_first = take(sizeof(int32_t) * (size_t(L.lvl_max_batches) + 2));
