@@ -4,7 +4,7 @@ A rollout evaluates the same population on T consecutive input batches (one
 per environment step).  The transformation stage runs once; the T forward
 launches, each reading its step's inputs and writing its step's outputs, are
 captured together with it into a single CUDA graph, so a whole rollout costs
-one graph launch.  With `events=True` an event pair brackets every forward
+one graph launch.  With `events=k` an event pair brackets every k-th forward
 launch inside the graph, which gives per-launch device durations.
 """
 from __future__ import annotations
@@ -16,7 +16,7 @@ from .api import Plan, Transformed
 
 class Rollout:
     def __init__(self, plan: Plan, T: int, S: int = 1, ring: int | None = None,
-                 events: bool = False, plain: bool = False):
+                 events: int = 0, plain: bool = False):
         """T steps of S input vectors per genome.  `ring` (<= T) input buffers
         are cycled through (step t reads buffer t % ring); default ring = T."""
         self.plan, self.T, self.S = plan, int(T), int(S)
@@ -32,20 +32,22 @@ class Rollout:
                               torch.empty((P,), dtype=torch.int32, device=dev),
                               torch.empty((P,), dtype=torch.int32, device=dev))
         self.plain = plain
+        self.every = int(events)
         self.ev = None
-        if events:
+        if self.every > 0:
             mk = lambda: torch.cuda.Event(enable_timing=True, external=True)  # noqa: E731
-            self.ev = [(mk(), mk()) for _ in range(self.T)]
+            self.ev = {t: (mk(), mk()) for t in range(0, self.T, self.every)}
         self.graph = None
 
     def _body(self):
         self.plan.transform(self.nodes, self.conns, out=self.tr)
         for t in range(self.T):
-            if self.ev is not None:
-                self.ev[t][0].record()
+            ev = self.ev.get(t) if self.ev is not None else None
+            if ev is not None:
+                ev[0].record()
             self.plan.forward(self.inputs[t % self.ring], out=self.outputs[t], plain=self.plain)
-            if self.ev is not None:
-                self.ev[t][1].record()
+            if ev is not None:
+                ev[1].record()
 
     def capture(self):
         """Capture transform + T forward steps into one graph (run once eagerly
@@ -85,7 +87,7 @@ class Rollout:
         return out_host
 
     def launch_durations_ms(self):
-        """Device duration of each forward launch of the last replay."""
+        """Device duration of the timed forward launches of the last replay."""
         if self.ev is None:
             return None
-        return [a.elapsed_time(b) for a, b in self.ev]
+        return [a.elapsed_time(b) for a, b in self.ev.values()]

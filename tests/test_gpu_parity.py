@@ -401,3 +401,31 @@ def test_cuda_graph_replay_matches_direct_calls():
         graph.replay()
         torch.cuda.synchronize()
         assert torch.equal(outs, direct)
+
+
+def test_tuning_knobs_and_autotuner(tmp_path, monkeypatch):
+    from paper_2504_08339_b300 import NeatError
+    from paper_2504_08339_b300.autotune import autotune
+    nodes, conns, spec = population_for("locomotion", seed=8, P=600)
+    plan = _plan(spec, 600)
+    t = plan.get_tuning()
+    assert t["lvl_threads"] == 256 and t["small_s_max"] == 8 and t["lvl_budget_kb"] >= 8
+    with pytest.raises(NeatError):
+        plan.set_tuning(lvl_threads=100)
+    with pytest.raises(NeatError):
+        plan.set_tuning(lvl_budget_kb=1)
+    x = np.random.default_rng(0).standard_normal((600, 1, spec.I)).astype(np.float32)
+    ref, bnd = oracle.forward(nodes, conns, x, spec.I, spec.O, with_bound=True)
+    monkeypatch.setenv("NEAT_TUNE_CACHE", str(tmp_path / "tune.json"))
+    dn, dc, dx = _dev(nodes), _dev(conns), _dev(x)
+    res = autotune(plan, dn, dc, dx, reps=3)
+    assert res["trials"] and res["tuning"]
+    compare_outputs(plan.forward(dx).cpu().numpy(), ref, bnd)
+    # every candidate tuning gives a correct result
+    for tr in res["trials"]:
+        plan.set_tuning(**tr["tuning"])
+        plan.transform(dn, dc)
+        compare_outputs(plan.forward(dx).cpu().numpy(), ref, bnd, what=str(tr["tuning"]))
+    # the cache answers the second call
+    res2 = autotune(plan, dn, dc, dx, reps=3)
+    assert res2["tuning"] == res["tuning"]
