@@ -194,6 +194,31 @@ neat_status neat_backward(neat_plan *plan, const float *inputs, int64_t in_pop_s
 neat_status neat_hyperneat_query(neat_plan *plan, int grid, float thresh, float *weights,
                                  cudaStream_t stream);
 
+/* Size of the fixed device array used by neat_forward_noalloc. */
+#define NEAT_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* Transformation + batched forward in one call that allocates nothing (the
+ * paper has no counterpart: this serves callers that cannot allocate device
+ * memory when they evaluate, e.g. code inside an allocator-free real-time
+ * loop or a plugin that is handed only its input and output buffers).
+ *   nodes [P, N, 5], conns [P, C, 4], inputs / in_pop_stride / S as in
+ *   neat_forward; outputs [P, S, O] f32 out; gstatus [P] u32 out.
+ * The plan workspace and the transform's order/layer tensors live in one
+ * static device array of NEAT_NOALLOC_SCRATCH_BYTES compiled into the library
+ * (held by every GPU that loads it until the process exits).  A population
+ * whose workspace does not fit returns NEAT_ERR_WORKSPACE before any launch
+ * (about P * (56 N + 28 C + 4 (I + O)) bytes plus the small-sample schedule;
+ * e.g. 600 genomes of N = 128, C = 512 fit).  Uses the sample-parallel
+ * forward for every S.
+ * The first call on a device (that device current) looks up the array's
+ * address with cudaGetSymbolAddress and sets kernel attributes: make it before
+ * any stream capture.  All calls share the array and each call overwrites it:
+ * calls that overlap on the GPU race and must be serialised by the caller.
+ * No cudaMalloc, cudaFree or other allocating call is made. */
+neat_status neat_forward_noalloc(const float *nodes, const float *conns, int P, int N, int C,
+                                 int I, int O, const float *inputs, int64_t in_pop_stride, int S,
+                                 float *outputs, uint32_t *gstatus, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,7 +23,8 @@ G_CYCLE, G_DANGLING_KEY, G_DUP_KEY, G_DUP_EDGE, G_EDGE_INTO_INPUT, G_BAD_ATTR, G
 SYMBOLS = ("neat_version", "neat_status_string", "neat_last_cuda_error",
            "neat_workspace_bytes", "neat_plan_create",
            "neat_plan_destroy", "neat_plan_set_tuning", "neat_plan_get_tuning", "neat_transform",
-           "neat_forward", "neat_forward_plain", "neat_backward", "neat_hyperneat_query")
+           "neat_forward", "neat_forward_plain", "neat_backward", "neat_hyperneat_query",
+           "neat_forward_noalloc")
 
 
 class NeatError(RuntimeError):
@@ -66,6 +67,8 @@ def load(path: str = LIB_PATH):
             "neat_forward_plain": (i32, [vp, vp, i64, i32, vp, vp]),
             "neat_backward": (i32, [vp, vp, i64, i32, vp, vp, vp, vp, vp, vp, vp]),
             "neat_hyperneat_query": (i32, [vp, i32, f32, vp, vp]),
+            "neat_forward_noalloc": (i32, [vp, vp, i32, i32, i32, i32, i32, vp, i64, i32, vp, vp,
+                                           vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
