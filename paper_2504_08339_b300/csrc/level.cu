@@ -248,12 +248,12 @@ __global__ void __launch_bounds__(BLD_THREADS) k_lvl_build(Ws w) {
   const int G = 1 + I + O;
   const int off_gio = int(sizeof(BatchHead));
   const int off_round = (off_gio + 4 * ng * G + 7) & ~7;
-  const int off_task = (off_round + 8 * (nrounds2 + 1) + 15) & ~15;
+  const int off_task = (off_round + int(sizeof(RoundRec)) * (nrounds2 + 1) + 15) & ~15;
   const int off_eslot = off_task + int(sizeof(TaskRec)) * ntasks;
   const int off_ew = (off_eslot + 8 * nchunks + 15) & ~15;
   const int bytes = (off_ew + 16 * nchunks + 15) & ~15;
   unsigned char *base = w.lvl_arena + w.lvl_goff[q0];
-  int2 *rt = reinterpret_cast<int2 *>(base + off_round);
+  RoundRec *rt = reinterpret_cast<RoundRec *>(base + off_round);
   TaskRec *tasks = reinterpret_cast<TaskRec *>(base + off_task);
   uint16_t *eslot = reinterpret_cast<uint16_t *>(base + off_eslot);
   float *ew = reinterpret_cast<float *>(base + off_ew);
@@ -271,19 +271,39 @@ __global__ void __launch_bounds__(BLD_THREADS) k_lvl_build(Ws w) {
     loc.head = off_task;
     loc.pad = 0;
     w.lvl_loc[b] = loc;
-    // round table (same walk as above)
+    // round table (same walk as above), with the activation groups of each
+    // round (tasks of a round are sorted by activation)
     int R = 0, in = 0, cur = -1;
+    RoundRec rr;
+    int hist[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    auto close_round = [&](int end) {
+      int acc = 0;
+      for (int a = 0; a < 8; ++a) {
+        rr.act[a] = uint16_t(acc);
+        acc += a < 7 ? hist[a] : 0;
+      }
+      rr.act[7] = uint16_t(end - rr.task);
+      rt[R++] = rr;
+      for (int a = 0; a < 8; ++a) hist[a] = 0;
+    };
     for (int j = 0; j < ntasks; ++j) {
       const int lay = int(keys[j] >> 33);
       const int nc = cnt[j + 1] - cnt[j];
       if (j == 0 || lay != cur || in + nc > LVL_PCAP) {
-        rt[R++] = make_int2(j, cnt[j]);
+        if (j > 0) close_round(j);
+        rr.task = j;
+        rr.chunk = cnt[j];
         in = 0;
         cur = lay;
       }
       in += nc;
+      ++hist[int((keys[j] >> 30) & 7u)];
     }
-    rt[R] = make_int2(ntasks, nchunks);
+    if (ntasks > 0) close_round(ntasks);
+    rr.task = ntasks;
+    rr.chunk = nchunks;
+    for (int a = 0; a < 8; ++a) rr.act[a] = 0;
+    rt[R] = rr;
   }
   // task records and their padded edge chunks
   for (int j = tid; j < ntasks; j += T) {
@@ -352,16 +372,18 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, int byte
 // One round, two fully packed phases.
 //  A: one thread per (4-edge chunk, sample): sum, product and max of the
 //     chunk's w * v terms (padding slots skipped) into part[].
-//  B: one thread per (task, sample): combine the task's chunk partials with
-//     its aggregation, then v[slot] = act(b + r * a).
+//  B: warp w takes the tasks of activation types w, w + nwarps, ...; one lane
+//     per (task, sample) combines the task's chunk partials with its
+//     aggregation, then v[slot] = act(b + r * a) -- one activation branch per
+//     warp.
 template <int ST>
 __device__ __forceinline__ void run_round(const TaskRec *__restrict__ tasks,
                                           const uint2 *__restrict__ eslot,
                                           const float4 *__restrict__ ew, float4 *part, float *v,
-                                          int2 lo, int2 hi) {
-  const int na = (hi.y - lo.y) * ST;
+                                          const RoundRec &lo, int hi_chunk) {
+  const int na = (hi_chunk - lo.chunk) * ST;
   for (int it = threadIdx.x; it < na; it += blockDim.x) {
-    const int c = lo.y + (ST == 1 ? it : it / ST);
+    const int c = lo.chunk + (ST == 1 ? it : it / ST);
     const int s = ST == 1 ? 0 : it % ST;
     const uint2 sl = eslot[c];
     const float4 w4 = ew[c];
@@ -381,13 +403,15 @@ __device__ __forceinline__ void run_round(const TaskRec *__restrict__ tasks,
     part[it] = make_float4(sum, prod, mx, 0.0f);
   }
   __syncthreads();
-  const int nb = (hi.x - lo.x) * ST;
-  for (int it = threadIdx.x; it < nb; it += blockDim.x) {
-    const int t = lo.x + (ST == 1 ? it : it / ST);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int act = warp; act < 7; act += nw) {
+  const int g0 = lo.task + lo.act[act], gn = (lo.act[act + 1] - lo.act[act]) * ST;
+  for (int it = lane; it < gn; it += 32) {
+    const int t = g0 + (ST == 1 ? it : it / ST);
     const int s = ST == 1 ? 0 : it % ST;
     const TaskRec tk = tasks[t];
     const int cnt = task_cnt(tk.meta), agg = task_agg(tk.meta);
-    const int c0 = int(tk.chunk) - lo.y, nc = (cnt + 3) >> 2;
+    const int c0 = int(tk.chunk) - lo.chunk, nc = (cnt + 3) >> 2;
     float a = 0.0f;
     if (nc > 0) {
       // partials four at a time: the loads of a group are independent, so
@@ -409,7 +433,8 @@ __device__ __forceinline__ void run_round(const TaskRec *__restrict__ tasks,
         : agg == NEAT_AGG_MEAN ? sum / float(cnt)
         : agg == NEAT_AGG_PRODUCT ? prod : mx;
     }
-    v[task_slot(tk.meta) * ST + s] = act_apply(task_act(tk.meta), fmaf(tk.resp, a, tk.bias));
+    v[task_slot(tk.meta) * ST + s] = act_apply(act, fmaf(tk.resp, a, tk.bias));
+  }
   }
 }
 
@@ -464,7 +489,7 @@ __global__ void __launch_bounds__(256) k_forward_lvl(Ws w, const float *__restri
     }
     const BatchHead hd = *reinterpret_cast<const BatchHead *>(sm);
     const int *gio = reinterpret_cast<const int *>(sm + hd.off_gio);
-    const int2 *rt = reinterpret_cast<const int2 *>(sm + hd.off_round);
+    const RoundRec *rt = reinterpret_cast<const RoundRec *>(sm + hd.off_round);
     const TaskRec *tasks = reinterpret_cast<const TaskRec *>(sm + hd.off_task);
     const uint2 *eslot = reinterpret_cast<const uint2 *>(sm + hd.off_eslot);
     const float4 *ew = reinterpret_cast<const float4 *>(sm + hd.off_ew);
@@ -489,7 +514,7 @@ __global__ void __launch_bounds__(256) k_forward_lvl(Ws w, const float *__restri
         __syncthreads();
       }
       for (int r = 0; r < hd.n_rounds; ++r) {
-        run_round<ST>(tasks, eslot, ew, part, v, rt[r], rt[r + 1]);
+        run_round<ST>(tasks, eslot, ew, part, v, rt[r], rt[r + 1].chunk);
         __syncthreads();
       }
       for (int it = tid; it < hd.n_genomes * O * ST; it += blockDim.x) {

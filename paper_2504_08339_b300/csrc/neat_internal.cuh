@@ -54,7 +54,8 @@ struct __align__(16) GenomeHdr {
 // program lives in the level arena as one contiguous, 16-byte aligned block:
 //   BatchHead (48 B)
 //   gio       int32[n_genomes*(1+I+O)] genome id, input slots, output slots
-//   rounds    int2[n_rounds + 1]       (first task, first chunk) of each round
+//   rounds    RoundRec[n_rounds + 1]   first task, first chunk and activation
+//                                      groups of each round
 //   --- off_task: the head part above is staged first, the rest after it
 //   tasks     TaskRec[n_tasks]         non-input nodes, by (layer, act, -cnt)
 //   eslot     uint16[4 * n_chunks]     source value slot of each edge (0xffff: pad)
@@ -69,6 +70,13 @@ struct __align__(16) BatchHead {
   int off_gio, prog_bytes, off_ew, pad;
 };
 constexpr int LVL_PCAP = 256;  // chunks per round (>= the chunks of any one node)
+// Round record (24 B): tasks [task, next.task), chunks [chunk, next.chunk);
+// tasks task + act[a] .. task + act[a+1] - 1 have activation a (act[7] = count).
+struct __align__(8) RoundRec {
+  int task;
+  int chunk;
+  uint16_t act[8];
+};
 // where a batch program sits in the arena
 struct __align__(16) BatchLoc {
   int off;    // byte offset in the arena
@@ -105,7 +113,7 @@ __host__ __device__ inline int task_slot(uint32_t m) { return int(m >> 19); }
 // entries (one per layer plus one per task, bounding the chunk-cap splits).
 __host__ __device__ inline int lvl_genome_bytes(int V, int nch, int L, int I, int O, bool ok) {
   const int tasks = ok ? (V - I) : 0;
-  const int b = 24 * tasks + 24 * (ok ? nch : 0) + 4 * (1 + I + O) + 8 * ((ok ? L : 0) + 2) + 160;
+  const int b = 24 * tasks + 24 * (ok ? nch : 0) + 4 * (1 + I + O) + 24 * ((ok ? L : 0) + 2) + 160;
   return (b + 15) & ~15;
 }
 // largest chunk count of a genome with N node rows and C connection rows
@@ -126,8 +134,10 @@ inline int lvl_pb_max(int N, int C, int I, int O) {
 constexpr int LVL_MIN_BUDGET = 8 * 1024;
 constexpr int LVL_MAX_BUDGET = 160 * 1024;
 inline int lvl_budget(int N, int C, int I, int O) {
+  // 48 KiB measured best on the locomotion rollout (sweep of 24..64 KiB);
+  // larger genomes get a budget of at least twice their largest program
   const int pbmax = lvl_pb_max(N, C, I, O);
-  int b = 32 * 1024;
+  int b = 48 * 1024;
   while (b < 2 * pbmax && b < 96 * 1024) b *= 2;
   return b;
 }
