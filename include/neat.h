@@ -219,6 +219,18 @@ neat_status neat_forward_noalloc(const float *nodes, const float *conns, int P, 
                                  int I, int O, const float *inputs, int64_t in_pop_stride, int S,
                                  float *outputs, uint32_t *gstatus, cudaStream_t stream);
 
+/* Measurement helper (the paper has no counterpart): shared-memory read
+ * bandwidth, the peak of the on-chip term of the roofline.  Launches `blocks`
+ * CTAs of 512 threads on `stream`; each CTA fills a 64 KiB shared array
+ * (32-bit word w = w * 0x9E3779B1 mod 2^32) and each thread then reads
+ * 8 * iters 16-byte words, consecutive threads on consecutive words (no bank
+ * conflicts): words (t + 512 u + it) mod 4096 for u < 8, it < iters.  The XOR
+ * of all words thread t read goes to sink[block * 512 + t] (device u32
+ * [blocks * 512], caller-owned), so no read is optimised away.  Bytes read =
+ * blocks * 512 * 128 * iters; time the launch with events on `stream`.
+ * NEAT_ERR_ARG for blocks < 1, iters < 0 or a NULL/misaligned sink. */
+neat_status neat_probe_smem_read(int blocks, int iters, uint32_t *sink, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

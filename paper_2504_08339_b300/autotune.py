@@ -35,9 +35,11 @@ def candidates(plan: Plan, S: int):
         for thr in (128, 256):
             for kb in (24, 32, 48):
                 out.append(dict(lvl_threads=thr, lvl_budget_kb=kb))
-    for w in (1, 2, 4, 6, 8):
-        if plan.N * 32 * 4 * w <= 200 * 1024:
-            out.append(dict(small_s_max=-1, warps_per_cta=w))
+    for spl in (1, 2, 4):
+        if spl > 1 and S < 32 * spl:
+            continue
+        for w in (4, 8, 16):
+            out.append(dict(small_s_max=-1, warps_per_cta=w, samples_per_lane=spl))
     return out
 
 

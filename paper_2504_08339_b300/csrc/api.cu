@@ -42,18 +42,35 @@ neat_status cuda_status(cudaError_t e) {
   return NEAT_ERR_CUDA;
 }
 
-// warps per CTA of the sample-parallel kernels: as many [N][32] value
-// arrays as fit in ~96 KB, 1..8
-int default_sp_warps(int N) {
-  const size_t per = size_t(N) * 32 * sizeof(float);
-  int w = int((96 * 1024) / per);
-  return std::max(1, std::min(8, w));
+// warps of a HyperNEAT query CTA: as many [N][32] shared-memory value arrays
+// as fit in ~96 KB, 1..8
+int hn_warps(const neat_plan *p) {
+  const size_t per = size_t(p->N) * 32 * sizeof(float);
+  int w = p->tune.warps_per_cta > 0 ? p->tune.warps_per_cta
+                                    : std::max(1, std::min(8, int((96 * 1024) / per)));
+  while (w > 1 && neat::forward_sp_smem(p->N, w, 1) > size_t(p->smem_optin)) --w;
+  return w;
 }
 
-int sp_warps(const neat_plan *p) {
-  int w = p->tune.warps_per_cta > 0 ? p->tune.warps_per_cta : default_sp_warps(p->N);
-  while (w > 1 && neat::forward_sp_smem(p->N, w) > size_t(p->smem_optin)) --w;
-  return w;
+// Launch shape of the sample-parallel forward for S samples per genome.
+// Every genome's values live in its warp's workspace slot (measured faster
+// than shared-memory value arrays on every workload: the L1 caches them and
+// many more warps fit on an SM); the slots bound the grid, which is kept to
+// whole multiples of the SM count.
+neat::SpShape sp_shape(const neat_plan *p, int S) {
+  neat::SpShape sh{};
+  sh.spl = p->tune.samples_per_lane > 0 ? p->tune.samples_per_lane : 1;
+  sh.warps = p->tune.warps_per_cta > 0 ? p->tune.warps_per_cta : 8;
+  sh.vcap = 0;
+  const int slots = neat::sp_scratch_slots(p->w, sh.spl);
+  const int occ = std::max(1, neat::forward_sp_occupancy(sh.warps, 0, sh.spl));
+  const int64_t tiles = (int64_t(S) + 32 * sh.spl - 1) / (32 * sh.spl);
+  const int64_t items = int64_t(p->P) * tiles;
+  int64_t cap = std::min<int64_t>(int64_t(p->sm_count) * occ, slots / sh.warps);
+  if (cap >= p->sm_count) cap = cap / p->sm_count * p->sm_count;
+  const int64_t grid = std::min<int64_t>(cap, (items + sh.warps - 1) / sh.warps);
+  sh.grid = int(std::max<int64_t>(1, grid));
+  return sh;
 }
 
 int lvl_threads(const neat_plan *p) { return p->tune.lvl_threads > 0 ? p->tune.lvl_threads : 256; }
@@ -171,8 +188,9 @@ neat_status neat_plan_set_tuning(neat_plan *plan, const neat_tuning *t) {
 neat_status neat_plan_get_tuning(const neat_plan *plan, neat_tuning *t) {
   if (plan == nullptr || t == nullptr) return NEAT_ERR_ARG;
   *t = plan->tune;
-  if (t->warps_per_cta == 0) t->warps_per_cta = sp_warps(plan);
-  if (t->samples_per_lane == 0) t->samples_per_lane = 1;
+  const neat::SpShape sh = sp_shape(plan, 32);
+  if (t->warps_per_cta == 0) t->warps_per_cta = sh.warps;
+  if (t->samples_per_lane == 0) t->samples_per_lane = sh.spl;
   if (t->lvl_threads == 0) t->lvl_threads = lvl_threads(plan);
   if (t->small_s_max == 0) t->small_s_max = small_s_max(plan);
   if (t->lvl_budget_kb == 0) t->lvl_budget_kb = plan->w.lvl_budget / 1024;
@@ -223,14 +241,11 @@ neat_status neat_forward(neat_plan *plan, const float *inputs, int64_t in_pop_st
     return cuda_status(neat::launch_forward_lvl(plan->w, inputs, in_pop_stride, S, outputs,
                                                 threads, grid, stream));
   }
-  const int warps = sp_warps(plan);
-  const size_t smem = neat::forward_sp_smem(plan->N, warps);
-  const int occ = std::max(1, neat::forward_sp_occupancy(warps, smem));
-  const int64_t items = int64_t(plan->P) * ((S + 31) / 32);
-  const int64_t want = (items + warps - 1) / warps;
-  const int grid = int(std::max<int64_t>(1, std::min<int64_t>(int64_t(plan->sm_count) * occ, want)));
-  return cuda_status(neat::launch_forward_sp(plan->w, inputs, in_pop_stride, S, outputs, saved,
-                                             warps, grid, stream));
+  const neat::SpShape sh = sp_shape(plan, S);
+  if (int64_t(sh.grid) * sh.warps > neat::sp_scratch_slots(plan->w, sh.spl))
+    return NEAT_ERR_UNSUPPORTED;
+  return cuda_status(neat::launch_forward_sp(plan->w, inputs, in_pop_stride, S, outputs, saved, sh,
+                                             stream));
 }
 
 neat_status neat_forward_plain(neat_plan *plan, const float *inputs, int64_t in_pop_stride, int S,
@@ -277,8 +292,9 @@ neat_status neat_hyperneat_query(neat_plan *plan, int grid, float thresh, float 
   if (grid < 2 || grid > 128) return NEAT_ERR_ARG;
   if (plan->P == 0) return NEAT_OK;
   if (weights == nullptr || !aligned(weights, 4)) return NEAT_ERR_ARG;
-  const int warps = sp_warps(plan);
-  const size_t smem = neat::forward_sp_smem(plan->N, warps);
+  const int warps = hn_warps(plan);
+  const size_t smem = neat::forward_sp_smem(plan->N, warps, 1);
+  if (smem > size_t(plan->smem_optin)) return NEAT_ERR_UNSUPPORTED;
   const int occ = std::max(1, neat::hyperneat_occupancy(warps, smem));
   return cuda_status(neat::launch_hyperneat(plan->w, grid, thresh, weights, warps,
                                             plan->sm_count * occ, stream));

@@ -2,14 +2,15 @@
 // order v[k] = act(b + r * agg_e(w_e * v[src_e])); O = v[outputs].
 //
 // Sample-parallel forms: a warp owns one genome and 32 samples; lane l walks
-// the genome's program for sample l with node values in shared memory laid
-// out [position][lane] (conflict-free), program records read with warp-uniform
-// (broadcast) loads.  No lane ever reads another lane's values, so the walk
-// needs no synchronisation at all.
+// the genome's program for sample l with node values laid out
+// [position][lane] (one 128-byte line per position), program records read
+// with warp-uniform (broadcast) loads.  No lane ever reads another lane's
+// values, so the walk needs no synchronisation at all.
 //
-//  k_forward_sp     persistent grid, warps claim (genome, 32-sample tile)
-//                   items from a device work queue in size-sorted order over
-//                   the ragged-packed programs (the batched form).
+//  k_forward_sp     persistent grid, warps claim (genome, 32 * SPL-sample
+//                   tile) items from a device work queue in size-sorted order
+//                   over the ragged-packed programs (the batched form); node
+//                   values in the warp's workspace slot, cached by L1.
 //  k_forward_plain  one CTA per (genome, tile) over the padded programs,
 //                   visiting all N padded positions (the plain form).
 //  k_hyperneat      the batched form with inputs generated in the kernel
@@ -41,57 +42,124 @@ __device__ __forceinline__ NodeRec ld_node(const NodeRec *p) {
   return n;
 }
 
-// Aggregated input a = agg_e(w_e * v[src_e]) of one node for this lane's
-// sample; v is the warp's [position][32] value array.
-__device__ __forceinline__ float node_agg(const NodeRec &n, const EdgeRec *__restrict__ er,
-                                          const float *v, int lane) {
+// Aggregated inputs a[j] = agg_e(w_e * v[src_e]) of one node for this lane's
+// SPL samples; vl = v + lane, v the warp's [position][SPL][32] value array
+// (shared or global memory).  Every sample uses the same rounding order
+// whatever SPL.
+template <int SPL>
+__device__ __forceinline__ void node_agg(const NodeRec &n, const EdgeRec *__restrict__ er,
+                                         const float *vl, float (&a)[SPL]) {
+  constexpr int RS = 32 * SPL;  // floats per position
   const int cnt = meta_cnt(n.meta), agg = meta_agg(n.meta);
   const EdgeRec *e = er + n.in_begin;
-  if (cnt == 0) return 0.0f;
+  if (cnt == 0) {
+#pragma unroll
+    for (int j = 0; j < SPL; ++j) a[j] = 0.0f;
+    return;
+  }
+  // U edges per block: their record and value loads are all issued before the
+  // first use (more loads in flight); sums keep two accumulators, even edges
+  // into a0 and odd edges into a1, so the rounding order does not depend on U
+  constexpr int U = SPL == 1 ? 8 : (SPL == 2 ? 4 : 2);
   if (agg == NEAT_AGG_SUM || agg == NEAT_AGG_MEAN) {
-    float a0 = 0.0f, a1 = 0.0f;
+    float a0[SPL], a1[SPL];
+#pragma unroll
+    for (int j = 0; j < SPL; ++j) a0[j] = a1[j] = 0.0f;
     int k = 0;
+    for (; k + U <= cnt; k += U) {
+      EdgeRec ee[U];
+      float vv[U][SPL];
+#pragma unroll
+      for (int u = 0; u < U; ++u) ee[u] = ld_edge(e + k + u);
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+#pragma unroll
+        for (int j = 0; j < SPL; ++j) vv[u][j] = vl[ee[u].src * RS + j * 32];
+#pragma unroll
+      for (int u = 0; u < U; u += 2)
+#pragma unroll
+        for (int j = 0; j < SPL; ++j) {
+          a0[j] = fmaf(ee[u].w, vv[u][j], a0[j]);
+          a1[j] = fmaf(ee[u + 1].w, vv[u + 1][j], a1[j]);
+        }
+    }
     for (; k + 1 < cnt; k += 2) {
       const EdgeRec e0 = ld_edge(e + k), e1 = ld_edge(e + k + 1);
-      a0 = fmaf(e0.w, v[e0.src * 32 + lane], a0);
-      a1 = fmaf(e1.w, v[e1.src * 32 + lane], a1);
+      const float *p0 = vl + e0.src * RS, *p1 = vl + e1.src * RS;
+#pragma unroll
+      for (int j = 0; j < SPL; ++j) {
+        a0[j] = fmaf(e0.w, p0[j * 32], a0[j]);
+        a1[j] = fmaf(e1.w, p1[j * 32], a1[j]);
+      }
     }
     if (k < cnt) {
       const EdgeRec e0 = ld_edge(e + k);
-      a0 = fmaf(e0.w, v[e0.src * 32 + lane], a0);
+      const float *p0 = vl + e0.src * RS;
+#pragma unroll
+      for (int j = 0; j < SPL; ++j) a0[j] = fmaf(e0.w, p0[j * 32], a0[j]);
     }
-    const float a = a0 + a1;
-    return agg == NEAT_AGG_MEAN ? a / float(cnt) : a;
-  }
-  if (agg == NEAT_AGG_PRODUCT) {
-    float a = 1.0f;
-    for (int k = 0; k < cnt; ++k) {
-      const EdgeRec e0 = ld_edge(e + k);
-      a *= e0.w * v[e0.src * 32 + lane];
+#pragma unroll
+    for (int j = 0; j < SPL; ++j) {
+      const float s = a0[j] + a1[j];
+      a[j] = agg == NEAT_AGG_MEAN ? s / float(cnt) : s;
     }
-    return a;
+    return;
   }
-  // max: fmax fold
-  EdgeRec e0 = ld_edge(e);
-  float a = e0.w * v[e0.src * 32 + lane];
-  for (int k = 1; k < cnt; ++k) {
-    e0 = ld_edge(e + k);
-    a = fmaxf(a, e0.w * v[e0.src * 32 + lane]);
+  // product and max: folds in edge order, loads issued U edges ahead
+  const bool prod = agg == NEAT_AGG_PRODUCT;
+  int k = 0;
+  if (prod) {
+#pragma unroll
+    for (int j = 0; j < SPL; ++j) a[j] = 1.0f;
+  } else {
+    const EdgeRec e0 = ld_edge(e);
+    const float *p0 = vl + e0.src * RS;
+#pragma unroll
+    for (int j = 0; j < SPL; ++j) a[j] = e0.w * p0[j * 32];
+    k = 1;
   }
-  return a;
+  for (; k + U <= cnt; k += U) {
+    EdgeRec ee[U];
+    float vv[U][SPL];
+#pragma unroll
+    for (int u = 0; u < U; ++u) ee[u] = ld_edge(e + k + u);
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int j = 0; j < SPL; ++j) vv[u][j] = vl[ee[u].src * RS + j * 32];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int j = 0; j < SPL; ++j)
+        a[j] = prod ? a[j] * (ee[u].w * vv[u][j]) : fmaxf(a[j], ee[u].w * vv[u][j]);
+  }
+  for (; k < cnt; ++k) {
+    const EdgeRec e0 = ld_edge(e + k);
+    const float *p0 = vl + e0.src * RS;
+#pragma unroll
+    for (int j = 0; j < SPL; ++j)
+      a[j] = prod ? a[j] * (e0.w * p0[j * 32]) : fmaxf(a[j], e0.w * p0[j * 32]);
+  }
 }
 
-// Walk positions [0, V) of a ragged program (inputs already in v).
-template <bool SAVE>
+// Walk positions [0, V) of a ragged program (inputs already in v); vl = v +
+// lane.  SAVE: srow[j] (nullptr for an inactive sample) receives the
+// aggregates of sample j.
+template <bool SAVE, int SPL>
 __device__ __forceinline__ void walk_program(const NodeRec *__restrict__ nr,
-                                             const EdgeRec *__restrict__ er, int V, float *v,
-                                             int lane, float *saved_row) {
+                                             const EdgeRec *__restrict__ er, int V, float *vl,
+                                             float *const (&srow)[SPL]) {
   for (int p = 0; p < V; ++p) {
     const NodeRec n = ld_node(nr + p);
     if (n.meta & META_INPUT) continue;
-    const float a = node_agg(n, er, v, lane);
-    v[p * 32 + lane] = act_apply(meta_act(n.meta), fmaf(n.resp, a, n.bias));
-    if (SAVE) saved_row[p] = a;
+    float a[SPL];
+    node_agg<SPL>(n, er, vl, a);
+    const int act = meta_act(n.meta);
+#pragma unroll
+    for (int j = 0; j < SPL; ++j) {
+      vl[(p * SPL + j) * 32] = act_apply(act, fmaf(n.resp, a[j], n.bias));
+      if (SAVE && srow[j] != nullptr) srow[j][p] = a[j];
+    }
   }
 }
 
@@ -109,12 +177,23 @@ __device__ __forceinline__ void grid_done_reset(uint32_t *item_ctr, uint32_t *do
   }
 }
 
+// Item = (genome in queue order, tile of 32 * SPL samples); lane l evaluates
+// samples tile * 32 * SPL + j * 32 + l, j < SPL.  The values of a genome with
+// V <= vcap live in this warp's shared-memory array, the others in the warp's
+// slot of the workspace value array (L1/L2-resident while in use).
+template <int SPL>
 __global__ void k_forward_sp(Ws w, const float *__restrict__ inputs, int64_t stride, int S,
-                             float *__restrict__ out, float *__restrict__ saved, int tiles) {
+                             float *__restrict__ out, float *__restrict__ saved, int tiles,
+                             int vcap) {
+  constexpr int RS = 32 * SPL;
   extern __shared__ __align__(16) float smv[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int N = w.N, I = w.I, O = w.O;
-  float *v = smv + size_t(wid) * N * 32;
+  float *vs = smv + size_t(wid) * vcap * RS;
+  const size_t slot = size_t(blockIdx.x) * (blockDim.x >> 5) + wid;
+  float *vg = (w.sp_scratch != nullptr && (slot + 1) * size_t(N) * RS <= w.sp_scratch_floats)
+                  ? w.sp_scratch + slot * size_t(N) * RS
+                  : nullptr;
   const int total = w.P * tiles;
   for (;;) {
     int item = 0;
@@ -124,25 +203,43 @@ __global__ void k_forward_sp(Ws w, const float *__restrict__ inputs, int64_t str
     const int q = item / tiles, tile = item - q * tiles;
     const int g = w.qorder[q];
     const GenomeHdr h = w.hdr[g];
-    const int s = tile * 32 + lane;
-    const bool active = s < S;
-    float *orow = out + (size_t(g) * S + (active ? s : 0)) * O;
-    if (h.status != 0u) {
-      if (active)
-        for (int j = 0; j < O; ++j) orow[j] = qnan();
+    float *v = h.V <= vcap ? vs : vg;
+    int sj[SPL];
+#pragma unroll
+    for (int j = 0; j < SPL; ++j) sj[j] = tile * RS + j * 32 + lane;
+    if (h.status != 0u || v == nullptr) {
+      if (v == nullptr && lane == 0) atomicOr(w.counters + CTR_ERR, ERR_SP_NO_SCRATCH);
+#pragma unroll
+      for (int j = 0; j < SPL; ++j)
+        if (sj[j] < S)
+          for (int o = 0; o < O; ++o) out[(size_t(g) * S + sj[j]) * O + o] = qnan();
       continue;
     }
+    float *vl = v + lane;
     const int32_t *io = w.pio + size_t(g) * (I + O);
-    const float *in = inputs + size_t(g) * stride + size_t(active ? s : 0) * I;
-    for (int i = 0; i < I; ++i) v[io[i] * 32 + lane] = active ? __ldg(in + i) : 0.0f;
+#pragma unroll
+    for (int j = 0; j < SPL; ++j) {
+      const bool active = sj[j] < S;
+      const float *in = inputs + size_t(g) * stride + size_t(active ? sj[j] : 0) * I;
+      for (int i = 0; i < I; ++i) vl[(io[i] * SPL + j) * 32] = active ? __ldg(in + i) : 0.0f;
+    }
     const NodeRec *nr = w.knode + h.node_off;
     const EdgeRec *er = w.kedge + h.edge_off;
-    if (saved != nullptr && active)
-      walk_program<true>(nr, er, h.V, v, lane, saved + (size_t(g) * S + s) * N);
-    else
-      walk_program<false>(nr, er, h.V, v, lane, nullptr);
-    if (active)
-      for (int j = 0; j < O; ++j) orow[j] = v[io[I + j] * 32 + lane];
+    if (saved != nullptr) {
+      float *srow[SPL];
+#pragma unroll
+      for (int j = 0; j < SPL; ++j)
+        srow[j] = sj[j] < S ? saved + (size_t(g) * S + sj[j]) * N : nullptr;
+      walk_program<true, SPL>(nr, er, h.V, vl, srow);
+    } else {
+      float *const srow[SPL] = {};
+      walk_program<false, SPL>(nr, er, h.V, vl, srow);
+    }
+#pragma unroll
+    for (int j = 0; j < SPL; ++j)
+      if (sj[j] < S)
+        for (int o = 0; o < O; ++o)
+          out[(size_t(g) * S + sj[j]) * O + o] = vl[(io[I + o] * SPL + j) * 32];
   }
   grid_done_reset(w.counters + CTR_FWD_ITEM, w.counters + CTR_FWD_DONE);
 }
@@ -170,8 +267,9 @@ __global__ void __launch_bounds__(32) k_forward_plain(Ws w, const float *__restr
   for (int p = 0; p < N; ++p) {  // every padded position
     const NodeRec n = ld_node(nr + p);
     if (!(n.meta & META_VALID) || (n.meta & META_INPUT)) continue;
-    const float a = node_agg(n, er, smv, lane);
-    smv[p * 32 + lane] = act_apply(meta_act(n.meta), fmaf(n.resp, a, n.bias));
+    float a[1];
+    node_agg<1>(n, er, smv + lane, a);
+    smv[p * 32 + lane] = act_apply(meta_act(n.meta), fmaf(n.resp, a[0], n.bias));
   }
   if (active)
     for (int j = 0; j < O; ++j) orow[j] = smv[io[I + j] * 32 + lane];
@@ -217,7 +315,8 @@ __global__ void k_hyperneat(Ws w, int G, float thresh, float *__restrict__ weigh
       v[io[2] * 32 + lane] = -1.0f + step * float(ti);
       v[io[3] * 32 + lane] = -1.0f + step * float(tj);
       v[io[4] * 32 + lane] = 1.0f;
-      walk_program<false>(nr, er, h.V, v, lane, nullptr);
+      float *const srow[1] = {nullptr};
+      walk_program<false, 1>(nr, er, h.V, v + lane, srow);
       const float o = v[io[5] * 32 + lane];
       if (active) wg[qi] = fabsf(o) > thresh ? o : 0.0f;
     }
@@ -227,15 +326,25 @@ __global__ void k_hyperneat(Ws w, int G, float thresh, float *__restrict__ weigh
 
 }  // namespace
 
-size_t forward_sp_smem(int N, int warps) { return size_t(N) * 32 * sizeof(float) * warps; }
+size_t forward_sp_smem(int vcap, int warps, int spl) {
+  return size_t(vcap) * 32 * spl * sizeof(float) * warps;
+}
 
 cudaError_t launch_forward_sp(const Ws &w, const float *inputs, int64_t stride, int S,
-                              float *outputs, float *saved, int warps, int grid,
-                              cudaStream_t st) {
+                              float *outputs, float *saved, const SpShape &sh, cudaStream_t st) {
   if (w.P == 0 || S == 0) return cudaSuccess;
-  const size_t smem = forward_sp_smem(w.N, warps);
-  const int tiles = (S + 31) / 32;
-  k_forward_sp<<<grid, warps * 32, smem, st>>>(w, inputs, stride, S, outputs, saved, tiles);
+  const size_t smem = forward_sp_smem(sh.vcap, sh.warps, sh.spl);
+  const int tiles = (S + 32 * sh.spl - 1) / (32 * sh.spl);
+  const dim3 grid(unsigned(sh.grid)), block(unsigned(sh.warps * 32));
+  switch (sh.spl) {
+    case 1: k_forward_sp<1><<<grid, block, smem, st>>>(w, inputs, stride, S, outputs, saved, tiles,
+                                                       sh.vcap); break;
+    case 2: k_forward_sp<2><<<grid, block, smem, st>>>(w, inputs, stride, S, outputs, saved, tiles,
+                                                       sh.vcap); break;
+    case 4: k_forward_sp<4><<<grid, block, smem, st>>>(w, inputs, stride, S, outputs, saved, tiles,
+                                                       sh.vcap); break;
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
@@ -251,7 +360,7 @@ cudaError_t launch_forward_plain(const Ws &w, const float *inputs, int64_t strid
 cudaError_t launch_hyperneat(const Ws &w, int G, float thresh, float *weights, int warps,
                              int ctas, cudaStream_t st) {
   if (w.P == 0) return cudaSuccess;
-  const size_t smem = forward_sp_smem(w.N, warps);
+  const size_t smem = forward_sp_smem(w.N, warps, 1);
   const int64_t G4 = int64_t(G) * G * G * G;
   const int64_t tiles = (G4 + 31) / 32;
   const int tiles_per_chunk = 16;
@@ -264,18 +373,20 @@ cudaError_t launch_hyperneat(const Ws &w, int G, float thresh, float *weights, i
 
 namespace neat {
 cudaError_t forward_set_smem_limit(int bytes) {
-  cudaError_t e = set_dyn_smem_limit(k_forward_sp, bytes);
-  if (e != cudaSuccess) return e;
-  e = set_dyn_smem_limit(k_forward_plain, bytes);
+  cudaError_t e = set_dyn_smem_limit(k_forward_sp<1>, bytes);
+  if (e == cudaSuccess) e = set_dyn_smem_limit(k_forward_sp<2>, bytes);
+  if (e == cudaSuccess) e = set_dyn_smem_limit(k_forward_sp<4>, bytes);
+  if (e == cudaSuccess) e = set_dyn_smem_limit(k_forward_plain, bytes);
   if (e != cudaSuccess) return e;
   return set_dyn_smem_limit(k_hyperneat, bytes);
 }
-int forward_sp_occupancy(int warps, size_t smem) {
+int forward_sp_occupancy(int warps, size_t smem, int spl) {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_forward_sp, warps * 32, smem) !=
-      cudaSuccess)
-    return 0;
-  return n;
+  cudaError_t e = cudaErrorInvalidValue;
+  if (spl == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_forward_sp<1>, warps * 32, smem);
+  if (spl == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_forward_sp<2>, warps * 32, smem);
+  if (spl == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_forward_sp<4>, warps * 32, smem);
+  return e == cudaSuccess ? n : 0;
 }
 int hyperneat_occupancy(int warps, size_t smem) {
   int n = 0;

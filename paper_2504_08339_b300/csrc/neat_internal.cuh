@@ -151,8 +151,17 @@ struct Layout {
   size_t qlvl, lvl_goff, lvl_first, lvl_loc, lvl_arena;  // small-S schedule
   size_t lvl_arena_bytes;
   int lvl_max_batches;
+  size_t core;                       // bytes of everything above
+  size_t sp_scratch, sp_scratch_bytes;  // per-warp node value slots
   size_t total;
 };
+
+// Sample-parallel value arrays: SP_SCRATCH_WARP_SAMPLES / 32 warp slots of
+// [N][32] floats in the workspace (fewer slots when a lane evaluates several
+// samples); a warp keeps the node values of the genome it evaluates in its
+// slot, where they stay L1/L2-resident while in use.
+constexpr size_t SP_SCRATCH_WARP_SAMPLES = 8192 * 32;
+inline size_t sp_scratch_bytes(int N) { return SP_SCRATCH_WARP_SAMPLES * size_t(N) * sizeof(float); }
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -184,6 +193,9 @@ inline Layout make_layout(int P, int N, int C, int I, int O) {
   L.lvl_loc = take(sizeof(BatchLoc) * (size_t(L.lvl_max_batches) + 1));
   L.lvl_arena_bytes = p * size_t(lvl_pb_max(N, C, I, O)) + 256;
   L.lvl_arena = take(L.lvl_arena_bytes);
+  L.core = off;
+  L.sp_scratch_bytes = sp_scratch_bytes(N);
+  L.sp_scratch = take(L.sp_scratch_bytes);
   L.total = off;
   return L;
 }
@@ -207,6 +219,8 @@ struct Ws {
   int32_t *lvl_first;
   BatchLoc *lvl_loc;
   unsigned char *lvl_arena;
+  float *sp_scratch;  // per-warp node value slots (nullptr: none)
+  size_t sp_scratch_floats;
   int lvl_budget, lvl_max_batches;
   int P, N, C, I, O;
 };
@@ -231,6 +245,8 @@ inline Ws make_ws(void *base, const Layout &L, int P, int N, int C, int I, int O
   w.lvl_first = reinterpret_cast<int32_t *>(b + L.lvl_first);
   w.lvl_loc = reinterpret_cast<BatchLoc *>(b + L.lvl_loc);
   w.lvl_arena = reinterpret_cast<unsigned char *>(b + L.lvl_arena);
+  w.sp_scratch = L.sp_scratch_bytes ? reinterpret_cast<float *>(b + L.sp_scratch) : nullptr;
+  w.sp_scratch_floats = L.sp_scratch_bytes / sizeof(float);
   w.lvl_budget = lvl_budget(N, C, I, O);
   w.lvl_max_batches = L.lvl_max_batches;
   w.P = P; w.N = N; w.C = C; w.I = I; w.O = O;
@@ -241,7 +257,7 @@ inline Ws make_ws(void *base, const Layout &L, int P, int N, int C, int I, int O
 constexpr int CTR_FWD_ITEM = 0, CTR_FWD_DONE = 1, CTR_HN_ITEM = 2, CTR_HN_DONE = 3,
               CTR_LVL_ITEM = 4, CTR_LVL_DONE = 5, CTR_NBATCH = 8, CTR_ERR = 9;
 // error bits in counters[CTR_ERR]
-constexpr uint32_t ERR_TMA_TIMEOUT = 1u;
+constexpr uint32_t ERR_TMA_TIMEOUT = 1u, ERR_SP_NO_SCRATCH = 2u;
 
 // -- activations (textbook forms; accurate libm-style device functions) -----------
 __device__ __forceinline__ float act_apply(int a, float z) {
@@ -278,10 +294,19 @@ cudaError_t launch_transform(const Ws &w, const float *nodes, const float *conns
                              int32_t *layer, int32_t *n_layers, uint32_t *gstatus,
                              cudaStream_t st);
 cudaError_t launch_queue_build(const Ws &w, int mode, cudaStream_t st);
+// Sample-parallel launch shape: `spl` samples per lane (1, 2, 4); genomes
+// with V <= vcap keep their values in shared memory, the others in the
+// warp's workspace slot (vcap 0: every genome in the workspace, N: none).
+struct SpShape {
+  int warps, spl, vcap, grid;
+};
 cudaError_t launch_forward_sp(const Ws &w, const float *inputs, int64_t stride, int S,
-                              float *outputs, float *saved, int warps, int grid,
-                              cudaStream_t st);
-size_t forward_sp_smem(int N, int warps);
+                              float *outputs, float *saved, const SpShape &sh, cudaStream_t st);
+size_t forward_sp_smem(int vcap, int warps, int spl);
+// warp slots of the workspace value array for `spl` samples per lane
+inline int sp_scratch_slots(const Ws &w, int spl) {
+  return w.sp_scratch ? int(w.sp_scratch_floats / (size_t(w.N) * 32 * spl)) : 0;
+}
 cudaError_t launch_forward_plain(const Ws &w, const float *inputs, int64_t stride, int S,
                                  float *outputs, cudaStream_t st);
 cudaError_t launch_backward(const Ws &w, const float *inputs, int64_t stride, int S,
@@ -295,7 +320,7 @@ cudaError_t transform_set_smem_limit(int bytes);
 size_t transform_smem(int N, int C);
 cudaError_t forward_set_smem_limit(int bytes);
 cudaError_t backward_set_smem_limit(int bytes);
-int forward_sp_occupancy(int warps, size_t smem);
+int forward_sp_occupancy(int warps, size_t smem, int spl);
 int hyperneat_occupancy(int warps, size_t smem);
 // level-synchronous small-S form
 cudaError_t launch_lvl_build(const Ws &w, cudaStream_t st);

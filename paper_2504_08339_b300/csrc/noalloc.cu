@@ -61,9 +61,11 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 size_t scratch_needed(int P, int N, int C, int I, int O) {
   if (P < 0 || I < 1 || O < 1 || N < I + O || N > NEAT_MAX_NODES || C < 1 || C > NEAT_MAX_CONNS)
     return 0;
+  // the plan layout without its value array for large genomes (this call keeps
+  // every genome's values in shared memory)
   const neat::Layout L = neat::make_layout(P, N, C, I, O);
   const size_t tr = sizeof(int32_t) * (2 * size_t(P) * N + size_t(P));
-  return align256(L.total) + align256(tr);
+  return align256(L.core) + align256(tr);
 }
 
 }  // namespace
@@ -94,7 +96,9 @@ extern "C" neat_status neat_forward_noalloc(const float *nodes, const float *con
   unsigned char *base = g_scratch_ptr[dev];
   const neat::Layout L = neat::make_layout(P, N, C, I, O);
   neat::Ws w = neat::make_ws(base, L, P, N, C, I, O);
-  int32_t *order = reinterpret_cast<int32_t *>(base + align256(L.total));
+  w.sp_scratch = nullptr;
+  w.sp_scratch_floats = 0;
+  int32_t *order = reinterpret_cast<int32_t *>(base + align256(L.core));
   int32_t *layer = order + size_t(P) * N;
   int32_t *n_layers = layer + size_t(P) * N;
 
@@ -105,14 +109,15 @@ extern "C" neat_status neat_forward_noalloc(const float *nodes, const float *con
   if (e == cudaSuccess) e = neat::launch_queue_build(w, 0, stream);
   if (e == cudaSuccess && S > 0) {
     int warps = 8;
-    while (warps > 1 && neat::forward_sp_smem(N, warps) > size_t(96 * 1024)) --warps;
-    const size_t smem = neat::forward_sp_smem(N, warps);
+    while (warps > 1 && neat::forward_sp_smem(N, warps, 1) > size_t(96 * 1024)) --warps;
+    const size_t smem = neat::forward_sp_smem(N, warps, 1);
     if (smem > size_t(g_smem_optin[dev])) return NEAT_ERR_UNSUPPORTED;
-    const int occ = std::max(1, neat::forward_sp_occupancy(warps, smem));
+    const int occ = std::max(1, neat::forward_sp_occupancy(warps, smem, 1));
     const int64_t items = int64_t(P) * ((S + 31) / 32);
     const int grid = int(std::max<int64_t>(
         1, std::min<int64_t>(int64_t(g_sm_count[dev]) * occ, (items + warps - 1) / warps)));
-    e = neat::launch_forward_sp(w, inputs, in_pop_stride, S, outputs, nullptr, warps, grid, stream);
+    const neat::SpShape sh{warps, 1, N, grid};
+    e = neat::launch_forward_sp(w, inputs, in_pop_stride, S, outputs, nullptr, sh, stream);
   }
   return e == cudaSuccess ? NEAT_OK : NEAT_ERR_CUDA;
 }

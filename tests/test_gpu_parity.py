@@ -138,6 +138,38 @@ def test_forward_parity(name, P, S, path):
         assert stats["ill_conditioned"] == 0, stats
 
 
+@pytest.mark.parametrize("name,P,S", [("uneven", 300, 77), ("locomotion", 200, 45),
+                                      ("differentiation", 128, 100)])
+def test_sample_parallel_shapes_agree_bitwise(name, P, S):
+    """Samples per lane and warps per CTA change which lane and which value
+    slot evaluate a sample, not the arithmetic: every shape gives the same
+    bits, and the saved aggregates too.  S = 77, 45, 100 leave a ragged last
+    tile for 1, 2 and 4 samples per lane."""
+    nodes, conns, spec, x = _fwd_case(name, P, S)
+    plan = _plan(spec, P)
+    plan.set_tuning(small_s_max=-1)
+    plan.transform(_dev(nodes), _dev(conns))
+    dx = _dev(x)
+    base_saved = torch.full((P, S, spec.N), float("nan"), device="cuda")
+    base = plan.forward(dx, saved=base_saved)
+    ref, bnd = oracle.forward(nodes, conns, x, spec.I, spec.O, with_bound=True)
+    compare_outputs(base.cpu().numpy(), ref, bnd)
+    shapes = [dict(samples_per_lane=2), dict(samples_per_lane=4),
+              dict(samples_per_lane=1, warps_per_cta=1),
+              dict(samples_per_lane=2, warps_per_cta=4),
+              dict(samples_per_lane=4, warps_per_cta=16),
+              dict(samples_per_lane=1, warps_per_cta=16)]
+    for sh in shapes:
+        plan.set_tuning(small_s_max=-1, **sh)
+        saved = torch.full((P, S, spec.N), float("nan"), device="cuda")
+        out = plan.forward(dx, saved=saved)
+        bits = lambda t: t.view(torch.int32)  # noqa: E731  (NaN-safe equality)
+        assert torch.equal(bits(out), bits(base)), sh
+        # (positions the forward does not write stay NaN on both sides)
+        assert torch.equal(bits(saved), bits(base_saved)), sh
+        assert torch.equal(bits(plan.forward(dx)), bits(base)), sh
+
+
 def test_forward_saved_aggregates_match_oracle_values():
     nodes, conns, spec, x = _fwd_case("differentiation", 64, 45)
     plan = _plan(spec, 64)
@@ -414,6 +446,8 @@ def test_tuning_knobs_and_autotuner(tmp_path, monkeypatch):
         plan.set_tuning(lvl_threads=100)
     with pytest.raises(NeatError):
         plan.set_tuning(lvl_budget_kb=1)
+    with pytest.raises(NeatError):
+        plan.set_tuning(samples_per_lane=3)
     x = np.random.default_rng(0).standard_normal((600, 1, spec.I)).astype(np.float32)
     ref, bnd = oracle.forward(nodes, conns, x, spec.I, spec.O, with_bound=True)
     monkeypatch.setenv("NEAT_TUNE_CACHE", str(tmp_path / "tune.json"))
