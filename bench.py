@@ -335,7 +335,7 @@ def bench_ours(args, rank, world, local, pg):
         d_conns = torch.from_numpy(conns).to(dev)
         d_x = torch.from_numpy(x).to(dev)
         d_y = torch.from_numpy(y).to(dev)
-        saved = torch.empty((P, S, spec.N), device=dev)
+        saved = torch.empty((P, spec.N, S), device=dev)
         out = torch.empty((P, S, spec.O), device=dev)
         go = torch.empty((P, S, spec.O), device=dev)
         tr = plan.transform(d_nodes, d_conns)

@@ -157,8 +157,11 @@ neat_status neat_transform(neat_plan *plan, const float *nodes, const float *con
  *           >= S * I)
  *   S       input vectors per genome (S >= 0)
  *   outputs [P, S, O] f32 out; NaN for genomes with a nonzero status
- *   saved   optional [P, S, N] f32 out (NULL to skip): per canonical position,
- *           the aggregated input a of each node, kept for neat_backward. */
+ *   saved   optional [P, N, S] f32 out (NULL to skip): saved[g][p][s] is the
+ *           aggregated input a of the node at canonical position p for sample
+ *           s (positions of input nodes and p >= V are not written), kept for
+ *           neat_backward; sample-contiguous so that both kernels move it in
+ *           whole 128-byte lines. */
 neat_status neat_forward(neat_plan *plan, const float *inputs, int64_t in_pop_stride, int S,
                          float *outputs, float *saved, cudaStream_t stream);
 

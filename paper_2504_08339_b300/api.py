@@ -128,7 +128,7 @@ class Plan:
             _lib.check(code, "neat_forward_plain")
         else:
             if saved is not None:
-                _need(saved, "saved", torch.float32, (self.P, S, self.N))
+                _need(saved, "saved", torch.float32, (self.P, self.N, S))
             code = self._lib.neat_forward(self._h, _ptr(inputs), stride, S, _ptr(out),
                                           _ptr(saved), _stream(stream))
             _lib.check(code, "neat_forward")
@@ -139,7 +139,7 @@ class Plan:
         S, stride = self._inputs(inputs)
         _need(grad_out, "grad_out", torch.float32, (self.P, S, self.O))
         if saved is not None:
-            _need(saved, "saved", torch.float32, (self.P, S, self.N))
+            _need(saved, "saved", torch.float32, (self.P, self.N, S))
         dev = inputs.device
         gw = torch.empty((self.P, self.C), dtype=torch.float32, device=dev)
         gb = torch.empty((self.P, self.N), dtype=torch.float32, device=dev)
@@ -174,7 +174,7 @@ class NeatFunction(torch.autograd.Function):
         S = inputs.shape[1]
         saved = None
         if store:
-            saved = torch.empty((plan.P, S, plan.N), dtype=torch.float32, device=inputs.device)
+            saved = torch.empty((plan.P, plan.N, S), dtype=torch.float32, device=inputs.device)
         out = plan.forward(inputs, saved=saved)
         ctx.plan = plan
         ctx.saved_agg = saved

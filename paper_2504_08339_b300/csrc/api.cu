@@ -83,11 +83,10 @@ bool lvl_fits(const neat_plan *p, int S) {
   return neat::forward_lvl_smem(p->w, neat::lvl_tile(S)) <= size_t(p->smem_optin);
 }
 
-int backward_warps(const neat_plan *p) {
-  int w = 8;
-  while (w > 1 && neat::backward_smem(p->N, p->C, w) > size_t(200 * 1024)) --w;
-  return w;
-}
+// Backward CTA: 16 warps over all the shared memory a CTA may have; each
+// genome runs on as many warps as its per-warp blocks fit (smaller genomes,
+// more warps).
+constexpr int kBackwardWarps = 16;
 
 neat_status check_inputs(const neat_plan *p, const float *inputs, int64_t stride, int S) {
   if (S < 0) return NEAT_ERR_ARG;
@@ -276,12 +275,13 @@ neat_status neat_backward(neat_plan *plan, const float *inputs, int64_t in_pop_s
       (grad_outputs && !aligned(grad_outputs, 4)) || (saved && !aligned(saved, 4)) ||
       (grad_inputs && !aligned(grad_inputs, 4)))
     return NEAT_ERR_ARG;
-  const int warps = backward_warps(plan);
-  if (neat::backward_smem(plan->N, plan->C, warps) > size_t(plan->smem_optin))
+  if (neat::backward_smem(plan->N, plan->C, 1) > size_t(plan->smem_optin))
     return NEAT_ERR_UNSUPPORTED;
+  const int smem = int(std::min<size_t>(size_t(plan->smem_optin),
+                                        neat::backward_smem(plan->N, plan->C, kBackwardWarps)));
   return cuda_status(neat::launch_backward(plan->w, inputs, in_pop_stride, S, grad_outputs, saved,
                                            grad_weight, grad_bias, grad_response, grad_inputs,
-                                           warps, stream));
+                                           kBackwardWarps, smem, stream));
 }
 
 neat_status neat_hyperneat_query(neat_plan *plan, int grid, float thresh, float *weights,

@@ -143,12 +143,12 @@ __device__ __forceinline__ void node_agg(const NodeRec &n, const EdgeRec *__rest
 }
 
 // Walk positions [0, V) of a ragged program (inputs already in v); vl = v +
-// lane.  SAVE: srow[j] (nullptr for an inactive sample) receives the
-// aggregates of sample j.
+// lane.  SAVE: scol[j][p * S] (scol[j] nullptr for an inactive sample)
+// receives the aggregate of position p for sample j.
 template <bool SAVE, int SPL>
 __device__ __forceinline__ void walk_program(const NodeRec *__restrict__ nr,
                                              const EdgeRec *__restrict__ er, int V, float *vl,
-                                             float *const (&srow)[SPL]) {
+                                             float *const (&scol)[SPL], int S) {
   for (int p = 0; p < V; ++p) {
     const NodeRec n = ld_node(nr + p);
     if (n.meta & META_INPUT) continue;
@@ -158,7 +158,7 @@ __device__ __forceinline__ void walk_program(const NodeRec *__restrict__ nr,
 #pragma unroll
     for (int j = 0; j < SPL; ++j) {
       vl[(p * SPL + j) * 32] = act_apply(act, fmaf(n.resp, a[j], n.bias));
-      if (SAVE && srow[j] != nullptr) srow[j][p] = a[j];
+      if (SAVE && scol[j] != nullptr) scol[j][size_t(p) * S] = a[j];
     }
   }
 }
@@ -226,14 +226,14 @@ __global__ void k_forward_sp(Ws w, const float *__restrict__ inputs, int64_t str
     const NodeRec *nr = w.knode + h.node_off;
     const EdgeRec *er = w.kedge + h.edge_off;
     if (saved != nullptr) {
-      float *srow[SPL];
+      float *scol[SPL];
 #pragma unroll
       for (int j = 0; j < SPL; ++j)
-        srow[j] = sj[j] < S ? saved + (size_t(g) * S + sj[j]) * N : nullptr;
-      walk_program<true, SPL>(nr, er, h.V, vl, srow);
+        scol[j] = sj[j] < S ? saved + size_t(g) * N * S + sj[j] : nullptr;
+      walk_program<true, SPL>(nr, er, h.V, vl, scol, S);
     } else {
-      float *const srow[SPL] = {};
-      walk_program<false, SPL>(nr, er, h.V, vl, srow);
+      float *const scol[SPL] = {};
+      walk_program<false, SPL>(nr, er, h.V, vl, scol, S);
     }
 #pragma unroll
     for (int j = 0; j < SPL; ++j)
@@ -315,8 +315,8 @@ __global__ void k_hyperneat(Ws w, int G, float thresh, float *__restrict__ weigh
       v[io[2] * 32 + lane] = -1.0f + step * float(ti);
       v[io[3] * 32 + lane] = -1.0f + step * float(tj);
       v[io[4] * 32 + lane] = 1.0f;
-      float *const srow[1] = {nullptr};
-      walk_program<false, 1>(nr, er, h.V, v + lane, srow);
+      float *const scol[1] = {nullptr};
+      walk_program<false, 1>(nr, er, h.V, v + lane, scol, 0);
       const float o = v[io[5] * 32 + lane];
       if (active) wg[qi] = fabsf(o) > thresh ? o : 0.0f;
     }

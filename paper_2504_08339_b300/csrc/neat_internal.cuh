@@ -309,9 +309,12 @@ inline int sp_scratch_slots(const Ws &w, int spl) {
 }
 cudaError_t launch_forward_plain(const Ws &w, const float *inputs, int64_t stride, int S,
                                  float *outputs, cudaStream_t st);
+// Backward: `warps` per CTA, `smem_bytes` of dynamic shared memory (at least
+// backward_smem(N, C, 1)); a genome runs on as many warps as blocks of its
+// size fit in smem_bytes.
 cudaError_t launch_backward(const Ws &w, const float *inputs, int64_t stride, int S,
                             const float *grad_out, const float *saved, float *gw, float *gb,
-                            float *gr, float *gi, int warps, cudaStream_t st);
+                            float *gr, float *gi, int warps, int smem_bytes, cudaStream_t st);
 size_t backward_smem(int N, int C, int warps);
 cudaError_t launch_hyperneat(const Ws &w, int grid, float thresh, float *weights, int warps,
                              int ctas, cudaStream_t st);

@@ -150,7 +150,7 @@ def test_sample_parallel_shapes_agree_bitwise(name, P, S):
     plan.set_tuning(small_s_max=-1)
     plan.transform(_dev(nodes), _dev(conns))
     dx = _dev(x)
-    base_saved = torch.full((P, S, spec.N), float("nan"), device="cuda")
+    base_saved = torch.full((P, spec.N, S), float("nan"), device="cuda")
     base = plan.forward(dx, saved=base_saved)
     ref, bnd = oracle.forward(nodes, conns, x, spec.I, spec.O, with_bound=True)
     compare_outputs(base.cpu().numpy(), ref, bnd)
@@ -161,7 +161,7 @@ def test_sample_parallel_shapes_agree_bitwise(name, P, S):
               dict(samples_per_lane=1, warps_per_cta=16)]
     for sh in shapes:
         plan.set_tuning(small_s_max=-1, **sh)
-        saved = torch.full((P, S, spec.N), float("nan"), device="cuda")
+        saved = torch.full((P, spec.N, S), float("nan"), device="cuda")
         out = plan.forward(dx, saved=saved)
         bits = lambda t: t.view(torch.int32)  # noqa: E731  (NaN-safe equality)
         assert torch.equal(bits(out), bits(base)), sh
@@ -174,7 +174,7 @@ def test_forward_saved_aggregates_match_oracle_values():
     nodes, conns, spec, x = _fwd_case("differentiation", 64, 45)
     plan = _plan(spec, 64)
     tr = plan.transform(_dev(nodes), _dev(conns))
-    saved = torch.empty((64, 45, spec.N), device="cuda")
+    saved = torch.empty((64, spec.N, 45), device="cuda")
     out = plan.forward(_dev(x), saved=saved)
     out2 = plan.forward(_dev(x))
     assert torch.equal(out, out2)
@@ -184,7 +184,7 @@ def test_forward_saved_aggregates_match_oracle_values():
     sv = saved.cpu().numpy()
     for g in range(64):
         pos_out = int(np.flatnonzero(order[g] == spec.I)[0])      # output row I
-        a = sv[g, :, pos_out].astype(np.float64)
+        a = sv[g, pos_out, :].astype(np.float64)
         b, r = float(nodes[g, spec.I, 1]), float(nodes[g, spec.I, 2])
         np.testing.assert_allclose(b + r * a, vals[g, :, spec.I], rtol=1e-4, atol=1e-5)
 
@@ -232,7 +232,7 @@ def test_backward_parity(name, P, S, stored):
     xd = _dev(x)
     saved = None
     if stored:
-        saved = torch.empty((P, S, spec.N), device="cuda")
+        saved = torch.empty((P, spec.N, S), device="cuda")
         plan.forward(xd, saved=saved)
     go = np.random.default_rng(9).standard_normal((P, S, spec.O)).astype(np.float32)
     gw, gb, gr, gi = plan.backward(xd, _dev(go), saved=saved)
