@@ -5,18 +5,24 @@
 // sample.
 //
 // One CTA per genome (queue order, large genomes first).  Each warp handles
-// 32-sample tiles: it recomputes (or reloads) the forward values, then walks
-// the canonical order backwards with per-lane adjoints in shared memory; the
-// walk only propagates adjoints (each node's u = dL/dz overwrites its
-// adjoint).  The cross-sample sums then run lane-parallel over the tile:
-// lane per node for dL/db = sum_s u and dL/dr = sum_s u a, lane per edge for
-// dL/dw_e = c_e sum_s u_dst v_src (sum: c = r, mean: c = r / n), each into a
-// lane-owned per-warp accumulator; product and max edges, whose factor
-// differs per sample, are summed with warp butterflies during the walk.  The
-// per-warp accumulators are combined across warps in a fixed order: the
-// result is deterministic (no floating-point atomics).
+// 32-sample tiles (lane = sample): it reloads (or recomputes) the forward
+// values, then walks the canonical order backwards.  A node's adjoint is
+//   dL/dv_p = (pushed part) + sum over sum/mean consumers c of c_e w_e u_c,
+// with u = dL/dz and c_e = r_c (sum) or r_c / n_c (mean).  The second term is
+// PULLED by p from a per-genome list of its outgoing sum/mean edges (sorted
+// by edge, so the rounding order is fixed), reading u_c where the consumer
+// left it; product and max consumers, whose factor differs per sample, PUSH
+// their terms into the adjoint slot of their sources (all in earlier
+// frontiers, so never before those sources are visited) and sum dL/dw with
+// warp butterflies.  Pulling keeps the walk free of read-modify-write chains.
 //
-// Per-warp arrays are [N][33] floats: a lane's sample column (row p, column
+// The cross-sample sums of a tile then run lane-parallel: lane per node for
+// dL/db = sum_s u and dL/dr = sum_s u a, lane per sum/mean edge for
+// dL/dw_e = c_e sum_s u_dst v_src, each into a lane-owned per-warp
+// accumulator.  The per-warp accumulators are combined across warps in a
+// fixed order: the result is deterministic (no floating-point atomics).
+//
+// Per-warp arrays are [V][33] floats: a lane's sample column (row p, column
 // lane) and a lane's row (row p, columns s) both hit 32 distinct banks.
 #include <cuda_runtime.h>
 
@@ -27,15 +33,24 @@
 namespace neat {
 namespace {
 
+constexpr int RS = 33;  // row stride (floats) of the per-warp [V][RS] arrays
+
 __device__ __forceinline__ float warp_sum(float x) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
   return x;
 }
 
-constexpr int RS = 33;  // row stride (floats) of the per-warp [N][RS] arrays
+// 4-byte asynchronous global -> shared copy (completes at cp_async_wait)
+__device__ __forceinline__ void cp_async4(float *smem, const float *gmem) {
+  const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
 
-// z[j] = act(z[j]) for four nodes of one activation: the four evaluations
+// z[j] = act(z[j]) for four values of one activation: the four evaluations
 // are independent and overlap
 template <int A>
 __device__ __forceinline__ void act_same4(float (&z)[4]) {
@@ -54,13 +69,47 @@ __device__ __forceinline__ void act4(int act, float (&z)[4]) {
   }
 }
 
-// Shared memory of a CTA: the genome's node and edge records, c_e and the
-// destination of every edge, then one block per working warp of
+// Ascending bitonic sort of a[0..n2) by the whole CTA, n2 a power of two.
+__device__ void bitonic_sort_u32(uint32_t *a, int n2) {
+  for (int k = 2; k <= n2; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+        const int l = i ^ j;
+        if (l > i) {
+          const uint32_t x = a[i], y = a[l];
+          if (((i & k) == 0) == (x > y)) {
+            a[i] = y;
+            a[l] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+}
+
+__host__ __device__ inline int pow2_at_least(int x) {
+  int p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+// One pulled edge: consumer position and c_e * w_e.
+struct __align__(8) PullRec {
+  int dst;
+  float cw;
+};
+
+// Shared memory of a CTA: the genome's node and edge records; per edge c_e
+// and its destination (-1: product/max); the pull lists (PullRec per
+// sum/mean edge, grouped by source) with each position's range; the sort
+// keys; then one block per working warp of
 // bwd_warp_floats(V, E) floats: v, a, adjoint [V][RS] and the warp's
 // accumulators for dL/dw [E], dL/db [V], dL/dr [V].  As many warps work as
 // blocks of this genome's size fit; the others only join the barriers.
 __host__ __device__ inline size_t bwd_fixed_bytes(int N, int C) {
-  return sizeof(NodeRec) * size_t(N) + sizeof(EdgeRec) * size_t(C) + 2 * sizeof(float) * size_t(C);
+  return sizeof(NodeRec) * size_t(N) + sizeof(EdgeRec) * size_t(C) +
+         2 * sizeof(float) * size_t(C) + sizeof(PullRec) * size_t(C) +
+         2 * sizeof(int) * size_t(N) + sizeof(uint32_t) * size_t(pow2_at_least(C));
 }
 __host__ __device__ inline size_t bwd_warp_floats(int V, int E) {
   return 3 * size_t(V) * RS + size_t(E) + 2 * size_t(V);
@@ -90,24 +139,34 @@ __global__ void k_backward(Ws w, const float *__restrict__ inputs, int64_t strid
     return;
   }
   const int V = h.V, E = h.E;
-  NodeRec *nr = reinterpret_cast<NodeRec *>(sm);      // [N] the genome's node records
-  EdgeRec *er = reinterpret_cast<EdgeRec *>(nr + N);  // [C] and edge records
-  float *ecoef = reinterpret_cast<float *>(er + C);   // [C] c_e of a sum/mean edge
-  int *edst = reinterpret_cast<int *>(ecoef + C);     // [C] its destination (-1: product/max)
-  float *wbase = reinterpret_cast<float *>(edst + C);
+  NodeRec *nr = reinterpret_cast<NodeRec *>(sm);          // [N] node records
+  EdgeRec *er = reinterpret_cast<EdgeRec *>(nr + N);      // [C] edge records
+  float *ecoef = reinterpret_cast<float *>(er + C);       // [C] c_e of a sum/mean edge
+  int *edst = reinterpret_cast<int *>(ecoef + C);         // [C] its destination (-1: product/max)
+  PullRec *pull = reinterpret_cast<PullRec *>(edst + C);  // [C] pull lists
+  int *pbeg = reinterpret_cast<int *>(pull + C);          // [N] pull list of position p:
+  int *pend = pbeg + N;                                   // [N]   pull[pbeg[p] .. pend[p])
+  uint32_t *keys = reinterpret_cast<uint32_t *>(pend + N);  // [pow2(C)] sort keys
+  float *wbase = reinterpret_cast<float *>(keys + pow2_at_least(C));
   const size_t pw = bwd_warp_floats(V, E);
   const int nwa = min(int(blockDim.x >> 5),
                       int((size_t(smem_bytes) - bwd_fixed_bytes(N, C)) / (pw * sizeof(float))));
-  float *v = wbase + size_t(wid) * pw;  // values   [V][RS]
-  float *av = v + V * RS;               // agg      [V][RS]
-  float *dv = av + V * RS;              // adjoints [V][RS]; u once a node is done
-  float *accw = dv + V * RS;            // [E]
-  float *accb = accw + E;               // [V]
-  float *accr = accb + V;               // [V]
+  float *v = wbase + size_t(wid) * pw + lane;  // values   [V][RS] (this lane's column)
+  float *av = v + V * RS;                      // agg      [V][RS]
+  float *dv = av + V * RS;                     // adjoints [V][RS]; u once a node is done
+  float *accw = wbase + size_t(wid) * pw + 3 * V * RS;  // [E]
+  float *accb = accw + E;                               // [V]
+  float *accr = accb + V;                               // [V]
 
+  // ---- per-genome setup: records, edge coefficients, pull lists
   const int32_t *io = w.pio + size_t(g) * (I + O);
   const int32_t *erow = w.kerow + h.edge_off;
-  for (int p = threadIdx.x; p < V; p += blockDim.x) nr[p] = w.knode[h.node_off + p];
+  const int E2 = pow2_at_least(E);
+  for (int p = threadIdx.x; p < V; p += blockDim.x) {
+    nr[p] = w.knode[h.node_off + p];
+    pbeg[p] = 0;
+    pend[p] = 0;
+  }
   for (int k = threadIdx.x; k < E; k += blockDim.x) er[k] = w.kedge[h.edge_off + k];
   for (size_t i = threadIdx.x; i < size_t(nwa) * pw; i += blockDim.x) wbase[i] = 0.0f;
   for (int p = threadIdx.x; p < V; p += blockDim.x) {
@@ -122,30 +181,48 @@ __global__ void k_backward(Ws w, const float *__restrict__ inputs, int64_t strid
     }
   }
   __syncthreads();
+  // keys (source << 16 | edge) of the sum/mean edges; the rest sort last
+  for (int k = threadIdx.x; k < E2; k += blockDim.x)
+    keys[k] = (k < E && edst[k] >= 0) ? (er[k].src << 16) | uint32_t(k) : 0xffffffffu;
+  __syncthreads();
+  bitonic_sort_u32(keys, E2);
+  for (int i = threadIdx.x; i < E; i += blockDim.x) {
+    const uint32_t key = keys[i];
+    if (key == 0xffffffffu) continue;
+    const int src = int(key >> 16), k = int(key & 0xffffu);
+    pull[i].dst = edst[k];
+    pull[i].cw = ecoef[k] * er[k].w;
+    if (i == 0 || (keys[i - 1] >> 16) != uint32_t(src)) pbeg[src] = i;
+    if (i + 1 == E || keys[i + 1] == 0xffffffffu || (keys[i + 1] >> 16) != uint32_t(src))
+      pend[src] = i + 1;
+  }
+  __syncthreads();
 
   for (int tile = wid; wid < nwa && tile < tiles; tile += nwa) {
     const int s = tile * 32 + lane;
     const bool active = s < S;
-    const size_t srow = size_t(g) * S + (active ? s : 0);
     // ---- forward values
     const float *in = inputs + size_t(g) * stride + size_t(active ? s : 0) * I;
-    for (int i = 0; i < I; ++i) v[io[i] * RS + lane] = active ? __ldg(in + i) : 0.0f;
+    for (int i = 0; i < I; ++i) v[io[i] * RS] = active ? __ldg(in + i) : 0.0f;
     if (STORED) {
-      // saved[g][p][s]: one 128-byte line per position, all issued at once
-      const float *col = saved + size_t(g) * N * S + (active ? s : 0);
-#pragma unroll 4
-      for (int p = 0; p < V; ++p) av[p * RS + lane] = active ? __ldg(col + size_t(p) * S) : 0.0f;
-    }
-    if (STORED) {
+      // saved[g][p][s]: every position's line requested at once, straight
+      // into shared memory
+      const float *col = saved + size_t(g) * N * S + s;
+      if (active) {
+        for (int p = 0; p < V; ++p) cp_async4(av + p * RS, col + size_t(p) * S);
+      } else {
+        for (int p = 0; p < V; ++p) av[p * RS] = 0.0f;
+      }
+      cp_async_wait();
       // v = act(b + r a) of every node, four positions at a time
       for (int p = 0; p < V; p += 4) {
         NodeRec n[4];
         float z[4];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int q = min(p + j, V - 1);
-          n[j] = nr[q];
-          z[j] = fmaf(n[j].resp, av[q * RS + lane], n[j].bias);
+        for (int q = 0; q < 4; ++q) {
+          const int pq = min(p + q, V - 1);
+          n[q] = nr[pq];
+          z[q] = fmaf(n[q].resp, av[pq * RS], n[q].bias);
         }
         const int act = meta_act(n[0].meta);
         if (act == meta_act(n[1].meta) && act == meta_act(n[2].meta) &&
@@ -153,20 +230,19 @@ __global__ void k_backward(Ws w, const float *__restrict__ inputs, int64_t strid
           act4(act, z);
         } else {
 #pragma unroll
-          for (int j = 0; j < 4; ++j) z[j] = act_apply(meta_act(n[j].meta), z[j]);
+          for (int q = 0; q < 4; ++q) z[q] = act_apply(meta_act(n[q].meta), z[q]);
         }
 #pragma unroll
-        for (int j = 0; j < 4; ++j)
-          if (p + j < V && !(n[j].meta & META_INPUT)) v[(p + j) * RS + lane] = z[j];
+        for (int q = 0; q < 4; ++q)
+          if (p + q < V && !(n[q].meta & META_INPUT)) v[(p + q) * RS] = z[q];
       }
-    }
-    for (int p = 0; !STORED && p < V; ++p) {
-      const NodeRec n = nr[p];
-      if (n.meta & META_INPUT) continue;
-      float a;
-      {
+    } else {
+      for (int p = 0; p < V; ++p) {
+        const NodeRec n = nr[p];
+        if (n.meta & META_INPUT) continue;
         const int cnt = meta_cnt(n.meta), agg = meta_agg(n.meta);
         const EdgeRec *e = er + n.in_begin;
+        float a;
         if (cnt == 0) {
           a = 0.0f;
         } else if (agg == NEAT_AGG_SUM || agg == NEAT_AGG_MEAN) {
@@ -174,97 +250,87 @@ __global__ void k_backward(Ws w, const float *__restrict__ inputs, int64_t strid
           int k = 0;
           for (; k + 1 < cnt; k += 2) {
             const EdgeRec e0 = e[k], e1 = e[k + 1];
-            a0 = fmaf(e0.w, v[e0.src * RS + lane], a0);
-            a1 = fmaf(e1.w, v[e1.src * RS + lane], a1);
+            a0 = fmaf(e0.w, v[e0.src * RS], a0);
+            a1 = fmaf(e1.w, v[e1.src * RS], a1);
           }
-          if (k < cnt) {
-            const EdgeRec e0 = e[k];
-            a0 = fmaf(e0.w, v[e0.src * RS + lane], a0);
-          }
+          if (k < cnt) a0 = fmaf(e[k].w, v[e[k].src * RS], a0);
           a = a0 + a1;
           if (agg == NEAT_AGG_MEAN) a = a / float(cnt);
         } else if (agg == NEAT_AGG_PRODUCT) {
           a = 1.0f;
-          for (int k = 0; k < cnt; ++k) {
-            const EdgeRec e0 = e[k];
-            a *= e0.w * v[e0.src * RS + lane];
-          }
+          for (int k = 0; k < cnt; ++k) a *= e[k].w * v[e[k].src * RS];
         } else {
-          EdgeRec e0 = e[0];
-          a = e0.w * v[e0.src * RS + lane];
-          for (int k = 1; k < cnt; ++k) {
-            e0 = e[k];
-            a = fmaxf(a, e0.w * v[e0.src * RS + lane]);
-          }
+          a = e[0].w * v[e[0].src * RS];
+          for (int k = 1; k < cnt; ++k) a = fmaxf(a, e[k].w * v[e[k].src * RS]);
         }
+        av[p * RS] = a;
+        v[p * RS] = act_apply(meta_act(n.meta), fmaf(n.resp, a, n.bias));
       }
-      av[p * RS + lane] = a;
-      v[p * RS + lane] = act_apply(meta_act(n.meta), fmaf(n.resp, a, n.bias));
     }
-    // ---- adjoints (inactive lanes carry zero adjoints throughout)
-    for (int p = 0; p < V; ++p) dv[p * RS + lane] = 0.0f;
-    for (int j = 0; j < O; ++j)
-      dv[io[I + j] * RS + lane] += active ? __ldg(gout + srow * O + j) : 0.0f;
+    // ---- adjoints (inactive lanes carry zero adjoints throughout): the
+    // pushed part starts as dL/dO
+    for (int p = 0; p < V; ++p) dv[p * RS] = 0.0f;
+    for (int o = 0; o < O; ++o)
+      dv[io[I + o] * RS] += active ? __ldg(gout + (size_t(g) * S + s) * O + o) : 0.0f;
     for (int p = V - 1; p >= 0; --p) {
       const NodeRec n = nr[p];
-      if (n.meta & META_INPUT) continue;
-      const float a = av[p * RS + lane];
+      // pulled part: sum over this position's sum/mean consumers
+      const int b = pbeg[p], en = pend[p];
+      float d0 = dv[p * RS], d1 = 0.0f;
+      int i = b;
+      for (; i + 3 < en; i += 4) {
+        const PullRec r0 = pull[i], r1 = pull[i + 1], r2 = pull[i + 2], r3 = pull[i + 3];
+        const float u0 = dv[r0.dst * RS], u1 = dv[r1.dst * RS], u2 = dv[r2.dst * RS],
+                    u3 = dv[r3.dst * RS];
+        d0 = fmaf(r0.cw, u0, d0);
+        d1 = fmaf(r1.cw, u1, d1);
+        d0 = fmaf(r2.cw, u2, d0);
+        d1 = fmaf(r3.cw, u3, d1);
+      }
+      for (; i < en; ++i) d0 = fmaf(pull[i].cw, dv[pull[i].dst * RS], d0);
+      const float d = d0 + d1;
+      if (n.meta & META_INPUT) {
+        dv[p * RS] = d;  // dL/dx
+        continue;
+      }
+      const float a = av[p * RS];
       const float z = fmaf(n.resp, a, n.bias);
-      const float u = dv[p * RS + lane] * act_deriv(meta_act(n.meta), z, v[p * RS + lane]);
-      dv[p * RS + lane] = u;  // every consumer of p sits later and is done
+      const float u = d * act_deriv(meta_act(n.meta), z, v[p * RS]);
+      dv[p * RS] = u;  // every consumer of p sits later and is done
       const int cnt = meta_cnt(n.meta), agg = meta_agg(n.meta);
-      if (cnt == 0) continue;
+      if (cnt == 0 || agg == NEAT_AGG_SUM || agg == NEAT_AGG_MEAN) continue;
+      // product / max: push into the sources' adjoints (earlier frontiers)
       const float da = u * n.resp;
       const EdgeRec *e = er + n.in_begin;
       float *aw = accw + n.in_begin;
-      if (agg == NEAT_AGG_SUM || agg == NEAT_AGG_MEAN) {
-        const float dt = agg == NEAT_AGG_MEAN ? da / float(cnt) : da;
-        // the sources of one node are distinct (duplicate edges are rejected),
-        // so four read-modify-writes can be in flight at once
-        int k = 0;
-        for (; k + 3 < cnt; k += 4) {
-          const EdgeRec e0 = e[k], e1 = e[k + 1], e2 = e[k + 2],
-                        e3 = e[k + 3];
-          const float d0 = dv[e0.src * RS + lane], d1 = dv[e1.src * RS + lane],
-                      d2 = dv[e2.src * RS + lane], d3 = dv[e3.src * RS + lane];
-          dv[e0.src * RS + lane] = fmaf(dt, e0.w, d0);
-          dv[e1.src * RS + lane] = fmaf(dt, e1.w, d1);
-          dv[e2.src * RS + lane] = fmaf(dt, e2.w, d2);
-          dv[e3.src * RS + lane] = fmaf(dt, e3.w, d3);
-        }
-        for (; k < cnt; ++k) {
-          const EdgeRec e0 = e[k];
-          dv[e0.src * RS + lane] = fmaf(dt, e0.w, dv[e0.src * RS + lane]);
-        }
-      } else if (agg == NEAT_AGG_PRODUCT) {
+      if (agg == NEAT_AGG_PRODUCT) {
         // prod_{f != k} t_f from the product of the nonzero factors and the
         // number of zero factors
         float pnz = 1.0f;
         int nz = 0;
         for (int k = 0; k < cnt; ++k) {
-          const EdgeRec e0 = e[k];
-          const float t = e0.w * v[e0.src * RS + lane];
+          const float t = e[k].w * v[e[k].src * RS];
           if (t == 0.0f) ++nz; else pnz *= t;
         }
         for (int k = 0; k < cnt; ++k) {
           const EdgeRec e0 = e[k];
-          const float t = e0.w * v[e0.src * RS + lane];
+          const float x = v[e0.src * RS];
+          const float t = e0.w * x;
           float part;
           if (nz == 0) part = pnz / t;
           else if (nz == 1) part = (t == 0.0f) ? pnz : 0.0f;
           else part = 0.0f;
           const float dt = da * part;
-          const float c = warp_sum(dt * v[e0.src * RS + lane]);
+          const float c = warp_sum(dt * x);
           if (lane == 0) aw[k] += c;
-          dv[e0.src * RS + lane] = fmaf(dt, e0.w, dv[e0.src * RS + lane]);
+          dv[e0.src * RS] = fmaf(dt, e0.w, dv[e0.src * RS]);
         }
       } else {  // max: the first (lowest connection row) edge attaining the max
         int best = 0;
         float bt = 0.0f;
         int brow = 0x7fffffff;
         for (int k = 0; k < cnt; ++k) {
-          const EdgeRec e0 = e[k];
-          const float t = e0.w * v[e0.src * RS + lane];
+          const float t = e[k].w * v[e[k].src * RS];
           const int row = __ldg(erow + n.in_begin + k);
           const bool better = (k == 0) || (t > bt) || (bt != bt && t == t) ||
                               (t == bt && row < brow);
@@ -276,21 +342,23 @@ __global__ void k_backward(Ws w, const float *__restrict__ inputs, int64_t strid
         }
         for (int k = 0; k < cnt; ++k) {
           const EdgeRec e0 = e[k];
+          const float x = v[e0.src * RS];
           const float dt = (k == best) ? da : 0.0f;
-          const float c = warp_sum(dt * v[e0.src * RS + lane]);
+          const float c = warp_sum(dt * x);
           if (lane == 0) aw[k] += c;
-          dv[e0.src * RS + lane] = fmaf(dt, e0.w, dv[e0.src * RS + lane]);
+          dv[e0.src * RS] = fmaf(dt, e0.w, dv[e0.src * RS]);
         }
       }
     }
     if (gi_out != nullptr && active)
-      for (int i = 0; i < I; ++i) gi_out[srow * I + i] = dv[io[i] * RS + lane];
+      for (int i = 0; i < I; ++i) gi_out[(size_t(g) * S + s) * I + i] = dv[io[i] * RS];
     __syncwarp();
-    // ---- cross-sample sums of this tile, lane-parallel (inactive samples
-    // have u = 0 and add nothing)
+    // ---- cross-sample sums of this tile, lane-parallel over positions and
+    // edges (inactive samples have u = 0 and add nothing)
+    const float *vw = v - lane, *aww = av - lane, *dw = dv - lane;  // warp arrays
     for (int p = lane; p < V; p += 32) {
       if (nr[p].meta & META_INPUT) continue;
-      const float *up = dv + p * RS, *ap = av + p * RS;
+      const float *up = dw + p * RS, *ap = aww + p * RS;
       float sb0 = 0.0f, sb1 = 0.0f, sr0 = 0.0f, sr1 = 0.0f;
 #pragma unroll 8
       for (int q = 0; q < 32; q += 2) {
@@ -303,9 +371,9 @@ __global__ void k_backward(Ws w, const float *__restrict__ inputs, int64_t strid
       accr[p] += sr0 + sr1;
     }
     for (int k = lane; k < E; k += 32) {
-      const int d = edst[k];
-      if (d < 0) continue;
-      const float *up = dv + d * RS, *vp = v + er[k].src * RS;
+      const int dd = edst[k];
+      if (dd < 0) continue;
+      const float *up = dw + dd * RS, *vp = vw + er[k].src * RS;
       float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
 #pragma unroll 8
       for (int q = 0; q < 32; q += 4) {
@@ -322,9 +390,9 @@ __global__ void k_backward(Ws w, const float *__restrict__ inputs, int64_t strid
   // combine the per-warp partial sums in a fixed order and scatter to rows
   const size_t ow = 3 * size_t(V) * RS;  // accumulators inside a warp block
   for (int k = threadIdx.x; k < E; k += blockDim.x) {
-    float s = 0.0f;
-    for (int ww = 0; ww < nwa; ++ww) s += wbase[ww * pw + ow + k];
-    gw_out[size_t(g) * C + erow[k]] = s;
+    float sum = 0.0f;
+    for (int ww = 0; ww < nwa; ++ww) sum += wbase[ww * pw + ow + k];
+    gw_out[size_t(g) * C + erow[k]] = sum;
   }
   const int32_t *prow = w.prow + size_t(g) * N;
   for (int p = threadIdx.x; p < V; p += blockDim.x) {
@@ -350,19 +418,20 @@ cudaError_t launch_backward(const Ws &w, const float *inputs, int64_t stride, in
                             const float *grad_out, const float *saved, float *gw, float *gb,
                             float *gr, float *gi, int warps, int smem_bytes, cudaStream_t st) {
   if (w.P == 0) return cudaSuccess;
+  const dim3 grid(unsigned(w.P)), block(unsigned(warps * 32));
   if (saved != nullptr)
-    k_backward<true><<<w.P, warps * 32, smem_bytes, st>>>(w, inputs, stride, S, grad_out, saved,
-                                                          gw, gb, gr, gi, smem_bytes);
+    k_backward<true><<<grid, block, smem_bytes, st>>>(w, inputs, stride, S, grad_out, saved, gw,
+                                                      gb, gr, gi, smem_bytes);
   else
-    k_backward<false><<<w.P, warps * 32, smem_bytes, st>>>(w, inputs, stride, S, grad_out,
-                                                           nullptr, gw, gb, gr, gi, smem_bytes);
+    k_backward<false><<<grid, block, smem_bytes, st>>>(w, inputs, stride, S, grad_out, nullptr,
+                                                       gw, gb, gr, gi, smem_bytes);
   return cudaGetLastError();
 }
 
 cudaError_t backward_set_smem_limit(int bytes) {
   cudaError_t e = set_dyn_smem_limit(k_backward<true>, bytes);
-  if (e != cudaSuccess) return e;
-  return set_dyn_smem_limit(k_backward<false>, bytes);
+  if (e == cudaSuccess) e = set_dyn_smem_limit(k_backward<false>, bytes);
+  return e;
 }
 
 }  // namespace neat

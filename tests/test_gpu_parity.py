@@ -224,7 +224,7 @@ def test_uneven_full_population_sampled_genomes():
 
 @pytest.mark.parametrize("stored", [True, False])
 @pytest.mark.parametrize("name,P,S", [("differentiation", 96, 77), ("locomotion", 48, 40),
-                                      ("hyperneat", 32, 20)])
+                                      ("hyperneat", 32, 20), ("differentiation", 40, 300)])
 def test_backward_parity(name, P, S, stored):
     nodes, conns, spec, x = _fwd_case(name, P, S, seed=5)
     plan = _plan(spec, P)
@@ -241,6 +241,36 @@ def test_backward_parity(name, P, S, stored):
     compare_grads(gb.cpu().numpy(), rb, "grad_bias")
     compare_grads(gr.cpu().numpy(), rr, "grad_response")
     compare_grads(gi.cpu().numpy(), ri, "grad_inputs")
+
+
+@pytest.mark.parametrize("S", [77, 300])
+def test_backward_parity_every_aggregation(S):
+    """Product and max nodes (per-sample factors, summed with warp reductions
+    during the reverse walk) next to sum and mean nodes, with kinked
+    activations (relu, abs); S = 77 and 300 leave ragged last tiles."""
+    from workloads import GenomeSpec, make_population
+    spec = GenomeSpec(I=4, O=2, N=32, C=128, hidden=(4, 20), E_uniform=(12, 80),
+                      acts=("tanh", "sigmoid", "relu", "abs", "sin", "identity"),
+                      aggs=("sum", "product", "max", "mean"), w_std=0.8, b_std=0.3,
+                      r_mean=1.0, r_std=0.3)
+    P = 48
+    nodes, conns = make_population(spec, P, seed=21)
+    x = np.random.default_rng(4).uniform(-1, 1, (P, S, spec.I)).astype(np.float32)
+    go = np.random.default_rng(6).standard_normal((P, S, spec.O)).astype(np.float32)
+    plan = _plan(spec, P)
+    plan.transform(_dev(nodes), _dev(conns))
+    xd = _dev(x)
+    rw, rb, rr, ri = oracle.backward(nodes, conns, x, spec.I, spec.O, go)
+    for stored in (True, False):
+        saved = None
+        if stored:
+            saved = torch.empty((P, spec.N, S), device="cuda")
+            plan.forward(xd, saved=saved)
+        gw, gb, gr, gi = plan.backward(xd, _dev(go), saved=saved)
+        compare_grads(gw.cpu().numpy(), rw, f"grad_weight stored={stored}")
+        compare_grads(gb.cpu().numpy(), rb, f"grad_bias stored={stored}")
+        compare_grads(gr.cpu().numpy(), rr, f"grad_response stored={stored}")
+        compare_grads(gi.cpu().numpy(), ri, f"grad_inputs stored={stored}")
 
 
 def test_backward_and_forward_are_deterministic():
