@@ -44,27 +44,33 @@ UNIT = "conn-evals/s"
 PEAKS_FALLBACK = {"hbm_gbs": 6400.0, "source": "fallback"}
 
 # DRAM bytes (read + write) per launch of the timed kernel from one ncu
-# capture (summaries under profiles/), keyed by workload and kernel, with the
-# hash prefix of the kernel sources they were taken on: the figure is reported
-# only while those sources are unchanged.
+# capture (summaries under profiles/), keyed by workload and kernel: (bytes,
+# population of the capture, hash prefixes of the kernel sources it was taken
+# on).  A capture on a smaller population is scaled by population (the
+# traffic grows with the genomes processed); the figure is reported only
+# while those sources are unchanged.
+_INTERNAL = ("paper_2504_08339_b300/csrc/neat_internal.cuh", "cae31d2d0b3f29d1")
 TRAFFIC = {
-    ("locomotion", "k_forward_lvl"): (32517376, {
-        "paper_2504_08339_b300/csrc/level.cu": "916a30680134c047",
-        "paper_2504_08339_b300/csrc/neat_internal.cuh": "3655c1d323cda791"}),
+    ("locomotion", "k_forward_lvl"): (32599296, 10000, dict([
+        ("paper_2504_08339_b300/csrc/level.cu", "d3c4990b7be89b2e"), _INTERNAL])),
+    ("uneven", "k_forward_sp"): (116634112, 2048, dict([
+        ("paper_2504_08339_b300/csrc/forward.cu", "7cdea6ff82e6aa42"), _INTERNAL])),
+    ("differentiation", "k_backward"): (359581440, 512, dict([
+        ("paper_2504_08339_b300/csrc/backward.cu", "8524e28e5af10c82"), _INTERNAL])),
 }
 
 
-def measured_traffic(name, kernel):
+def measured_traffic(name, kernel, pop):
     import hashlib
     rec = TRAFFIC.get((name, kernel))
     if rec is None:
         return None
-    nbytes, srcs = rec
+    nbytes, ref_pop, srcs = rec
     for path, prefix in srcs.items():
         with open(os.path.join(ROOT, path), "rb") as f:
             if hashlib.sha256(f.read()).hexdigest()[:16] != prefix:
                 return None
-    return nbytes
+    return int(round(nbytes * pop / ref_pop))
 
 
 def load_peaks():
@@ -113,6 +119,9 @@ def parse_args():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--pop", type=int, default=None,
+                    help="population override (profiling captures and small cases; the line's "
+                         "config then says so)")
     return ap.parse_args()
 
 
@@ -217,9 +226,11 @@ def enabled_counts(nodes, conns):
     return en.sum(axis=1).astype(np.int64), (~np.isnan(nodes[..., 0])).sum(axis=1).astype(np.int64)
 
 
-def workload(name, seed):
+def workload(name, seed, pop=None):
     from workloads import CONFIGS, make_population
-    cfg = CONFIGS[name]
+    cfg = dict(CONFIGS[name])
+    if pop is not None:
+        cfg["P"] = pop
     spec = cfg["spec"]
     nodes, conns = make_population(spec, cfg["P"], seed=seed)
     return cfg, spec, nodes, conns
@@ -300,7 +311,7 @@ def bench_ours(args, rank, world, local, pg):
     dev = torch.device("cuda", local)
     peaks = load_peaks()
     name = args.config
-    cfg, spec, nodes, conns = workload(name, args.seed + rank)
+    cfg, spec, nodes, conns = workload(name, args.seed + rank, args.pop)
     P = cfg["P"]
     E, Vn = enabled_counts(nodes, conns)
     plan = Plan(P, spec.N, spec.C, spec.I, spec.O, device=dev)
@@ -339,23 +350,34 @@ def bench_ours(args, rank, world, local, pg):
         out = torch.empty((P, S, spec.O), device=dev)
         go = torch.empty((P, S, spec.O), device=dev)
         tr = plan.transform(d_nodes, d_conns)
+        # ev[0]: the backward (the dominant kernel, the roofline's); ev_f: the forward
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))]
+        ev_f = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
 
         def run():
             plan.transform(d_nodes, d_conns, out=tr)
-            ev[0][0].record()
+            ev_f[0].record()
             plan.forward(d_x, out=out, saved=saved)
-            ev[0][1].record()
+            ev_f[1].record()
             torch.sub(out[..., 0], d_y, out=go[..., 0])
             go.mul_(2.0 / S)
-            return plan.backward(d_x, go, saved=saved)
+            ev[0][0].record()
+            g = plan.backward(d_x, go, saved=saved)
+            ev[0][1].record()
+            return g
 
         units_per_step = float(E.sum()) * S
         launches_per_step += 2
         fwd_launches = 1
         ro = None
-        alg_bytes = float((8 * E + 12 * Vn).sum() + 4 * S * (spec.I + spec.O) + 4 * S * spec.N * P)
-        chip_bytes = float(4 * S * (E + Vn).sum())
+        # backward: program again, grads out, saved aggregates in, dL/dO in,
+        # dL/dx out, the shared inputs in; on chip 12 S E + 8 S V
+        alg_bytes = float((8 * E + 12 * Vn).sum() + (4 * E + 8 * Vn).sum() + 4 * S * Vn.sum() +
+                          4 * S * spec.O * P + 4 * S * spec.I * P + 4 * S * spec.I)
+        chip_bytes = float((12 * S * E + 8 * S * Vn).sum())
+        fwd_hbm = float((8 * E + 12 * Vn).sum() + 4 * S * spec.I + 4 * S * spec.O * P +
+                        4 * S * Vn.sum())
+        fwd_chip = float(4 * S * (E + Vn).sum())
     else:  # hyperneat
         d_nodes = torch.from_numpy(nodes).to(dev)
         d_conns = torch.from_numpy(conns).to(dev)
@@ -413,12 +435,16 @@ def bench_ours(args, rank, world, local, pg):
         if name == "hyperneat":
             kernel = "k_hyperneat"
         elif name == "differentiation":
-            kernel = "k_forward_sp"  # forward with the saved aggregates
+            kernel = "k_backward"
+            fwd_us = 1e3 * ev_f[0].elapsed_time(ev_f[1])
+            extra["forward"] = roofline(fwd_hbm, fwd_chip, fwd_us, peaks, dev)
+            extra["forward"].update({"kernel": "k_forward_sp (with the saved aggregates)",
+                                     "launch_us": round(fwd_us, 3)})
         else:
             tune = plan.get_tuning()
             kernel = "k_forward_lvl" if S <= tune["small_s_max"] else "k_forward_sp"
         roof = roofline(alg_bytes, chip_bytes, avg_launch_us, peaks, dev)
-        roof.update({"traffic": measured_traffic(name, kernel), "kernel": kernel,
+        roof.update({"traffic": measured_traffic(name, kernel, P), "kernel": kernel,
                      "avg_launch_us": round(avg_launch_us, 3), "launches_timed": len(launch_ms)})
         extra["launch_us_min"] = round(1e3 * min(launch_ms), 3)
         extra["launch_us_max"] = round(1e3 * max(launch_ms), 3)
@@ -487,6 +513,7 @@ def bench_ours(args, rank, world, local, pg):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded generators; random genomes shaped like the workload)",
         "config": {"workload": describe(name, cfg, spec), "name": name, "pop": P,
+                   "pop_override": args.pop is not None,
                    "enabled_conns_per_genome_mean": round(float(E.mean()), 2),
                    "valid_nodes_per_genome_mean": round(float(Vn.mean()), 2),
                    "form": "batched: persistent size-sorted queue over ragged-packed programs, "
@@ -506,7 +533,7 @@ def bench_reference(args, rank, world):
     if rank != 0:
         return
     name = args.config
-    cfg, spec, nodes, conns = workload(name, args.seed)
+    cfg, spec, nodes, conns = workload(name, args.seed, args.pop)
     budget = {"locomotion": 8, "uneven": 150, "differentiation": 4, "hyperneat": 1, "tiny": None}[name]
     for _ in range(max(3, args.warmup)):
         cpu_baseline(name, cfg, spec, nodes, conns, args.seed, budget)
@@ -524,7 +551,8 @@ def bench_reference(args, rank, world):
         "steps": args.steps, "warmup": max(3, args.warmup),
         "ms_per_step": round(1e3 * secs / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": describe(name, cfg, spec), "name": name, "pop": cfg["P"]},
+        "config": {"workload": describe(name, cfg, spec), "name": name, "pop": cfg["P"],
+                   "pop_override": args.pop is not None},
         "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": rec["sample"], "value": value,
                          "unit": UNIT},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
