@@ -142,6 +142,22 @@ __device__ __forceinline__ void node_agg(const NodeRec &n, const EdgeRec *__rest
   }
 }
 
+// Value (and saved aggregate) of the node at position p for this lane's SPL
+// samples; inputs are left alone.
+template <bool SAVE, int SPL>
+__device__ __forceinline__ void eval_node(const NodeRec &n, int p, const EdgeRec *__restrict__ er,
+                                          float *vl, float *const (&scol)[SPL], int S) {
+  if (n.meta & META_INPUT) return;
+  float a[SPL];
+  node_agg<SPL>(n, er, vl, a);
+  const int act = meta_act(n.meta);
+#pragma unroll
+  for (int j = 0; j < SPL; ++j) {
+    vl[(p * SPL + j) * 32] = act_apply(act, fmaf(n.resp, a[j], n.bias));
+    if (SAVE && scol[j] != nullptr) scol[j][size_t(p) * S] = a[j];
+  }
+}
+
 // Walk positions [0, V) of a ragged program (inputs already in v); vl = v +
 // lane.  SAVE: scol[j][p * S] (scol[j] nullptr for an inactive sample)
 // receives the aggregate of position p for sample j.
@@ -149,21 +165,11 @@ template <bool SAVE, int SPL>
 __device__ __forceinline__ void walk_program(const NodeRec *__restrict__ nr,
                                              const EdgeRec *__restrict__ er, int V, float *vl,
                                              float *const (&scol)[SPL], int S) {
-  for (int p = 0; p < V; ++p) {
-    const NodeRec n = ld_node(nr + p);
-    if (n.meta & META_INPUT) continue;
-    float a[SPL];
-    node_agg<SPL>(n, er, vl, a);
-    const int act = meta_act(n.meta);
-#pragma unroll
-    for (int j = 0; j < SPL; ++j) {
-      vl[(p * SPL + j) * 32] = act_apply(act, fmaf(n.resp, a[j], n.bias));
-      if (SAVE && scol[j] != nullptr) scol[j][size_t(p) * S] = a[j];
-    }
-  }
+  for (int p = 0; p < V; ++p) eval_node<SAVE, SPL>(ld_node(nr + p), p, er, vl, scol, S);
 }
 
-__device__ __forceinline__ void grid_done_reset(uint32_t *item_ctr, uint32_t *done_ctr) {
+__device__ __forceinline__ void grid_done_reset(uint32_t *item_ctr, uint32_t *done_ctr,
+                                                uint32_t *extra_ctr = nullptr) {
   // the last CTA to finish returns the queue counters to zero, so every launch
   // (including graph replays) starts from a clean queue
   __syncthreads();
@@ -172,6 +178,7 @@ __device__ __forceinline__ void grid_done_reset(uint32_t *item_ctr, uint32_t *do
     const unsigned t = atomicAdd(done_ctr, 1u);
     if (t == gridDim.x - 1) {
       atomicExch(item_ctr, 0u);
+      if (extra_ctr != nullptr) atomicExch(extra_ctr, 0u);
       atomicExch(done_ctr, 0u);
     }
   }
@@ -181,24 +188,101 @@ __device__ __forceinline__ void grid_done_reset(uint32_t *item_ctr, uint32_t *do
 // samples tile * 32 * SPL + j * 32 + l, j < SPL.  The values of a genome with
 // V <= vcap live in this warp's shared-memory array, the others in the warp's
 // slot of the workspace value array (L1/L2-resident while in use).
+//
+// With `coop`, the items of the queue's first counters[CTR_SP_NBIG] genomes
+// (the most expensive ones, E + 2V >= SP_COOP_COST) are taken by whole CTAs:
+// the CTA's warps split each frontier's positions (no position of a frontier
+// reads another's value) with a barrier between frontiers, in the slot of the
+// CTA's first warp.  One warp walking such a genome alone would finish long
+// after the rest of the grid.  The remaining items are claimed per warp.
 template <int SPL>
-__global__ void k_forward_sp(Ws w, const float *__restrict__ inputs, int64_t stride, int S,
+__global__ void __launch_bounds__(512, 3)
+    k_forward_sp(Ws w, const float *__restrict__ inputs, int64_t stride, int S,
                              float *__restrict__ out, float *__restrict__ saved, int tiles,
-                             int vcap) {
+                             int vcap, int coop) {
   constexpr int RS = 32 * SPL;
   extern __shared__ __align__(16) float smv[];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  __shared__ int s_item;
+  __shared__ int s_lstart[NEAT_MAX_NODES + 1];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int N = w.N, I = w.I, O = w.O;
   float *vs = smv + size_t(wid) * vcap * RS;
-  const size_t slot = size_t(blockIdx.x) * (blockDim.x >> 5) + wid;
+  const size_t slot = size_t(blockIdx.x) * nw + wid;
   float *vg = (w.sp_scratch != nullptr && (slot + 1) * size_t(N) * RS <= w.sp_scratch_floats)
                   ? w.sp_scratch + slot * size_t(N) * RS
                   : nullptr;
   const int total = w.P * tiles;
+  const int big_items = coop ? min(total, int(w.counters[CTR_SP_NBIG]) * tiles) : 0;
+
+  // ---- CTA-wide items (vg of warp 0 is the CTA's slot: the grid is sized
+  // so that every warp of it has one)
+  float *vc = (w.sp_scratch != nullptr &&
+               (size_t(blockIdx.x) * nw + 1) * size_t(N) * RS <= w.sp_scratch_floats)
+                  ? w.sp_scratch + size_t(blockIdx.x) * nw * size_t(N) * RS
+                  : nullptr;
+  while (big_items > 0) {
+    if (threadIdx.x == 0) s_item = int(atomicAdd(w.counters + CTR_FWD_BIG, 1u));
+    __syncthreads();
+    const int item = s_item;
+    __syncthreads();
+    if (item >= big_items) break;
+    const int q = item / tiles, tile = item - q * tiles;
+    const int g = w.qorder[q];
+    const GenomeHdr h = w.hdr[g];
+    int sj[SPL];
+#pragma unroll
+    for (int j = 0; j < SPL; ++j) sj[j] = tile * RS + j * 32 + lane;
+    if (vc == nullptr || h.L > NEAT_MAX_NODES) {  // no slot: never with a plan's shape
+      if (threadIdx.x == 0) atomicOr(w.counters + CTR_ERR, ERR_SP_NO_SCRATCH);
+      if (wid == 0)
+#pragma unroll
+        for (int j = 0; j < SPL; ++j)
+          if (sj[j] < S)
+            for (int o = 0; o < O; ++o) out[(size_t(g) * S + sj[j]) * O + o] = qnan();
+      continue;
+    }
+    const int32_t *lay = w.player + size_t(g) * N;
+    for (int p = threadIdx.x; p < h.V; p += blockDim.x)
+      if (p == 0 || lay[p - 1] != lay[p]) s_lstart[lay[p]] = p;
+    if (threadIdx.x == 0) s_lstart[h.L] = h.V;
+    float *vl = vc + lane;
+    const int32_t *io = w.pio + size_t(g) * (I + O);
+    for (int i = wid; i < I; i += nw)
+#pragma unroll
+      for (int j = 0; j < SPL; ++j) {
+        const bool active = sj[j] < S;
+        const float *in = inputs + size_t(g) * stride + size_t(active ? sj[j] : 0) * I;
+        vl[(io[i] * SPL + j) * 32] = active ? __ldg(in + i) : 0.0f;
+      }
+    __syncthreads();
+    const NodeRec *nr = w.knode + h.node_off;
+    const EdgeRec *er = w.kedge + h.edge_off;
+    float *scol[SPL];
+#pragma unroll
+    for (int j = 0; j < SPL; ++j)
+      scol[j] = (saved != nullptr && sj[j] < S) ? saved + size_t(g) * N * S + sj[j] : nullptr;
+    for (int l = 0; l < h.L; ++l) {
+      const int p1 = s_lstart[l + 1];
+      for (int p = s_lstart[l] + wid; p < p1; p += nw) {
+        if (saved != nullptr)
+          eval_node<true, SPL>(ld_node(nr + p), p, er, vl, scol, S);
+        else
+          eval_node<false, SPL>(ld_node(nr + p), p, er, vl, scol, S);
+      }
+      __syncthreads();
+    }
+    for (int o = wid; o < O; o += nw)
+#pragma unroll
+      for (int j = 0; j < SPL; ++j)
+        if (sj[j] < S) out[(size_t(g) * S + sj[j]) * O + o] = vl[(io[I + o] * SPL + j) * 32];
+    __syncthreads();  // the slot and s_lstart are reused by the next item
+  }
+
+  // ---- per-warp items
   for (;;) {
     int item = 0;
     if (lane == 0) item = int(atomicAdd(w.counters + CTR_FWD_ITEM, 1u));
-    item = __shfl_sync(0xffffffffu, item, 0);
+    item = __shfl_sync(0xffffffffu, item, 0) + big_items;
     if (item >= total) break;
     const int q = item / tiles, tile = item - q * tiles;
     const int g = w.qorder[q];
@@ -241,7 +325,7 @@ __global__ void k_forward_sp(Ws w, const float *__restrict__ inputs, int64_t str
         for (int o = 0; o < O; ++o)
           out[(size_t(g) * S + sj[j]) * O + o] = vl[(io[I + o] * SPL + j) * 32];
   }
-  grid_done_reset(w.counters + CTR_FWD_ITEM, w.counters + CTR_FWD_DONE);
+  grid_done_reset(w.counters + CTR_FWD_ITEM, w.counters + CTR_FWD_DONE, w.counters + CTR_FWD_BIG);
 }
 
 __global__ void __launch_bounds__(32) k_forward_plain(Ws w, const float *__restrict__ inputs,
@@ -338,11 +422,11 @@ cudaError_t launch_forward_sp(const Ws &w, const float *inputs, int64_t stride, 
   const dim3 grid(unsigned(sh.grid)), block(unsigned(sh.warps * 32));
   switch (sh.spl) {
     case 1: k_forward_sp<1><<<grid, block, smem, st>>>(w, inputs, stride, S, outputs, saved, tiles,
-                                                       sh.vcap); break;
+                                                       sh.vcap, sh.coop); break;
     case 2: k_forward_sp<2><<<grid, block, smem, st>>>(w, inputs, stride, S, outputs, saved, tiles,
-                                                       sh.vcap); break;
+                                                       sh.vcap, sh.coop); break;
     case 4: k_forward_sp<4><<<grid, block, smem, st>>>(w, inputs, stride, S, outputs, saved, tiles,
-                                                       sh.vcap); break;
+                                                       sh.vcap, sh.coop); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

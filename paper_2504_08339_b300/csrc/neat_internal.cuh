@@ -255,7 +255,14 @@ inline Ws make_ws(void *base, const Layout &L, int P, int N, int C, int I, int O
 
 // counters[] slots
 constexpr int CTR_FWD_ITEM = 0, CTR_FWD_DONE = 1, CTR_HN_ITEM = 2, CTR_HN_DONE = 3,
-              CTR_LVL_ITEM = 4, CTR_LVL_DONE = 5, CTR_NBATCH = 8, CTR_ERR = 9;
+              CTR_LVL_ITEM = 4, CTR_LVL_DONE = 5, CTR_FWD_BIG = 6, CTR_SP_NBIG = 7,
+              CTR_NBATCH = 8, CTR_ERR = 9;
+// genomes of at least this cost (E + 2V) are evaluated by a whole CTA in the
+// sample-parallel forward (counters[CTR_SP_NBIG] of them, a queue prefix)
+#ifndef NEAT_SP_COOP_COST
+#define NEAT_SP_COOP_COST 2048
+#endif
+constexpr int SP_COOP_COST = NEAT_SP_COOP_COST;
 // error bits in counters[CTR_ERR]
 constexpr uint32_t ERR_TMA_TIMEOUT = 1u, ERR_SP_NO_SCRATCH = 2u;
 
@@ -299,6 +306,7 @@ cudaError_t launch_queue_build(const Ws &w, int mode, cudaStream_t st);
 // warp's workspace slot (vcap 0: every genome in the workspace, N: none).
 struct SpShape {
   int warps, spl, vcap, grid;
+  int coop;  // CTA-wide evaluation of the most expensive genomes (needs value slots)
 };
 cudaError_t launch_forward_sp(const Ws &w, const float *inputs, int64_t stride, int S,
                               float *outputs, float *saved, const SpShape &sh, cudaStream_t st);

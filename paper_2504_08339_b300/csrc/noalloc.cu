@@ -116,7 +116,7 @@ extern "C" neat_status neat_forward_noalloc(const float *nodes, const float *con
     const int64_t items = int64_t(P) * ((S + 31) / 32);
     const int grid = int(std::max<int64_t>(
         1, std::min<int64_t>(int64_t(g_sm_count[dev]) * occ, (items + warps - 1) / warps)));
-    const neat::SpShape sh{warps, 1, N, grid};
+    const neat::SpShape sh{warps, 1, N, grid, 0};
     e = neat::launch_forward_sp(w, inputs, in_pop_stride, S, outputs, nullptr, sh, stream);
   }
   return e == cudaSuccess ? NEAT_OK : NEAT_ERR_CUDA;

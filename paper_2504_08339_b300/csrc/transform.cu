@@ -413,15 +413,22 @@ __global__ void __launch_bounds__(256) k_rank(Ws w, int mode, int32_t *__restric
 // Exclusive scans of V and E in queue order -> ragged offsets (one CTA).
 __global__ void __launch_bounds__(1024) k_offsets(Ws w) {
   __shared__ int wv[33], we[33];
+  __shared__ int nbig;
   const int P = w.P, T = blockDim.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int per = (P + T - 1) / T;
   const int b = min(tid * per, P), e = min(b + per, P);
-  int sv = 0, se = 0;
+  if (tid == 0) nbig = 0;
+  __syncthreads();
+  int sv = 0, se = 0, sb = 0;
   for (int q = b; q < e; ++q) {
     const GenomeHdr h = w.hdr[w.qorder[q]];
     sv += h.V;
     se += h.E;
+    // the most expensive genomes (a prefix of the cost-sorted queue) go to
+    // whole CTAs in the sample-parallel forward
+    sb += (h.status == 0u && h.E + 2 * h.V >= SP_COOP_COST) ? 1 : 0;
   }
+  if (sb) atomicAdd(&nbig, sb);
   int xv = sv, xe = se;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
@@ -441,6 +448,7 @@ __global__ void __launch_bounds__(1024) k_offsets(Ws w) {
     we[lane] = c;
   }
   __syncthreads();
+  if (tid == 0) w.counters[CTR_SP_NBIG] = uint32_t(nbig);
   int ov = (wid > 0 ? wv[wid - 1] : 0) + xv - sv;
   int oe = (wid > 0 ? we[wid - 1] : 0) + xe - se;
   for (int q = b; q < e; ++q) {
