@@ -16,6 +16,10 @@ Parity status of each function (what pins it, in tests/test_oracle_*.py):
   backward   -- central finite differences of the forward; MLP special case
                 against numpy back-propagation.
   hyperneat  -- single-node CPPNs with closed forms over the grid.
+  forward_recurrent -- linear (identity, sum) recurrent genomes against numpy
+                matrix powers, a self-loop closed form, equality with the
+                feed-forward forward on DAGs once T reaches their depth,
+                status bits without CYCLE.
 """
 from __future__ import annotations
 
@@ -58,6 +62,8 @@ def _load():
             lib.or_transform.argtypes = [i32, i32, i32, i32, i32, P, P, P, P, P, P]
             lib.or_forward.argtypes = [i32, i32, i32, i32, i32, P, P, P, i64, i32, P, P, P]
             lib.or_backward.argtypes = [i32, i32, i32, i32, i32, P, P, P, i64, i32, P, P, P, P, P]
+            lib.or_forward_recurrent.argtypes = [i32, i32, i32, i32, i32, P, P, P, i64, i32, i32,
+                                                 P, P, P]
             lib.or_hyperneat.argtypes = [i32, i32, i32, P, P, i32, dbl, P, i64, P, P, P]
             for f in (lib.or_transform, lib.or_forward, lib.or_backward, lib.or_hyperneat):
                 f.restype = ctypes.c_int
@@ -123,6 +129,26 @@ def forward(nodes, conns, inputs, I, O, with_bound=False, with_values=False):
         res.append(bnd)
     if with_values:
         res.append(vals)
+    return res[0] if len(res) == 1 else tuple(res)
+
+
+def forward_recurrent(nodes, conns, inputs, I, O, T, with_bound=False, with_status=False):
+    """Recurrent calculation over T synchronous iterations (reading R11):
+    outputs [P,S,O] f64 (and bound [P,S,O], status [P] u32 when asked)."""
+    nodes, conns = _f64(nodes), _f64(conns)
+    P, N, C = _shapes(nodes, conns)
+    inputs, stride, S = _inputs(inputs, P, I)
+    out = np.empty((P, S, O), np.float64)
+    bnd = np.empty((P, S, O), np.float64) if with_bound else None
+    st = np.empty(P, np.uint32) if with_status else None
+    rc = _load().or_forward_recurrent(P, N, C, I, O, _ptr(nodes), _ptr(conns), _ptr(inputs),
+                                      stride, S, int(T), _ptr(out), _ptr(bnd), _ptr(st))
+    assert rc == 0, rc
+    res = [out]
+    if with_bound:
+        res.append(bnd)
+    if with_status:
+        res.append(st)
     return res[0] if len(res) == 1 else tuple(res)
 
 

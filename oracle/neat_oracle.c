@@ -44,6 +44,11 @@
  *   R9 HyperNEAT query: cell c = j*G + i has coordinates
  *      (-1 + 2i/(G-1), -1 + 2j/(G-1)); query (s, d) feeds
  *      (x_s, y_s, x_d, y_d, 1); the stored weight is o if |o| > thresh else 0.
+ *   R11 recurrent ("concurrent", Sec. 3.3 names the network type without
+ *      its calculation): T synchronous iterations; v^0 = inputs on the input
+ *      rows and 0 elsewhere; in iteration t every valid non-input node takes
+ *      act(b + r * agg(w * v^{t-1}[src])) while the inputs stay clamped; the
+ *      outputs are v^T.  Cycles and self-loops are allowed (no CYCLE bit).
  *
  * All arithmetic is double precision.  The forward can also return a first
  * order bound on the error an fp32 evaluation of the same network may make
@@ -349,6 +354,71 @@ static double act_lip(int a, double z, double h) {
 
 #define U32 (1.0 / 16777216.0) /* fp32 unit roundoff 2^-24 */
 
+/* One node of the calculation stage (Sec. 3.3): a = agg over the node's
+ * enabled incoming connections (ascending row) of w * vin[src], z = b + r a,
+ * v = act(z).  bin / bout (nullable): fp32 error bound of the inputs read and
+ * of the result (first order; unit roundoff 2^-24, any summation order). */
+static void eval_node(const genome_t *g, int r, const double *vin, const double *bin,
+                      double *v_out, double *a_out, double *z_out, double *b_out) {
+  const int beg = g->in_beg[r], n = g->in_beg[r + 1] - beg;
+  const int want_b = bin != NULL && b_out != NULL;
+  double acc = 0.0, sabs = 0.0, eb = 0.0;
+  if (n > 0) {
+    /* f_c on every incoming enabled connection, then f_agg */
+    if (g->agg[r] == G_SUM || g->agg[r] == G_MEAN) {
+      acc = 0.0;
+      for (int q = 0; q < n; ++q) {
+        int e = g->in_list[beg + q];
+        double t = g->ew[e] * vin[g->esrc[e]];
+        acc += t;
+        if (want_b) { sabs += fabs(t); eb += fabs(g->ew[e]) * bin[g->esrc[e]] + U32 * fabs(t); }
+      }
+      if (want_b) eb += (n * U32 / (1.0 - n * U32)) * sabs;
+      if (g->agg[r] == G_MEAN) { acc /= n; if (want_b) eb = eb / n + U32 * fabs(acc); }
+    } else if (g->agg[r] == G_PRODUCT) {
+      acc = 1.0;
+      for (int q = 0; q < n; ++q) {
+        int e = g->in_list[beg + q];
+        acc *= g->ew[e] * vin[g->esrc[e]];
+      }
+      if (want_b) {
+        /* first order: sum_e beta_e * prod_{f != e} |t_f|, plus 2n roundings */
+        for (int q = 0; q < n; ++q) {
+          int e = g->in_list[beg + q];
+          double others = 1.0;
+          for (int q2 = 0; q2 < n; ++q2)
+            if (q2 != q) { int f = g->in_list[beg + q2]; others *= fabs(g->ew[f] * vin[g->esrc[f]]); }
+          eb += fabs(g->ew[e]) * bin[g->esrc[e]] * others;
+        }
+        eb += 2.0 * n * U32 * fabs(acc) * 1.01;
+      }
+    } else { /* G_MAX: fmax fold */
+      for (int q = 0; q < n; ++q) {
+        int e = g->in_list[beg + q];
+        double t = g->ew[e] * vin[g->esrc[e]];
+        acc = (q == 0) ? t : fmax(acc, t);
+        if (want_b) eb = fmax(eb, fabs(g->ew[e]) * bin[g->esrc[e]] + U32 * fabs(t));
+      }
+    }
+  }
+  const double z = g->bias[r] + g->resp[r] * acc;
+  const double v = act_f(g->act[r], z);
+  *a_out = acc;
+  *z_out = z;
+  *v_out = v;
+  if (want_b) {
+    double bz = fabs(g->resp[r]) * eb + U32 * fabs(g->resp[r] * acc) + U32 * fabs(z);
+    double lip = act_lip(g->act[r], z, bz);
+    double ef = 0.0; /* error of the fp32 activation itself */
+    switch (g->act[r]) {
+      case A_SIGMOID: case A_TANH: case A_SIN: ef = 8.0 * U32 * fabs(v); break;
+      case A_GAUSS: ef = (8.0 + z * z) * 2.0 * U32 * fabs(v); break;
+      default: ef = 0.0;
+    }
+    *b_out = lip * bz + ef + 1e-300;
+  }
+}
+
 /* Sec. 3.3 calculation for one input vector.  v, a, z are per row; bnd (may be
  * NULL) receives the fp32 error bound per row; in_bnd is the error already in
  * the inputs (0 for exact fp32 inputs). */
@@ -360,61 +430,29 @@ static void forward_one(const genome_t *g, const double *x, double in_bnd, doubl
   for (int p = 0; p < g->nord; ++p) {
     const int r = g->order[p];
     if (r < I) continue;
-    const int beg = g->in_beg[r], n = g->in_beg[r + 1] - beg;
-    double acc = 0.0, sabs = 0.0, eb = 0.0;
-    if (n > 0) {
-      /* f_c on every incoming enabled connection, then f_agg */
-      if (g->agg[r] == G_SUM || g->agg[r] == G_MEAN) {
-        acc = 0.0;
-        for (int q = 0; q < n; ++q) {
-          int e = g->in_list[beg + q];
-          double t = g->ew[e] * v[g->esrc[e]];
-          acc += t;
-          if (bnd) { sabs += fabs(t); eb += fabs(g->ew[e]) * bnd[g->esrc[e]] + U32 * fabs(t); }
-        }
-        if (bnd) eb += (n * U32 / (1.0 - n * U32)) * sabs;
-        if (g->agg[r] == G_MEAN) { acc /= n; if (bnd) eb = eb / n + U32 * fabs(acc); }
-      } else if (g->agg[r] == G_PRODUCT) {
-        acc = 1.0;
-        for (int q = 0; q < n; ++q) {
-          int e = g->in_list[beg + q];
-          acc *= g->ew[e] * v[g->esrc[e]];
-        }
-        if (bnd) {
-          /* first order: sum_e beta_e * prod_{f != e} |t_f|, plus 2n roundings */
-          for (int q = 0; q < n; ++q) {
-            int e = g->in_list[beg + q];
-            double others = 1.0;
-            for (int q2 = 0; q2 < n; ++q2)
-              if (q2 != q) { int f = g->in_list[beg + q2]; others *= fabs(g->ew[f] * v[g->esrc[f]]); }
-            eb += fabs(g->ew[e]) * bnd[g->esrc[e]] * others;
-          }
-          eb += 2.0 * n * U32 * fabs(acc) * 1.01;
-        }
-      } else { /* G_MAX: fmax fold */
-        for (int q = 0; q < n; ++q) {
-          int e = g->in_list[beg + q];
-          double t = g->ew[e] * v[g->esrc[e]];
-          acc = (q == 0) ? t : fmax(acc, t);
-          if (bnd) eb = fmax(eb, fabs(g->ew[e]) * bnd[g->esrc[e]] + U32 * fabs(t));
-        }
-      }
-    }
-    a[r] = acc;
-    z[r] = g->bias[r] + g->resp[r] * acc;
-    v[r] = act_f(g->act[r], z[r]);
-    if (bnd) {
-      double bz = fabs(g->resp[r]) * eb + U32 * fabs(g->resp[r] * acc) + U32 * fabs(z[r]);
-      double lip = act_lip(g->act[r], z[r], bz);
-      double ef = 0.0; /* error of the fp32 activation itself */
-      switch (g->act[r]) {
-        case A_SIGMOID: case A_TANH: case A_SIN: ef = 8.0 * U32 * fabs(v[r]); break;
-        case A_GAUSS: ef = (8.0 + z[r] * z[r]) * 2.0 * U32 * fabs(v[r]); break;
-        default: ef = 0.0;
-      }
-      bnd[r] = lip * bz + ef + 1e-300;
-    }
+    eval_node(g, r, v, bnd, &v[r], &a[r], &z[r], bnd ? &bnd[r] : NULL);
   }
+}
+
+/* Recurrent ("concurrent") network, synchronous iterations (R11): v^0 is the
+ * input vector on rows 0..I-1 and 0 on every other valid row; for t = 1..T
+ * every valid non-input row takes eval_node over v^{t-1} (inputs stay
+ * clamped); v receives v^T (and bnd its fp32 error bound when non-NULL). */
+static void recurrent_one(const genome_t *g, const double *x, int T, double *v, double *bnd) {
+  const int N = g->N, I = g->I;
+  double *vp = malloc(sizeof(double) * (size_t)N * 4 + 32);
+  double *bp = vp + N, *vn = vp + 2 * N, *bn = vp + 3 * N;
+  double a, z;
+  for (int r = 0; r < N; ++r) { vp[r] = g->valid[r] ? 0.0 : NAN; bp[r] = 0.0; }
+  for (int i = 0; i < I; ++i) vp[i] = x[i];
+  for (int t = 0; t < T; ++t) {
+    for (int r = 0; r < N; ++r) { vn[r] = vp[r]; bn[r] = bp[r]; }
+    for (int r = I; r < N; ++r)
+      if (g->valid[r]) eval_node(g, r, vp, bnd ? bp : NULL, &vn[r], &a, &z, bnd ? &bn[r] : NULL);
+    for (int r = 0; r < N; ++r) { vp[r] = vn[r]; bp[r] = bn[r]; }
+  }
+  for (int r = 0; r < N; ++r) { v[r] = vp[r]; if (bnd) bnd[r] = bp[r]; }
+  free(vp);
 }
 
 /* -------------------------------------------------------------------------- */
@@ -471,6 +509,43 @@ int or_forward(int P, int N, int C, int I, int O, const double *nodes, const dou
         if (bound) bound[((size_t)p * S + s) * O + j] = bn[I + j];
       }
       if (values) for (int r = 0; r < N; ++r) values[((size_t)p * S + s) * N + r] = v[r];
+    }
+  }
+  free(v);
+  free(x);
+  g_free(&g);
+  return 0;
+}
+
+/* Recurrent calculation (R11) over T synchronous iterations.  No
+ * topological order is needed: cycles and self-loops are allowed, and status
+ * (nullable) [P] receives every other bit of R7.  outputs [P,S,O] (NaN for a
+ * genome with a status bit); bound (nullable) [P,S,O] fp32 error bound. */
+int or_forward_recurrent(int P, int N, int C, int I, int O, const double *nodes,
+                         const double *conns, const double *inputs, int64_t in_pop_stride, int S,
+                         int T, double *outputs, double *bound, uint32_t *status) {
+  genome_t g;
+  if (P < 0 || N < I + O || S < 0 || T < 0) return -1;
+  if (g_alloc(&g, N, C, I, O)) return -2;
+  double *v = malloc(sizeof(double) * (size_t)N * 2 + 32);
+  double *bn = v + N;
+  double *x = malloc(sizeof(double) * (size_t)(I + 1));
+  for (int p = 0; p < P; ++p) {
+    parse_genome(&g, nodes + (size_t)p * N * 5, conns + (size_t)p * C * 4);
+    if (status) status[p] = g.status;
+    for (int s = 0; s < S; ++s) {
+      const double *in = inputs + (size_t)p * (size_t)in_pop_stride + (size_t)s * I;
+      double *out = outputs + ((size_t)p * S + s) * O;
+      if (g.status) {
+        for (int j = 0; j < O; ++j) { out[j] = NAN; if (bound) bound[((size_t)p * S + s) * O + j] = 0; }
+        continue;
+      }
+      for (int i = 0; i < I; ++i) x[i] = in[i];
+      recurrent_one(&g, x, T, v, bound ? bn : NULL);
+      for (int j = 0; j < O; ++j) {
+        out[j] = v[I + j];
+        if (bound) bound[((size_t)p * S + s) * O + j] = bn[I + j];
+      }
     }
   }
   free(v);

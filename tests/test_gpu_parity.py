@@ -146,6 +146,14 @@ def test_sample_parallel_shapes_agree_bitwise(name, P, S):
     bits, and the saved aggregates too.  S = 77, 45, 100 leave a ragged last
     tile for 1, 2 and 4 samples per lane."""
     nodes, conns, spec, x = _fwd_case(name, P, S)
+    if name == "uneven":
+        # genomes with E + 2V >= 2048 are evaluated by whole CTAs (frontier by
+        # frontier); the others by single warps: both run here
+        valid = ~np.isnan(nodes[:, :, 0])
+        enabled = (~np.isnan(conns[:, :, 0]) & ~np.isnan(conns[:, :, 1]) &
+                   ~np.isnan(conns[:, :, 3]) & (conns[:, :, 3] != 0))
+        cost = enabled.sum(1) + 2 * valid.sum(1)
+        assert (cost >= 2048).sum() >= 10 and (cost < 2048).sum() >= 10
     plan = _plan(spec, P)
     plan.set_tuning(small_s_max=-1)
     plan.transform(_dev(nodes), _dev(conns))

@@ -48,6 +48,7 @@ class GenomeSpec:
     r_mean: float = 1.0
     r_std: float = 0.0
     hole_frac: float = 0.05
+    back_frac: float = 0.0               # extra enabled back-edges / self-loops (recurrent)
 
 
 def _distinct_ints(rng, n: int, k: int) -> np.ndarray:
@@ -127,6 +128,21 @@ def random_genome(rng, spec: GenomeSpec):
         en = np.zeros(x.size, dtype=bool)
         en[:E] = True
 
+    if spec.back_frac > 0.0:
+        # recurrent genomes: extra enabled pairs with pos(a) >= pos(b) (back
+        # edges and self-loops), b not an input; index x -> (a, b)
+        nb = (M - dst_pos).astype(np.int64)
+        cumb = np.concatenate([[0], np.cumsum(nb)])
+        n_back = int(round(int(en.sum()) * spec.back_frac))
+        n_back = max(0, min(n_back, int(cumb[-1]), C - a_pos.size))
+        xb = _distinct_ints(rng, int(cumb[-1]), n_back)
+        bi = np.searchsorted(cumb, xb, side="right") - 1
+        b_b = I + bi
+        a_b = b_b + (xb - cumb[bi])
+        a_pos = np.concatenate([a_pos, a_b])
+        b_pos = np.concatenate([b_pos, b_b])
+        en = np.concatenate([en, np.ones(n_back, dtype=bool)])
+
     nodes = np.full((N, 5), np.nan, dtype=np.float32)
     conns = np.full((C, 4), np.nan, dtype=np.float32)
 
@@ -173,7 +189,7 @@ def make_population(spec: GenomeSpec, P: int, seed: int = 0):
 
 
 # ---------------------------------------------------------------------------
-# The five workloads.  Sizes follow the benchmark definitions; where a workload
+# The workloads.  Sizes follow the benchmark definitions; where a workload
 # leaves a choice open (activation/aggregation sets of the uneven and HyperNEAT
 # populations, edge-count ranges) the choice is written here.
 CONFIGS = {
@@ -205,6 +221,13 @@ CONFIGS = {
         I=5, O=1, N=64, C=256, hidden=(0, 58), E_uniform=(32, 256),
         acts=("sin", "gaussian", "tanh", "abs", "identity"), aggs=("sum",),
         w_std=1.0, b_std=0.5)),
+    # Recurrent ("concurrent") networks: the locomotion shape plus 15 % extra
+    # enabled back-edges and self-loops; T synchronous iterations per input
+    # vector, S = 64 vectors per genome.  Bounded activations, no product.
+    "recurrent": dict(P=10000, S=64, T=8, spec=GenomeSpec(
+        I=27, O=8, N=128, C=512, hidden=(0, 90), E_uniform=(50, 400),
+        acts=("sigmoid", "tanh", "sin", "gaussian"), aggs=("sum", "mean", "max"),
+        w_std=1.0, b_std=0.5, back_frac=0.15)),
 }
 
 
