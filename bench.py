@@ -114,7 +114,8 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="locomotion",
-                    choices=["locomotion", "uneven", "differentiation", "hyperneat", "tiny"])
+                    choices=["locomotion", "uneven", "differentiation", "hyperneat", "tiny",
+                             "recurrent"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -247,6 +248,10 @@ def describe(name, cfg, spec):
         return f"differentiation: pop={cfg['P']}, S={cfg['S']}, forward+backward (MSE)"
     if name == "hyperneat":
         return f"HyperNEAT query: pop={cfg['P']} CPPNs, 32x32 substrate (2^20 queries each)"
+    if name == "recurrent":
+        return (f"recurrent networks: pop={cfg['P']}, {spec.I} in / {spec.O} out, N={spec.N}, "
+                f"C={spec.C}, 15 % back edges / self-loops, S={cfg['S']}, T={cfg['T']} "
+                f"synchronous iterations; conn-evals count every iteration")
     return f"tiny XOR: pop={cfg['P']}, S=4"
 
 
@@ -281,6 +286,13 @@ def cpu_baseline(name, cfg, spec, nodes, conns, seed, budget_steps=None):
         oracle.backward(nodes[:k], conns[:k], x, spec.I, spec.O, go[..., None], want_inputs=True)
         units = float(E[:k].sum()) * cfg["S"]
         sample = f"{k} of {cfg['P']} genomes, forward + backward at S={cfg['S']}"
+    elif name == "recurrent":
+        k = budget_steps or 300
+        x = np.random.default_rng(seed).standard_normal((k, cfg["S"], spec.I)).astype(np.float32)
+        t0 = time.perf_counter()
+        oracle.forward_recurrent(nodes[:k], conns[:k], x, spec.I, spec.O, cfg["T"])
+        units = float(E[:k].sum()) * cfg["S"] * cfg["T"]
+        sample = f"{k} of {cfg['P']} genomes x S={cfg['S']} x T={cfg['T']}"
     elif name == "hyperneat":
         k = budget_steps or 2
         q = np.arange(32 ** 4 // 4)
@@ -378,6 +390,31 @@ def bench_ours(args, rank, world, local, pg):
         fwd_hbm = float((8 * E + 12 * Vn).sum() + 4 * S * spec.I + 4 * S * spec.O * P +
                         4 * S * Vn.sum())
         fwd_chip = float(4 * S * (E + Vn).sum())
+    elif name == "recurrent":
+        S, T = cfg["S"], cfg["T"]
+        x = np.random.default_rng(args.seed + rank).standard_normal((P, S, spec.I)).astype(
+            np.float32)
+        d_nodes = torch.from_numpy(nodes).to(dev)
+        d_conns = torch.from_numpy(conns).to(dev)
+        d_x = torch.from_numpy(x).to(dev)
+        out = torch.empty((P, S, spec.O), device=dev)
+        status = plan.transform_recurrent(d_nodes, d_conns)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))]
+
+        def run():
+            plan.transform_recurrent(d_nodes, d_conns, status=status)
+            ev[0][0].record()
+            plan.forward_recurrent(d_x, T, out=out)
+            ev[0][1].record()
+
+        units_per_step = float(E.sum()) * S * T
+        launches_per_step += 1
+        fwd_launches = 1
+        ro = None
+        # HBM: program once, inputs, outputs; on chip: every iteration reads a
+        # value per enabled connection and writes one per node
+        alg_bytes = float((8 * E + 12 * Vn).sum() + 4 * S * (spec.I + spec.O) * P)
+        chip_bytes = float(4 * S * T * (E + Vn).sum())
     else:  # hyperneat
         d_nodes = torch.from_numpy(nodes).to(dev)
         d_conns = torch.from_numpy(conns).to(dev)
@@ -434,6 +471,8 @@ def bench_ours(args, rank, world, local, pg):
     if avg_launch_us:
         if name == "hyperneat":
             kernel = "k_hyperneat"
+        elif name == "recurrent":
+            kernel = "k_forward_rec"
         elif name == "differentiation":
             kernel = "k_backward"
             fwd_us = 1e3 * ev_f[0].elapsed_time(ev_f[1])
@@ -534,7 +573,8 @@ def bench_reference(args, rank, world):
         return
     name = args.config
     cfg, spec, nodes, conns = workload(name, args.seed, args.pop)
-    budget = {"locomotion": 8, "uneven": 150, "differentiation": 4, "hyperneat": 1, "tiny": None}[name]
+    budget = {"locomotion": 8, "uneven": 150, "differentiation": 4, "hyperneat": 1, "tiny": None,
+              "recurrent": 40}[name]
     for _ in range(max(3, args.warmup)):
         cpu_baseline(name, cfg, spec, nodes, conns, args.seed, budget)
     vals, secs = [], 0.0

@@ -165,6 +165,27 @@ neat_status neat_transform(neat_plan *plan, const float *nodes, const float *con
 neat_status neat_forward(neat_plan *plan, const float *inputs, int64_t in_pop_stride, int S,
                          float *outputs, float *saved, cudaStream_t stream);
 
+/* Transformation for RECURRENT ("concurrent") networks (Sec. 3.3 names
+ * feed-forward and concurrent networks; only the former gets a topological
+ * order).  Same validation and status bits as neat_transform except that
+ * cycles and self-loops are legal (NEAT_G_CYCLE is never set); every valid
+ * node is placed in ascending key order.  gstatus [P] u32 out.  Afterwards
+ * only neat_forward_recurrent applies (the other calculation entry points
+ * return NEAT_ERR_STATE until the next neat_transform). */
+neat_status neat_transform_recurrent(neat_plan *plan, const float *nodes, const float *conns,
+                                     uint32_t *gstatus, cudaStream_t stream);
+
+/* Recurrent calculation over T synchronous iterations (0 <= T <= 65536):
+ * v^0 = the inputs on input nodes and 0 on every other node; in iteration t
+ * every non-input node k takes act(b_k + r_k * agg_e(w_e * v^{t-1}[src_e]))
+ * while the inputs stay clamped; outputs [P, S, O] = v^T at the output
+ * nodes (NaN for genomes with a nonzero status).  Inputs, strides and S as in
+ * neat_forward.  Valid after neat_transform_recurrent or neat_transform (a
+ * genome with NEAT_G_CYCLE then has NaN outputs).  With T at least the depth
+ * of an acyclic genome the outputs equal the feed-forward ones. */
+neat_status neat_forward_recurrent(neat_plan *plan, const float *inputs, int64_t in_pop_stride,
+                                   int S, int T, float *outputs, cudaStream_t stream);
+
 /* Calculation stage, plain padded form (the comparison baseline): one CTA per
  * (genome, 32 samples) walking all N padded positions; no queue, no packing.
  * Same arguments and results as neat_forward (no saved buffer). */

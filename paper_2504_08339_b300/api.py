@@ -102,6 +102,30 @@ class Plan:
                    "neat_transform")
         return out
 
+    def transform_recurrent(self, nodes, conns, status=None, stream=None):
+        """Transformation for recurrent networks (cycles legal); returns the
+        per-genome status words [P] (int32 view of the u32 bits)."""
+        P, N, C = self.P, self.N, self.C
+        _need(nodes, "nodes", torch.float32, (P, N, 5))
+        _need(conns, "conns", torch.float32, (P, C, 4))
+        if status is None:
+            status = torch.empty((P,), dtype=torch.int32, device=nodes.device)
+        _lib.check(self._lib.neat_transform_recurrent(self._h, _ptr(nodes), _ptr(conns),
+                                                      _ptr(status), _stream(stream)),
+                   "neat_transform_recurrent")
+        return status
+
+    def forward_recurrent(self, inputs, T, out=None, stream=None):
+        """outputs [P, S, O] after T synchronous iterations."""
+        S, stride = self._inputs(inputs)
+        if out is None:
+            out = torch.empty((self.P, S, self.O), dtype=torch.float32, device=inputs.device)
+        _need(out, "out", torch.float32, (self.P, S, self.O))
+        _lib.check(self._lib.neat_forward_recurrent(self._h, _ptr(inputs), stride, S, int(T),
+                                                    _ptr(out), _stream(stream)),
+                   "neat_forward_recurrent")
+        return out
+
     # -- calculation stage ---------------------------------------------------------
     def _inputs(self, inputs):
         _need(inputs, "inputs", torch.float32)

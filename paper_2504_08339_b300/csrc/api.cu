@@ -20,7 +20,7 @@ struct neat_plan {
   int sm_count;
   int smem_optin;
   neat_tuning tune;
-  int transformed;
+  int transformed;  // 0: none, 1: feed-forward (neat_transform), 2: recurrent
 };
 
 namespace {
@@ -115,7 +115,7 @@ const char *neat_status_string(neat_status s) {
     case NEAT_ERR_CUDA: return "CUDA error";
     case NEAT_ERR_WORKSPACE: return "workspace too small";
     case NEAT_ERR_UNSUPPORTED: return "unsupported size";
-    case NEAT_ERR_STATE: return "plan not transformed";
+    case NEAT_ERR_STATE: return "plan not transformed (for this network type)";
   }
   return "unknown status";
 }
@@ -228,7 +228,7 @@ neat_status neat_transform(neat_plan *plan, const float *nodes, const float *con
 neat_status neat_forward(neat_plan *plan, const float *inputs, int64_t in_pop_stride, int S,
                          float *outputs, float *saved, cudaStream_t stream) {
   if (plan == nullptr) return NEAT_ERR_ARG;
-  if (!plan->transformed) return NEAT_ERR_STATE;
+  if (plan->transformed != 1) return NEAT_ERR_STATE;
   neat_status s = check_inputs(plan, inputs, in_pop_stride, S);
   if (s != NEAT_OK) return s;
   if (S == 0 || plan->P == 0) return NEAT_OK;
@@ -254,7 +254,7 @@ neat_status neat_forward(neat_plan *plan, const float *inputs, int64_t in_pop_st
 neat_status neat_forward_plain(neat_plan *plan, const float *inputs, int64_t in_pop_stride, int S,
                                float *outputs, cudaStream_t stream) {
   if (plan == nullptr) return NEAT_ERR_ARG;
-  if (!plan->transformed) return NEAT_ERR_STATE;
+  if (plan->transformed != 1) return NEAT_ERR_STATE;
   neat_status s = check_inputs(plan, inputs, in_pop_stride, S);
   if (s != NEAT_OK) return s;
   if (S == 0 || plan->P == 0) return NEAT_OK;
@@ -268,7 +268,7 @@ neat_status neat_backward(neat_plan *plan, const float *inputs, int64_t in_pop_s
                           float *grad_bias, float *grad_response, float *grad_inputs,
                           cudaStream_t stream) {
   if (plan == nullptr) return NEAT_ERR_ARG;
-  if (!plan->transformed) return NEAT_ERR_STATE;
+  if (plan->transformed != 1) return NEAT_ERR_STATE;
   neat_status s = check_inputs(plan, inputs, in_pop_stride, S);
   if (s != NEAT_OK) return s;
   if (plan->P == 0) return NEAT_OK;
@@ -291,7 +291,7 @@ neat_status neat_backward(neat_plan *plan, const float *inputs, int64_t in_pop_s
 neat_status neat_hyperneat_query(neat_plan *plan, int grid, float thresh, float *weights,
                                  cudaStream_t stream) {
   if (plan == nullptr) return NEAT_ERR_ARG;
-  if (!plan->transformed) return NEAT_ERR_STATE;
+  if (plan->transformed != 1) return NEAT_ERR_STATE;
   if (plan->I != 5 || plan->O != 1) return NEAT_ERR_UNSUPPORTED;
   if (grid < 2 || grid > 128) return NEAT_ERR_ARG;
   if (plan->P == 0) return NEAT_OK;
@@ -302,6 +302,44 @@ neat_status neat_hyperneat_query(neat_plan *plan, int grid, float thresh, float 
   const int occ = std::max(1, neat::hyperneat_occupancy(warps, smem));
   return cuda_status(neat::launch_hyperneat(plan->w, grid, thresh, weights, warps,
                                             plan->sm_count * occ, stream));
+}
+
+neat_status neat_transform_recurrent(neat_plan *plan, const float *nodes, const float *conns,
+                                     uint32_t *gstatus, cudaStream_t stream) {
+  if (plan == nullptr) return NEAT_ERR_ARG;
+  if (plan->P > 0) {
+    if (nodes == nullptr || conns == nullptr || gstatus == nullptr) return NEAT_ERR_ARG;
+    if (!aligned(nodes, 4) || !aligned(conns, 16) || !aligned(gstatus, 4)) return NEAT_ERR_ARG;
+  }
+  cudaError_t e = neat::launch_transform(plan->w, nodes, conns, nullptr, nullptr, nullptr, gstatus,
+                                         stream, 1);
+  if (e == cudaSuccess) e = neat::launch_queue_build(plan->w, 0, stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  plan->transformed = 2;
+  return NEAT_OK;
+}
+
+neat_status neat_forward_recurrent(neat_plan *plan, const float *inputs, int64_t in_pop_stride,
+                                   int S, int T, float *outputs, cudaStream_t stream) {
+  if (plan == nullptr) return NEAT_ERR_ARG;
+  if (plan->transformed == 0) return NEAT_ERR_STATE;
+  if (T < 0 || T > (1 << 16)) return NEAT_ERR_ARG;
+  neat_status s = check_inputs(plan, inputs, in_pop_stride, S);
+  if (s != NEAT_OK) return s;
+  if (S == 0 || plan->P == 0) return NEAT_OK;
+  if (outputs == nullptr || !aligned(outputs, 4)) return NEAT_ERR_ARG;
+  // 8 warps per CTA (the tuning's warps_per_cta if set); two value buffers
+  // per warp bound the grid, kept to whole multiples of the SM count
+  const int warps = plan->tune.warps_per_cta > 0 ? plan->tune.warps_per_cta : 8;
+  const int slots = neat::sp_scratch_slots(plan->w, 2);
+  const int occ = std::max(1, neat::forward_rec_occupancy(warps));
+  const int64_t items = int64_t(plan->P) * ((S + 31) / 32);
+  int64_t cap = std::min<int64_t>(int64_t(plan->sm_count) * occ, slots / warps);
+  if (cap >= plan->sm_count) cap = cap / plan->sm_count * plan->sm_count;
+  const int grid = int(std::max<int64_t>(1, std::min<int64_t>(cap, (items + warps - 1) / warps)));
+  if (int64_t(grid) * warps > slots) return NEAT_ERR_UNSUPPORTED;
+  return cuda_status(neat::launch_forward_recurrent(plan->w, inputs, in_pop_stride, S, T, outputs,
+                                                    warps, grid, stream));
 }
 
 }  // extern "C"

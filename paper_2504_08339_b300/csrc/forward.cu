@@ -328,6 +328,70 @@ __global__ void __launch_bounds__(512, 3)
   grid_done_reset(w.counters + CTR_FWD_ITEM, w.counters + CTR_FWD_DONE, w.counters + CTR_FWD_BIG);
 }
 
+// Recurrent calculation (T synchronous iterations; inputs clamped, v^0 = 0
+// elsewhere, outputs v^T).  Warps claim (genome, 32-sample tile) items from
+// the size-sorted queue; the warp's workspace slot holds two [N][32] value
+// buffers, v^{t-1} (read) and v^t (written), swapped after every iteration.
+__global__ void __launch_bounds__(512, 3)
+    k_forward_rec(Ws w, const float *__restrict__ inputs, int64_t stride, int S, int T,
+                  float *__restrict__ out, int tiles) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int N = w.N, I = w.I, O = w.O;
+  const size_t slot = size_t(blockIdx.x) * (blockDim.x >> 5) + wid;
+  float *buf = (w.sp_scratch != nullptr && (slot + 1) * 2 * size_t(N) * 32 <= w.sp_scratch_floats)
+                   ? w.sp_scratch + slot * 2 * size_t(N) * 32
+                   : nullptr;
+  const int total = w.P * tiles;
+  for (;;) {
+    int item = 0;
+    if (lane == 0) item = int(atomicAdd(w.counters + CTR_REC_ITEM, 1u));
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= total) break;
+    const int q = item / tiles, tile = item - q * tiles;
+    const int g = w.qorder[q];
+    const GenomeHdr h = w.hdr[g];
+    const int s = tile * 32 + lane;
+    const bool active = s < S;
+    float *orow = out + (size_t(g) * S + (active ? s : 0)) * O;
+    if (h.status != 0u || buf == nullptr) {
+      if (buf == nullptr && lane == 0) atomicOr(w.counters + CTR_ERR, ERR_SP_NO_SCRATCH);
+      if (active)
+        for (int o = 0; o < O; ++o) orow[o] = qnan();
+      continue;
+    }
+    float *a = buf + lane, *b = buf + size_t(N) * 32 + lane;
+    const int V = h.V;
+    for (int p = 0; p < V; ++p) {
+      a[p * 32] = 0.0f;
+      b[p * 32] = 0.0f;
+    }
+    const int32_t *io = w.pio + size_t(g) * (I + O);
+    const float *in = inputs + size_t(g) * stride + size_t(active ? s : 0) * I;
+    for (int i = 0; i < I; ++i) {
+      const float x = active ? __ldg(in + i) : 0.0f;
+      a[io[i] * 32] = x;
+      b[io[i] * 32] = x;
+    }
+    const NodeRec *nr = w.knode + h.node_off;
+    const EdgeRec *er = w.kedge + h.edge_off;
+    for (int t = 0; t < T; ++t) {
+      for (int p = 0; p < V; ++p) {
+        const NodeRec n = ld_node(nr + p);
+        if (n.meta & META_INPUT) continue;
+        float ag[1];
+        node_agg<1>(n, er, a, ag);
+        b[p * 32] = act_apply(meta_act(n.meta), fmaf(n.resp, ag[0], n.bias));
+      }
+      float *tmp = a;
+      a = b;
+      b = tmp;
+    }
+    if (active)
+      for (int o = 0; o < O; ++o) orow[o] = a[io[I + o] * 32];
+  }
+  grid_done_reset(w.counters + CTR_REC_ITEM, w.counters + CTR_REC_DONE);
+}
+
 __global__ void __launch_bounds__(32) k_forward_plain(Ws w, const float *__restrict__ inputs,
                                                       int64_t stride, int S,
                                                       float *__restrict__ out) {
@@ -439,6 +503,22 @@ cudaError_t launch_forward_plain(const Ws &w, const float *inputs, int64_t strid
   const dim3 grid(unsigned(w.P), unsigned((S + 31) / 32));
   k_forward_plain<<<grid, 32, smem, st>>>(w, inputs, stride, S, outputs);
   return cudaGetLastError();
+}
+
+cudaError_t launch_forward_recurrent(const Ws &w, const float *inputs, int64_t stride, int S,
+                                     int T, float *outputs, int warps, int grid, cudaStream_t st) {
+  if (w.P == 0 || S == 0) return cudaSuccess;
+  const int tiles = (S + 31) / 32;
+  k_forward_rec<<<grid, warps * 32, 0, st>>>(w, inputs, stride, S, T, outputs, tiles);
+  return cudaGetLastError();
+}
+
+int forward_rec_occupancy(int warps) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_forward_rec, warps * 32, 0) !=
+      cudaSuccess)
+    return 0;
+  return n;
 }
 
 cudaError_t launch_hyperneat(const Ws &w, int G, float thresh, float *weights, int warps,

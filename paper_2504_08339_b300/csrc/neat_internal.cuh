@@ -256,7 +256,7 @@ inline Ws make_ws(void *base, const Layout &L, int P, int N, int C, int I, int O
 // counters[] slots
 constexpr int CTR_FWD_ITEM = 0, CTR_FWD_DONE = 1, CTR_HN_ITEM = 2, CTR_HN_DONE = 3,
               CTR_LVL_ITEM = 4, CTR_LVL_DONE = 5, CTR_FWD_BIG = 6, CTR_SP_NBIG = 7,
-              CTR_NBATCH = 8, CTR_ERR = 9;
+              CTR_NBATCH = 8, CTR_ERR = 9, CTR_REC_ITEM = 10, CTR_REC_DONE = 11;
 // genomes of at least this cost (E + 2V) are evaluated by a whole CTA in the
 // sample-parallel forward (counters[CTR_SP_NBIG] of them, a queue prefix)
 #ifndef NEAT_SP_COOP_COST
@@ -297,9 +297,11 @@ __device__ __forceinline__ float act_deriv(int a, float z, float v) {
 __device__ __forceinline__ float qnan() { return __int_as_float(0x7fc00000); }
 
 // -- launch wrappers (defined in the .cu files) ------------------------------------
+// recurrent != 0: no topological order (cycles legal); every valid node in
+// ascending key forms one frontier; order / layer / n_layers may be null
 cudaError_t launch_transform(const Ws &w, const float *nodes, const float *conns, int32_t *order,
                              int32_t *layer, int32_t *n_layers, uint32_t *gstatus,
-                             cudaStream_t st);
+                             cudaStream_t st, int recurrent = 0);
 cudaError_t launch_queue_build(const Ws &w, int mode, cudaStream_t st);
 // Sample-parallel launch shape: `spl` samples per lane (1, 2, 4); genomes
 // with V <= vcap keep their values in shared memory, the others in the
@@ -317,6 +319,11 @@ inline int sp_scratch_slots(const Ws &w, int spl) {
 }
 cudaError_t launch_forward_plain(const Ws &w, const float *inputs, int64_t stride, int S,
                                  float *outputs, cudaStream_t st);
+// recurrent calculation: T synchronous iterations, `warps` per CTA, `grid`
+// CTAs (grid * warps <= sp_scratch_slots(w, 2): two value buffers per warp)
+cudaError_t launch_forward_recurrent(const Ws &w, const float *inputs, int64_t stride, int S,
+                                     int T, float *outputs, int warps, int grid, cudaStream_t st);
+int forward_rec_occupancy(int warps);
 // Backward: `warps` per CTA, `smem_bytes` of dynamic shared memory (at least
 // backward_smem(N, C, 1)); a genome runs on as many warps as blocks of its
 // size fit in smem_bytes.

@@ -118,7 +118,8 @@ __global__ void __launch_bounds__(256) k_transform(Ws w, const float *__restrict
                                                    int32_t *__restrict__ order,
                                                    int32_t *__restrict__ layer,
                                                    int32_t *__restrict__ n_layers,
-                                                   uint32_t *__restrict__ gstatus) {
+                                                   uint32_t *__restrict__ gstatus,
+                                                   int recurrent) {
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ int wbuf[33];
   __shared__ unsigned s_status;
@@ -271,7 +272,19 @@ __global__ void __launch_bounds__(256) k_transform(Ws w, const float *__restrict
   // 5. Kahn by frontier.  Each round emits every ready node in ascending key
   // (sorted index order = key order), then releases their successors.
   int emitted = 0, t = 0;
-  if ((status0 & ~NEAT_G_CYCLE) == 0u) {
+  if (recurrent) {
+    // recurrent networks need no order: every valid node in ascending key
+    // (sorted index order) as one frontier; cycles are legal
+    if ((status0 & ~NEAT_G_CYCLE) == 0u) {
+      for (int s = tid; s < V; s += T) {
+        order_s[s] = s;
+        layer_s[s] = 0;
+        pos_of[s] = s;
+      }
+      emitted = V;
+      t = V > 0 ? 1 : 0;
+    }
+  } else if ((status0 & ~NEAT_G_CYCLE) == 0u) {
     for (int s = tid; s < V; s += T) {
       rem[s] = indeg[s];
       ready[s] = indeg[s] == 0;
@@ -308,15 +321,18 @@ __global__ void __launch_bounds__(256) k_transform(Ws w, const float *__restrict
   const unsigned status = s_status;
   const bool no_order = (status & ~NEAT_G_CYCLE) != 0u;
 
-  // 6. order / layer / n_layers / status outputs
-  for (int p = tid; p < N; p += T)
-    order[size_t(g) * N + p] = (!no_order && p < emitted) ? row_of_s[order_s[p]] : -1;
-  for (int r = tid; r < N; r += T) {
-    const int s = s_of_row[r];
-    layer[size_t(g) * N + r] = (!no_order && s >= 0) ? layer_s[s] : -1;
-  }
+  // 6. order / layer / n_layers / status outputs (order, layer and n_layers
+  // are optional in the recurrent mode)
+  if (order != nullptr)
+    for (int p = tid; p < N; p += T)
+      order[size_t(g) * N + p] = (!no_order && p < emitted) ? row_of_s[order_s[p]] : -1;
+  if (layer != nullptr)
+    for (int r = tid; r < N; r += T) {
+      const int s = s_of_row[r];
+      layer[size_t(g) * N + r] = (!no_order && s >= 0) ? layer_s[s] : -1;
+    }
   if (tid == 0) {
-    n_layers[g] = no_order ? 0 : t;
+    if (n_layers != nullptr) n_layers[g] = no_order ? 0 : t;
     gstatus[g] = status;
   }
 
@@ -480,11 +496,12 @@ __global__ void __launch_bounds__(128) k_pack(Ws w) {
 
 cudaError_t launch_transform(const Ws &w, const float *nodes, const float *conns, int32_t *order,
                              int32_t *layer, int32_t *n_layers, uint32_t *gstatus,
-                             cudaStream_t st) {
+                             cudaStream_t st, int recurrent) {
   if (w.P == 0) return cudaSuccess;
   const TSmem L = tsmem_layout(w.N, w.C);
   const int threads = w.N + w.C <= 384 ? 128 : 256;
-  k_transform<<<w.P, threads, L.total, st>>>(w, nodes, conns, order, layer, n_layers, gstatus);
+  k_transform<<<w.P, threads, L.total, st>>>(w, nodes, conns, order, layer, n_layers, gstatus,
+                                             recurrent);
   return cudaGetLastError();
 }
 
