@@ -313,7 +313,10 @@ __global__ void __launch_bounds__(BLD_THREADS) k_lvl_build(Ws w) {
     const int c = meta_cnt(n.meta);
     TaskRec t;
     t.bias = n.bias;
-    t.resp = n.resp;
+    // mean: fold 1/n into the response, so that the round combines partial
+    // sums the same way for sum and mean (r (s / n) -> (r / n) s, both
+    // rounded once)
+    t.resp = (meta_agg(n.meta) == NEAT_AGG_MEAN && c > 0) ? n.resp / float(c) : n.resp;
     t.chunk = uint32_t(cnt[j]);
     t.meta = task_meta(c, meta_act(n.meta), meta_agg(n.meta), g_slot[k] + p);
     tasks[j] = t;
@@ -376,6 +379,41 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, int byte
 //     per (task, sample) combines the task's chunk partials with its
 //     aggregation, then v[slot] = act(b + r * a) -- one activation branch per
 //     warp.
+// Node phase of one activation group: lane (task, sample) combines the
+// task's 4-edge chunk partials (sum, product, max), applies the aggregation
+// (a mean's 1/n is folded into its response) and the activation ACT.
+template <int ST, int ACT>
+__device__ __forceinline__ void node_group(const TaskRec *__restrict__ tasks, const float4 *part,
+                                           float *v, const RoundRec &lo, int g0, int gn,
+                                           int lane) {
+  for (int it = lane; it < gn; it += 32) {
+    const int t = g0 + (ST == 1 ? it : it / ST);
+    const int s = ST == 1 ? 0 : it % ST;
+    const TaskRec tk = tasks[t];
+    const int cnt = task_cnt(tk.meta), agg = task_agg(tk.meta);
+    const int c0 = int(tk.chunk) - lo.chunk, nc = (cnt + 3) >> 2;
+    float sum = 0.0f, prod = 1.0f, mx = qnan();
+    // partials four at a time: the loads of a group are in flight together
+    for (int k = 0; k < nc; k += 4) {
+      float4 p[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        p[u] = k + u < nc ? part[(c0 + k + u) * ST + s] : make_float4(0.0f, 1.0f, qnan(), 0.0f);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        sum += p[u].x;
+        prod *= p[u].y;
+        mx = fmaxf(mx, p[u].z);
+      }
+    }
+    // empty aggregation: 0 for every aggregation
+    const float a = nc == 0 ? 0.0f
+                  : agg == NEAT_AGG_PRODUCT ? prod
+                  : agg == NEAT_AGG_MAX ? mx : sum;
+    v[task_slot(tk.meta) * ST + s] = act_apply(ACT, fmaf(tk.resp, a, tk.bias));
+  }
+}
+
 template <int ST>
 __device__ __forceinline__ void run_round(const TaskRec *__restrict__ tasks,
                                           const uint2 *__restrict__ eslot,
@@ -405,36 +443,20 @@ __device__ __forceinline__ void run_round(const TaskRec *__restrict__ tasks,
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int act = warp; act < 7; act += nw) {
-  const int g0 = lo.task + lo.act[act], gn = (lo.act[act + 1] - lo.act[act]) * ST;
-  for (int it = lane; it < gn; it += 32) {
-    const int t = g0 + (ST == 1 ? it : it / ST);
-    const int s = ST == 1 ? 0 : it % ST;
-    const TaskRec tk = tasks[t];
-    const int cnt = task_cnt(tk.meta), agg = task_agg(tk.meta);
-    const int c0 = int(tk.chunk) - lo.chunk, nc = (cnt + 3) >> 2;
-    float a = 0.0f;
-    if (nc > 0) {
-      // partials four at a time: the loads of a group are independent, so
-      // they are in flight together
-      float sum = 0.0f, prod = 1.0f, mx = qnan();
-      for (int k = 0; k < nc; k += 4) {
-        float4 p[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          p[u] = k + u < nc ? part[(c0 + k + u) * ST + s] : make_float4(0.0f, 1.0f, qnan(), 0.0f);
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          sum += p[u].x;
-          prod *= p[u].y;
-          mx = fmaxf(mx, p[u].z);
-        }
-      }
-      a = agg == NEAT_AGG_SUM ? sum
-        : agg == NEAT_AGG_MEAN ? sum / float(cnt)
-        : agg == NEAT_AGG_PRODUCT ? prod : mx;
+    const int g0 = lo.task + lo.act[act], gn = (lo.act[act + 1] - lo.act[act]) * ST;
+    if (gn == 0) continue;
+    // the activation is a compile-time constant in each group loop
+#define NEAT_GROUP(A) node_group<ST, A>(tasks, part, v, lo, g0, gn, lane)
+    switch (act) {
+      case NEAT_ACT_IDENTITY: NEAT_GROUP(NEAT_ACT_IDENTITY); break;
+      case NEAT_ACT_SIGMOID: NEAT_GROUP(NEAT_ACT_SIGMOID); break;
+      case NEAT_ACT_TANH: NEAT_GROUP(NEAT_ACT_TANH); break;
+      case NEAT_ACT_RELU: NEAT_GROUP(NEAT_ACT_RELU); break;
+      case NEAT_ACT_SIN: NEAT_GROUP(NEAT_ACT_SIN); break;
+      case NEAT_ACT_GAUSSIAN: NEAT_GROUP(NEAT_ACT_GAUSSIAN); break;
+      default: NEAT_GROUP(NEAT_ACT_ABS); break;
     }
-    v[task_slot(tk.meta) * ST + s] = act_apply(act, fmaf(tk.resp, a, tk.bias));
-  }
+#undef NEAT_GROUP
   }
 }
 
@@ -459,7 +481,6 @@ __global__ void __launch_bounds__(256) k_forward_lvl(Ws w, const float *__restri
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb1) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  __syncthreads();
   uint32_t parity = 0;
   for (;;) {
     if (tid == 0) s_b = int(atomicAdd(w.counters + CTR_LVL_ITEM, 1u));
