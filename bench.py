@@ -120,6 +120,9 @@ def parse_args():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--recompute", action="store_true",
+                    help="differentiation at S = 65,536 with the forward values recomputed in the "
+                         "backward (no saved aggregates)")
     ap.add_argument("--pop", type=int, default=None,
                     help="population override (profiling captures and small cases; the line's "
                          "config then says so)")
@@ -245,7 +248,9 @@ def describe(name, cfg, spec):
         return (f"uneven batching: pop={cfg['P']}, V~logU[23,1024], E~logU[8,4096], S={cfg['S']}, "
                 f"{cfg['steps']} steps per rollout")
     if name == "differentiation":
-        return f"differentiation: pop={cfg['P']}, S={cfg['S']}, forward+backward (MSE)"
+        mode = "recompute" if cfg.get("recompute") else "saved aggregates"
+        return (f"differentiation: pop={cfg['P']}, S={cfg['S']}, forward+backward (MSE), "
+                f"{mode}")
     if name == "hyperneat":
         return f"HyperNEAT query: pop={cfg['P']} CPPNs, 32x32 substrate (2^20 queries each)"
     if name == "recurrent":
@@ -278,7 +283,7 @@ def cpu_baseline(name, cfg, spec, nodes, conns, seed, budget_steps=None):
         units = float(E[sel].sum()) * cfg["S"]
         sample = f"{k} of {cfg['P']} genomes x 1 step (S={cfg['S']})"
     elif name == "differentiation":
-        k = budget_steps or 64
+        k = budget_steps or (64 if cfg["S"] <= 4096 else 4)
         x, y = regression_batch(seed, cfg["S"])
         t0 = time.perf_counter()
         out = oracle.forward(nodes[:k], conns[:k], x, spec.I, spec.O)
@@ -324,6 +329,8 @@ def bench_ours(args, rank, world, local, pg):
     peaks = load_peaks()
     name = args.config
     cfg, spec, nodes, conns = workload(name, args.seed + rank, args.pop)
+    if name == "differentiation" and args.recompute:
+        cfg["S"], cfg["recompute"] = cfg["S_recompute"], True
     P = cfg["P"]
     E, Vn = enabled_counts(nodes, conns)
     plan = Plan(P, spec.N, spec.C, spec.I, spec.O, device=dev)
@@ -358,7 +365,7 @@ def bench_ours(args, rank, world, local, pg):
         d_conns = torch.from_numpy(conns).to(dev)
         d_x = torch.from_numpy(x).to(dev)
         d_y = torch.from_numpy(y).to(dev)
-        saved = torch.empty((P, spec.N, S), device=dev)
+        saved = None if cfg.get("recompute") else torch.empty((P, spec.N, S), device=dev)
         out = torch.empty((P, S, spec.O), device=dev)
         go = torch.empty((P, S, spec.O), device=dev)
         tr = plan.transform(d_nodes, d_conns)
@@ -384,11 +391,14 @@ def bench_ours(args, rank, world, local, pg):
         ro = None
         # backward: program again, grads out, saved aggregates in, dL/dO in,
         # dL/dx out, the shared inputs in; on chip 12 S E + 8 S V
-        alg_bytes = float((8 * E + 12 * Vn).sum() + (4 * E + 8 * Vn).sum() + 4 * S * Vn.sum() +
+        # (recompute: no saved aggregates; the forward's on-chip traffic again)
+        rec = saved is None
+        alg_bytes = float((8 * E + 12 * Vn).sum() + (4 * E + 8 * Vn).sum() +
+                          (0 if rec else 4 * S * Vn.sum()) +
                           4 * S * spec.O * P + 4 * S * spec.I * P + 4 * S * spec.I)
-        chip_bytes = float((12 * S * E + 8 * S * Vn).sum())
+        chip_bytes = float((12 * S * E + 8 * S * Vn).sum() + (4 * S * (E + Vn).sum() if rec else 0))
         fwd_hbm = float((8 * E + 12 * Vn).sum() + 4 * S * spec.I + 4 * S * spec.O * P +
-                        4 * S * Vn.sum())
+                        (0 if rec else 4 * S * Vn.sum()))
         fwd_chip = float(4 * S * (E + Vn).sum())
     elif name == "recurrent":
         S, T = cfg["S"], cfg["T"]
@@ -474,7 +484,7 @@ def bench_ours(args, rank, world, local, pg):
         elif name == "recurrent":
             kernel = "k_forward_rec"
         elif name == "differentiation":
-            kernel = "k_backward"
+            kernel = "k_backward<recompute>" if cfg.get("recompute") else "k_backward"
             fwd_us = 1e3 * ev_f[0].elapsed_time(ev_f[1])
             extra["forward"] = roofline(fwd_hbm, fwd_chip, fwd_us, peaks, dev)
             extra["forward"].update({"kernel": "k_forward_sp (with the saved aggregates)",

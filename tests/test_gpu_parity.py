@@ -281,6 +281,25 @@ def test_backward_parity_every_aggregation(S):
         compare_grads(gi.cpu().numpy(), ri, f"grad_inputs stored={stored}")
 
 
+def test_backward_recompute_at_65536_samples():
+    """The differentiation configuration's recompute mode (S = 65,536: the saved
+    aggregates would take P x 64 x 65,536 floats): gradients summed over every
+    sample of 12 genomes against the oracle."""
+    P, S = 12, 65536
+    nodes, conns, spec = population_for("differentiation", seed=8, P=P)
+    x, _ = regression_batch(8, S)
+    go = (np.random.default_rng(5).standard_normal((P, S, spec.O)) / S).astype(np.float32)
+    plan = _plan(spec, P)
+    plan.transform(_dev(nodes), _dev(conns))
+    gw, gb, gr, gi = plan.backward(_dev(x), _dev(go), saved=None)
+    rw, rb, rr, ri = oracle.backward(nodes, conns, x, spec.I, spec.O, go)
+    compare_grads(gw.cpu().numpy(), rw, "grad_weight")
+    compare_grads(gb.cpu().numpy(), rb, "grad_bias")
+    compare_grads(gr.cpu().numpy(), rr, "grad_response")
+    sel = np.random.default_rng(2).choice(S, 2048, replace=False)
+    compare_grads(gi.cpu().numpy()[:, sel], ri[:, sel], "grad_inputs")
+
+
 def test_backward_and_forward_are_deterministic():
     nodes, conns, spec, x = _fwd_case("differentiation", 128, 300, seed=3)
     plan = _plan(spec, 128)
