@@ -551,6 +551,54 @@ def bench_ours(args, rank, world, local, pg):
                "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                "ms_per_step": round(ems, 3), "steps": K}
 
+    if not args.no_e2e and name == "differentiation":
+        # through the public differentiable API (torch.autograd.Function):
+        # population and batch H2D, transform + forward + MSE + backward,
+        # gradients of nodes, conns and inputs and the loss D2H
+        from paper_2504_08339_b300.api import evaluate
+        h_nodes = torch.from_numpy(nodes).pin_memory()
+        h_conns = torch.from_numpy(conns).pin_memory()
+        h_x = torch.from_numpy(x).pin_memory()
+        h_y = torch.from_numpy(y).pin_memory()
+        g_nodes = torch.empty(h_nodes.shape, dtype=torch.float32).pin_memory()
+        g_conns = torch.empty(h_conns.shape, dtype=torch.float32).pin_memory()
+        g_x = torch.empty(h_x.shape, dtype=torch.float32).pin_memory()
+        h_loss = torch.empty((1,), dtype=torch.float32).pin_memory()
+        store = not cfg.get("recompute")
+
+        def step_e2e():
+            n_ = h_nodes.to(dev, non_blocking=True).requires_grad_()
+            c_ = h_conns.to(dev, non_blocking=True).requires_grad_()
+            x_ = h_x.to(dev, non_blocking=True).requires_grad_()
+            y_ = h_y.to(dev, non_blocking=True)
+            o_ = evaluate(plan, n_, c_, x_, store=store)
+            loss = ((o_[..., 0] - y_) ** 2).mean(dim=1).sum()
+            loss.backward()
+            g_nodes.copy_(n_.grad, non_blocking=True)
+            g_conns.copy_(c_.grad, non_blocking=True)
+            g_x.copy_(x_.grad, non_blocking=True)
+            h_loss.copy_(loss.detach().reshape(1), non_blocking=True)
+
+        step_e2e()
+        torch.cuda.synchronize()
+        K = max(1, min(5, args.steps))
+        w0 = time.perf_counter()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(K):
+            step_e2e()
+        b.record()
+        torch.cuda.synchronize()
+        wall = (time.perf_counter() - w0) / K
+        ems = max(a.elapsed_time(b) / K, wall * 1e3)
+        h2d = (h_nodes.numel() + h_conns.numel() + h_x.numel() + h_y.numel()) * 4
+        d2h = (g_nodes.numel() + g_conns.numel() + g_x.numel() + 1) * 4
+        e2e = {"value": allreduce_sum(pg, units_per_step, dev) / (allreduce_max(pg, ems, dev) / 1e3),
+               "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+               "ms_per_step": round(ems, 3), "steps": K,
+               "path": "paper_2504_08339_b300.api.evaluate (torch.autograd.Function), MSE loss"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = cpu_baseline(name, cfg, spec, nodes, conns, args.seed)
