@@ -16,6 +16,10 @@ Parity status of each function (what pins it, in tests/test_oracle_*.py):
   backward   -- central finite differences of the forward; MLP special case
                 against numpy back-propagation.
   hyperneat  -- single-node CPPNs with closed forms over the grid.
+  distance   -- brute force with Python sets and dicts on small genomes,
+                closed forms (one weight / one extra gene apart), symmetry,
+                zero self-distance, row-permutation invariance, NaN for
+                malformed genomes.
   forward_recurrent -- linear (identity, sum) recurrent genomes against numpy
                 matrix powers, a self-loop closed form, equality with the
                 feed-forward forward on DAGs once T reaches their depth,
@@ -64,6 +68,7 @@ def _load():
             lib.or_backward.argtypes = [i32, i32, i32, i32, i32, P, P, P, i64, i32, P, P, P, P, P]
             lib.or_forward_recurrent.argtypes = [i32, i32, i32, i32, i32, P, P, P, i64, i32, i32,
                                                  P, P, P]
+            lib.or_distance.argtypes = [i32, i32, i32, i32, i32, P, P, dbl, dbl, P]
             lib.or_hyperneat.argtypes = [i32, i32, i32, P, P, i32, dbl, P, i64, P, P, P]
             for f in (lib.or_transform, lib.or_forward, lib.or_backward, lib.or_hyperneat):
                 f.restype = ctypes.c_int
@@ -150,6 +155,17 @@ def forward_recurrent(nodes, conns, inputs, I, O, T, with_bound=False, with_stat
     if with_status:
         res.append(st)
     return res[0] if len(res) == 1 else tuple(res)
+
+
+def distance(nodes, conns, I, O, c_disjoint=1.0, c_homologous=0.5):
+    """Compatibility distance of every pair (reading R12): dist [P, P] f64."""
+    nodes, conns = _f64(nodes), _f64(conns)
+    P, N, C = _shapes(nodes, conns)
+    out = np.empty((P, P), np.float64)
+    rc = _load().or_distance(P, N, C, I, O, _ptr(nodes), _ptr(conns), float(c_disjoint),
+                             float(c_homologous), _ptr(out))
+    assert rc == 0, rc
+    return out
 
 
 def backward(nodes, conns, inputs, I, O, grad_out, want_inputs=True):

@@ -44,6 +44,17 @@
  *   R9 HyperNEAT query: cell c = j*G + i has coordinates
  *      (-1 + 2i/(G-1), -1 + 2j/(G-1)); query (s, d) feeds
  *      (x_s, y_s, x_d, y_d, 1); the stored weight is o if |o| > thresh else 0.
+ *   R12 compatibility distance (Alg. 1 divides the population by distances;
+ *      App. A names the disjoint / homologous coefficients without the
+ *      formula): delta(A,B) = node term + connection term, each
+ *      (c_d * D + c_h * H) / max(count_A, count_B) (0 when both counts are 0).
+ *      Node genes are the valid node rows keyed by node key; connection genes
+ *      the valid connection rows (enabled or not) keyed by (in key, out key),
+ *      the lowest row of a repeated key counting once.  D counts the keys in
+ *      exactly one genome; H sums over shared keys |b_A - b_B| + |r_A - r_B|
+ *      + [act differs] + [agg differs] for nodes (0 when either row is an
+ *      input row) and |w_A - w_B| + [enabled differs] for connections.  A
+ *      genome with a status bit other than CYCLE has NaN distances.
  *   R11 recurrent ("concurrent", Sec. 3.3 names the network type without
  *      its calculation): T synchronous iterations; v^0 = inputs on the input
  *      rows and 0 elsewhere; in iteration t every valid non-input node takes
@@ -550,6 +561,129 @@ int or_forward_recurrent(int P, int N, int C, int I, int O, const double *nodes,
   }
   free(v);
   free(x);
+  g_free(&g);
+  return 0;
+}
+
+/* Compatibility distance (R12) for every pair of the P genomes:
+ * dist[P, P] (row-major, symmetric, zero diagonal for valid genomes). */
+typedef struct {
+  int n, m;            /* node genes, connection genes */
+  double *nkey, *nb, *nr;
+  int *nact, *nagg, *ninput;
+  double *cin, *cout, *cw;
+  int *cen;
+  int bad;             /* status bit other than CYCLE */
+} genes_t;
+
+typedef struct { double a, b; int row; } key2_t;
+static int cmp_key2(const void *x, const void *y) {
+  const key2_t *p = x, *q = y;
+  if (p->a != q->a) return p->a < q->a ? -1 : 1;
+  if (p->b != q->b) return p->b < q->b ? -1 : 1;
+  return p->row - q->row;
+}
+
+static void collect_genes(genes_t *G, const genome_t *g, const double *nodes, const double *conns) {
+  const int N = g->N, C = g->C, I = g->I;
+  G->bad = (g->status & ~ST_CYCLE) != 0;
+  /* node genes in ascending key (rows of equal keys cannot occur unless bad) */
+  key2_t *t = malloc(sizeof(key2_t) * (size_t)(N + C + 1));
+  int n = 0;
+  for (int r = 0; r < N; ++r)
+    if (g->valid[r]) { t[n].a = g->key[r]; t[n].b = 0; t[n].row = r; ++n; }
+  qsort(t, (size_t)n, sizeof(key2_t), cmp_key2);
+  G->n = n;
+  for (int i = 0; i < n; ++i) {
+    const int r = t[i].row;
+    G->nkey[i] = g->key[r];
+    G->nb[i] = nodes[(size_t)r * 5 + 1];
+    G->nr[i] = nodes[(size_t)r * 5 + 2];
+    /* ids of non-input rows (integral and in range unless the genome is bad) */
+    G->nact[i] = (r >= I && g->act[r] >= 0) ? g->act[r] : -1;
+    G->nagg[i] = (r >= I && g->agg[r] >= 0) ? g->agg[r] : -1;
+    G->ninput[i] = r < I;
+  }
+  /* connection genes: valid rows by (in, out, row); the first of a key counts */
+  int m = 0;
+  for (int j = 0; j < C; ++j) {
+    const double *row = conns + (size_t)j * 4;
+    if (isnan(row[0]) || isnan(row[1])) continue;
+    t[m].a = row[0]; t[m].b = row[1]; t[m].row = j; ++m;
+  }
+  qsort(t, (size_t)m, sizeof(key2_t), cmp_key2);
+  int k = 0;
+  for (int i = 0; i < m; ++i) {
+    if (k > 0 && t[i].a == G->cin[k - 1] && t[i].b == G->cout[k - 1]) continue;
+    const double *row = conns + (size_t)t[i].row * 4;
+    G->cin[k] = t[i].a;
+    G->cout[k] = t[i].b;
+    G->cw[k] = row[2];
+    G->cen[k] = !isnan(row[3]) && row[3] != 0.0;
+    ++k;
+  }
+  G->m = k;
+  free(t);
+}
+
+static double pair_distance(const genes_t *A, const genes_t *B, double cd, double ch) {
+  if (A->bad || B->bad) return NAN;
+  /* nodes: merge the two key-sorted lists */
+  int i = 0, j = 0, D = 0;
+  double H = 0.0;
+  while (i < A->n || j < B->n) {
+    if (j >= B->n || (i < A->n && A->nkey[i] < B->nkey[j])) { ++D; ++i; continue; }
+    if (i >= A->n || B->nkey[j] < A->nkey[i]) { ++D; ++j; continue; }
+    if (!A->ninput[i] && !B->ninput[j])
+      H += fabs(A->nb[i] - B->nb[j]) + fabs(A->nr[i] - B->nr[j]) +
+           (A->nact[i] != B->nact[j]) + (A->nagg[i] != B->nagg[j]);
+    ++i; ++j;
+  }
+  const int nmax = A->n > B->n ? A->n : B->n;
+  double d = nmax > 0 ? (cd * D + ch * H) / nmax : 0.0;
+  /* connections */
+  i = 0; j = 0; D = 0; H = 0.0;
+  while (i < A->m || j < B->m) {
+    int less_a = 0, less_b = 0;
+    if (j >= B->m) less_a = 1;
+    else if (i >= A->m) less_b = 1;
+    else if (A->cin[i] != B->cin[j]) { less_a = A->cin[i] < B->cin[j]; less_b = !less_a; }
+    else if (A->cout[i] != B->cout[j]) { less_a = A->cout[i] < B->cout[j]; less_b = !less_a; }
+    if (less_a) { ++D; ++i; continue; }
+    if (less_b) { ++D; ++j; continue; }
+    H += fabs(A->cw[i] - B->cw[j]) + (A->cen[i] != B->cen[j]);
+    ++i; ++j;
+  }
+  const int mmax = A->m > B->m ? A->m : B->m;
+  if (mmax > 0) d += (cd * D + ch * H) / mmax;
+  return d;
+}
+
+int or_distance(int P, int N, int C, int I, int O, const double *nodes, const double *conns,
+                double cd, double ch, double *dist) {
+  genome_t g;
+  if (P < 0 || N < I + O || C < 0) return -1;
+  if (g_alloc(&g, N, C, I, O)) return -2;
+  genes_t *G = calloc((size_t)P + 1, sizeof(genes_t));
+  for (int p = 0; p < P; ++p) {
+    genes_t *x = &G[p];
+    x->nkey = malloc(sizeof(double) * (size_t)(N + 1)); x->nb = malloc(sizeof(double) * (size_t)(N + 1));
+    x->nr = malloc(sizeof(double) * (size_t)(N + 1)); x->nact = malloc(sizeof(int) * (size_t)(N + 1));
+    x->nagg = malloc(sizeof(int) * (size_t)(N + 1)); x->ninput = malloc(sizeof(int) * (size_t)(N + 1));
+    x->cin = malloc(sizeof(double) * (size_t)(C + 1)); x->cout = malloc(sizeof(double) * (size_t)(C + 1));
+    x->cw = malloc(sizeof(double) * (size_t)(C + 1)); x->cen = malloc(sizeof(int) * (size_t)(C + 1));
+    parse_genome(&g, nodes + (size_t)p * N * 5, conns + (size_t)p * C * 4);
+    collect_genes(x, &g, nodes + (size_t)p * N * 5, conns + (size_t)p * C * 4);
+  }
+  for (int a = 0; a < P; ++a)
+    for (int b = 0; b < P; ++b)
+      dist[(size_t)a * P + b] = pair_distance(&G[a], &G[b], cd, ch);
+  for (int p = 0; p < P; ++p) {
+    genes_t *x = &G[p];
+    free(x->nkey); free(x->nb); free(x->nr); free(x->nact); free(x->nagg); free(x->ninput);
+    free(x->cin); free(x->cout); free(x->cw); free(x->cen);
+  }
+  free(G);
   g_free(&g);
   return 0;
 }
