@@ -115,7 +115,7 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="locomotion",
                     choices=["locomotion", "uneven", "differentiation", "hyperneat", "tiny",
-                             "recurrent"])
+                             "recurrent", "distance"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -232,7 +232,8 @@ def enabled_counts(nodes, conns):
 
 def workload(name, seed, pop=None):
     from workloads import CONFIGS, make_population
-    cfg = dict(CONFIGS[name])
+    # the distance workload is the locomotion population, all pairs
+    cfg = dict(CONFIGS["locomotion" if name == "distance" else name])
     if pop is not None:
         cfg["P"] = pop
     spec = cfg["spec"]
@@ -253,6 +254,9 @@ def describe(name, cfg, spec):
                 f"{mode}")
     if name == "hyperneat":
         return f"HyperNEAT query: pop={cfg['P']} CPPNs, 32x32 substrate (2^20 queries each)"
+    if name == "distance":
+        return (f"compatibility distance of every pair: the locomotion population "
+                f"(pop={cfg['P']}, N={spec.N}, C={spec.C}), {cfg['P']}^2 pairs per step")
     if name == "recurrent":
         return (f"recurrent networks: pop={cfg['P']}, {spec.I} in / {spec.O} out, N={spec.N}, "
                 f"C={spec.C}, 15 % back edges / self-loops, S={cfg['S']}, T={cfg['T']} "
@@ -291,6 +295,15 @@ def cpu_baseline(name, cfg, spec, nodes, conns, seed, budget_steps=None):
         oracle.backward(nodes[:k], conns[:k], x, spec.I, spec.O, go[..., None], want_inputs=True)
         units = float(E[:k].sum()) * cfg["S"]
         sample = f"{k} of {cfg['P']} genomes, forward + backward at S={cfg['S']}"
+    elif name == "distance":
+        k = budget_steps or 300
+        t0 = time.perf_counter()
+        oracle.distance(nodes[:k], conns[:k], spec.I, spec.O)
+        units = float(k) * k
+        sample = f"all pairs of {k} of {cfg['P']} genomes"
+        dt = time.perf_counter() - t0
+        return {"value": units / dt, "unit": "genome-pairs/s", "cores": 1, "kind": "oracle",
+                "sample": sample, "seconds": round(dt, 3)}
     elif name == "recurrent":
         k = budget_steps or 300
         x = np.random.default_rng(seed).standard_normal((k, cfg["S"], spec.I)).astype(np.float32)
@@ -400,6 +413,28 @@ def bench_ours(args, rank, world, local, pg):
         fwd_hbm = float((8 * E + 12 * Vn).sum() + 4 * S * spec.I + 4 * S * spec.O * P +
                         (0 if rec else 4 * S * Vn.sum()))
         fwd_chip = float(4 * S * (E + Vn).sum())
+    elif name == "distance":
+        from paper_2504_08339_b300.api import distance
+        d_nodes = torch.from_numpy(nodes).to(dev)
+        d_conns = torch.from_numpy(conns).to(dev)
+        tr = plan.transform(d_nodes, d_conns)
+        dist = torch.empty((P, P), device=dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))]
+
+        def run():
+            ev[0][0].record()
+            distance(d_nodes, d_conns, spec.I, spec.O, status=tr.status, out=dist)
+            ev[0][1].record()
+
+        units_per_step = float(P) * P
+        launches_per_step = 2
+        fwd_launches = 1
+        ro = None
+        # HBM: the padded genomes in, the distance matrix out; on chip: both
+        # genomes' sorted gene lists (16 B a gene) streamed through for every pair
+        alg_bytes = float(P * (spec.N * 5 + spec.C * 4) * 4 + 4.0 * P * P)
+        M = (~np.isnan(conns[:, :, 0]) & ~np.isnan(conns[:, :, 1])).sum(1)  # connection genes
+        chip_bytes = float(P) * P * 16.0 * 2 * float((Vn + M).mean())
     elif name == "recurrent":
         S, T = cfg["S"], cfg["T"]
         x = np.random.default_rng(args.seed + rank).standard_normal((P, S, spec.I)).astype(
@@ -483,6 +518,8 @@ def bench_ours(args, rank, world, local, pg):
             kernel = "k_hyperneat"
         elif name == "recurrent":
             kernel = "k_forward_rec"
+        elif name == "distance":
+            kernel = "k_distance"
         elif name == "differentiation":
             kernel = "k_backward<recompute>" if cfg.get("recompute") else "k_backward"
             fwd_us = 1e3 * ev_f[0].elapsed_time(ev_f[1])
@@ -605,7 +642,9 @@ def bench_ours(args, rank, world, local, pg):
 
     gpu_launches = launches_per_step * args.steps
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": METRIC if name != "distance" else "genome-pairs/s (compatibility distance)",
+        "value": value, "unit": UNIT if name != "distance" else "genome-pairs/s",
+        "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": round(ms_max / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic (seeded generators; random genomes shaped like the workload)",
@@ -632,7 +671,7 @@ def bench_reference(args, rank, world):
     name = args.config
     cfg, spec, nodes, conns = workload(name, args.seed, args.pop)
     budget = {"locomotion": 8, "uneven": 150, "differentiation": 4, "hyperneat": 1, "tiny": None,
-              "recurrent": 40}[name]
+              "recurrent": 40, "distance": 200}[name]
     for _ in range(max(3, args.warmup)):
         cpu_baseline(name, cfg, spec, nodes, conns, args.seed, budget)
     vals, secs = [], 0.0
@@ -645,15 +684,18 @@ def bench_reference(args, rank, world):
     value = float(np.mean(vals))
     del units
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "impl": "reference",
+        "metric": METRIC if name != "distance" else "genome-pairs/s (compatibility distance)",
+        "value": value, "unit": UNIT if name != "distance" else "genome-pairs/s", "n_gpus": world,
         "steps": args.steps, "warmup": max(3, args.warmup),
         "ms_per_step": round(1e3 * secs / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": describe(name, cfg, spec), "name": name, "pop": cfg["P"],
                    "pop_override": args.pop is not None},
         "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": rec["sample"], "value": value,
-                         "unit": UNIT},
-        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                         "unit": rec["unit"]},
+        "e2e": {"value": value, "unit": rec["unit"], "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
 

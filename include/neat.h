@@ -243,6 +243,30 @@ neat_status neat_forward_noalloc(const float *nodes, const float *conns, int P, 
                                  int I, int O, const float *inputs, int64_t in_pop_stride, int S,
                                  float *outputs, uint32_t *gstatus, cudaStream_t stream);
 
+/* Compatibility distance of every pair of P genomes (Alg. 1 speciates the
+ * population by distances between networks; App. A names the disjoint and
+ * homologous coefficients, 1.0 and 0.5 by default there).  For genomes A, B:
+ *   delta = (c_d D_n + c_h H_n) / max(n_A, n_B) + (c_d D_c + c_h H_c) / max(m_A, m_B)
+ * (a term is 0 when both counts are 0).  Node genes (n of them): the valid node
+ * rows, keyed by node key.  Connection genes (m): the valid connection rows,
+ * enabled or not, keyed by (in key, out key); the lowest row of a repeated
+ * key counts once.  D = keys present in exactly one genome; H = sum over shared
+ * keys of |b_A - b_B| + |r_A - r_B| + [act differs] + [agg differs] (0 for input
+ * rows) for nodes, |w_A - w_B| + [enabled differs] for connections.
+ *   nodes [P, N, 5], conns [P, C, 4] f32 as for neat_transform
+ *   gstatus optional [P] u32 (from neat_transform or neat_transform_recurrent):
+ *           a genome with a bit other than NEAT_G_CYCLE gets NaN distances;
+ *           NULL: every genome is taken as valid
+ *   dist    [P, P] f32 out, row-major; symmetric bit for bit, 0 on the diagonal
+ *   scratch caller-owned device memory, 256-byte aligned, at least
+ *           neat_distance_scratch_bytes(P, N, C) bytes
+ * Plan-free; asynchronous on `stream`.  NEAT_ERR_WORKSPACE if the scratch is
+ * too small, NEAT_ERR_UNSUPPORTED for sizes beyond the limits. */
+size_t neat_distance_scratch_bytes(int P, int N, int C);
+neat_status neat_distance(const float *nodes, const float *conns, const uint32_t *gstatus, int P,
+                          int N, int C, int I, int O, float c_disjoint, float c_homologous,
+                          float *dist, void *scratch, size_t scratch_bytes, cudaStream_t stream);
+
 /* Measurement helper (the paper has no counterpart): shared-memory read
  * bandwidth, the peak of the on-chip term of the roofline.  Launches `blocks`
  * CTAs of 512 threads on `stream`; each CTA fills a 64 KiB shared array

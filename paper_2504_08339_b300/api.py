@@ -186,6 +186,29 @@ class Plan:
         return out
 
 
+def distance(nodes, conns, I, O, status=None, c_disjoint=1.0, c_homologous=0.5, out=None,
+             stream=None):
+    """Compatibility distance of every pair of genomes: [P, P] f32 on the
+    device of `nodes` (status: optional [P] status words of a transform)."""
+    lib = _lib.load()
+    _need(nodes, "nodes", torch.float32)
+    _need(conns, "conns", torch.float32)
+    P, N, C = nodes.shape[0], nodes.shape[1], conns.shape[1]
+    if out is None:
+        out = torch.empty((P, P), dtype=torch.float32, device=nodes.device)
+    _need(out, "out", torch.float32, (P, P))
+    nbytes = lib.neat_distance_scratch_bytes(P, N, C)
+    if nbytes == 0:
+        raise _lib.NeatError("distance: unsupported sizes")
+    scratch = torch.empty((nbytes + 255,), dtype=torch.uint8, device=nodes.device)
+    base = (scratch.data_ptr() + 255) // 256 * 256
+    code = lib.neat_distance(_ptr(nodes), _ptr(conns), _ptr(status), P, N, C, I, O,
+                             float(c_disjoint), float(c_homologous), _ptr(out),
+                             ctypes.c_void_p(base), nbytes, _stream(stream))
+    _lib.check(code, "neat_distance")
+    return out
+
+
 class NeatFunction(torch.autograd.Function):
     """outputs = network(nodes, conns)(inputs), differentiable with respect to
     the bias/response columns of nodes, the weight column of conns and the

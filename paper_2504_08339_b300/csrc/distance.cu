@@ -1,0 +1,321 @@
+// Population-wide compatibility distance between genomes, the quantity
+// TensorNEAT's Alg. 1 divides the population by (App. A names its disjoint
+// and homologous coefficients).  For genomes A and B:
+//   delta = node term + connection term, each (c_d D + c_h H) / max(n_A, n_B)
+// (0 when both counts are 0).  Node genes: valid node rows keyed by node key;
+// connection genes: valid connection rows (enabled or not) keyed by
+// (in key, out key), the lowest row of a repeated key counting once.  D
+// counts the keys present in exactly one genome; H sums over shared keys
+// |b_A - b_B| + |r_A - r_B| + [act differs] + [agg differs] for nodes (0 when
+// either row is an input row) and |w_A - w_B| + [enabled differs] for
+// connections.  A genome with a status bit other than CYCLE gets NaN.
+//
+//  k_dist_prep  one CTA per genome: sorts its node genes by key and its
+//               connection genes by (in, out, row) in shared memory (bitonic),
+//               drops repeated connection keys, writes the sorted gene lists
+//  k_distance   one thread per pair (16 x 16 pairs per CTA): merges the two
+//               pairs of sorted lists (keys compared as order-preserving
+//               integers, so exactly like the float values)
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "neat_internal.cuh"
+
+namespace neat {
+namespace {
+
+// node gene: order-preserving key, bias, response, act | agg << 8 | input << 16
+struct __align__(16) NodeGene {
+  uint32_t key;
+  float bias;
+  float resp;
+  uint32_t meta;
+};
+// connection gene: order-preserving in / out keys, weight, enabled flag
+struct __align__(16) ConnGene {
+  uint32_t kin;
+  uint32_t kout;
+  float w;
+  uint32_t en;
+};
+
+constexpr uint32_t KEY_END = 0xffffffffu;  // above every finite key's encoding
+
+// float -> uint32 with the same order (finite values; -0 and +0 are equal)
+__device__ __forceinline__ uint32_t ord_key(float x) {
+  if (x == 0.0f) x = 0.0f;
+  const uint32_t b = __float_as_uint(x);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+__device__ __forceinline__ int pow2_ceil(int x) {
+  int p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+// Exclusive prefix sum of flags[0..n) in place (one CTA), returns the total.
+__device__ int cta_scan(int *flags, int n, int *wsum) {
+  const int tid = threadIdx.x, T = blockDim.x, lane = tid & 31, wid = tid >> 5;
+  const int per = (n + T - 1) / T, b = min(tid * per, n), e = min(b + per, n);
+  int s = 0;
+  for (int i = b; i < e; ++i) s += flags[i];
+  int x = s;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane == 31) wsum[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int a = lane < (T >> 5) ? wsum[lane] : 0;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, a, d);
+      if (lane >= d) a += y;
+    }
+    wsum[lane] = a;
+  }
+  __syncthreads();
+  int run = (wid > 0 ? wsum[wid - 1] : 0) + x - s;
+  const int total = wsum[(T >> 5) - 1];
+  for (int i = b; i < e; ++i) {
+    const int f = flags[i];
+    flags[i] = run;
+    run += f;
+  }
+  __syncthreads();
+  return total;
+}
+
+__global__ void __launch_bounds__(256) k_dist_prep(const float *__restrict__ nodes,
+                                                   const float *__restrict__ conns,
+                                                   const uint32_t *__restrict__ gstatus, int N,
+                                                   int C, int I, NodeGene *__restrict__ ng,
+                                                   ConnGene *__restrict__ cg,
+                                                   int4 *__restrict__ counts) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int g = blockIdx.x, tid = threadIdx.x, T = blockDim.x;
+  const int N2 = pow2_ceil(N), C2 = pow2_ceil(C);
+  uint64_t *nk = reinterpret_cast<uint64_t *>(sm);  // [N2] key << 32 | row
+  uint64_t *ck = nk + N2;                           // [C2] in << 32 | out
+  uint32_t *cr = reinterpret_cast<uint32_t *>(ck + C2);  // [C2] row
+  int *flag = reinterpret_cast<int *>(cr + C2);          // [C2]
+  __shared__ int wsum[32];
+  __shared__ int s_n;
+  const float *gn = nodes + size_t(g) * N * 5;
+  const float *gc = conns + size_t(g) * C * 4;
+  if (tid == 0) s_n = 0;
+  __syncthreads();
+
+  // node genes by key
+  int my_n = 0;
+  for (int r = tid; r < N2; r += T) {
+    const bool valid = r < N && !isnan(gn[r * 5]);
+    nk[r] = valid ? (uint64_t(ord_key(gn[r * 5])) << 32) | uint32_t(r) : ~0ull;
+    my_n += valid;
+  }
+  if (my_n) atomicAdd(&s_n, my_n);
+  // connection genes by (in, out), ties by row
+  for (int r = tid; r < C2; r += T) {
+    const bool valid = r < C && !isnan(gc[r * 4]) && !isnan(gc[r * 4 + 1]);
+    ck[r] = valid ? (uint64_t(ord_key(gc[r * 4])) << 32) | ord_key(gc[r * 4 + 1]) : ~0ull;
+    cr[r] = valid ? uint32_t(r) : 0xffffffffu;
+  }
+  __syncthreads();
+  for (int k = 2; k <= N2; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = tid; i < N2; i += T) {
+        const int l = i ^ j;
+        if (l > i) {
+          const uint64_t x = nk[i], y = nk[l];
+          if (((i & k) == 0) == (x > y)) { nk[i] = y; nk[l] = x; }
+        }
+      }
+      __syncthreads();
+    }
+  for (int k = 2; k <= C2; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = tid; i < C2; i += T) {
+        const int l = i ^ j;
+        if (l > i) {
+          const uint64_t x = ck[i], y = ck[l];
+          const uint32_t xr = cr[i], yr = cr[l];
+          const bool gt = x > y || (x == y && xr > yr);
+          if (((i & k) == 0) == gt) {
+            ck[i] = y; ck[l] = x;
+            cr[i] = yr; cr[l] = xr;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  const int n = s_n;
+  for (int i = tid; i < n; i += T) {
+    const int r = int(nk[i] & 0xffffffffu);
+    const float *row = gn + r * 5;
+    NodeGene q;
+    q.key = uint32_t(nk[i] >> 32);
+    q.bias = row[1];
+    q.resp = row[2];
+    // ids of non-input rows (integral and in range unless the genome is bad)
+    const uint32_t act = r >= I ? uint32_t(int(row[3]) & 0xff) : 0xffu;
+    const uint32_t agg = r >= I ? uint32_t(int(row[4]) & 0xff) : 0xffu;
+    q.meta = act | (agg << 8) | (uint32_t(r < I) << 16);
+    ng[size_t(g) * N + i] = q;
+  }
+  // first row of every (in, out) key
+  for (int i = tid; i < C; i += T)
+    flag[i] = (cr[i] != 0xffffffffu && (i == 0 || ck[i] != ck[i - 1])) ? 1 : 0;
+  __syncthreads();
+  // keep = flag before the scan overwrites it
+  for (int i = tid; i < C; i += T) cr[i] = flag[i] ? cr[i] : 0xffffffffu;
+  __syncthreads();
+  const int m = cta_scan(flag, C, wsum);
+  for (int i = tid; i < C; i += T) {
+    if (cr[i] == 0xffffffffu) continue;
+    const float *row = gc + cr[i] * 4;
+    ConnGene q;
+    q.kin = uint32_t(ck[i] >> 32);
+    q.kout = uint32_t(ck[i] & 0xffffffffu);
+    q.w = row[2];
+    q.en = (!isnan(row[3]) && row[3] != 0.0f) ? 1u : 0u;
+    cg[size_t(g) * C + flag[i]] = q;
+  }
+  if (tid == 0) {
+    const bool bad = gstatus != nullptr && (gstatus[g] & ~uint32_t(NEAT_G_CYCLE)) != 0u;
+    counts[g] = make_int4(n, m, bad ? 1 : 0, 0);
+  }
+}
+
+__device__ __forceinline__ NodeGene ld_ng(const NodeGene *p) {
+  const uint4 x = __ldg(reinterpret_cast<const uint4 *>(p));
+  NodeGene q;
+  q.key = x.x; q.bias = __uint_as_float(x.y); q.resp = __uint_as_float(x.z); q.meta = x.w;
+  return q;
+}
+__device__ __forceinline__ ConnGene ld_cg(const ConnGene *p) {
+  const uint4 x = __ldg(reinterpret_cast<const uint4 *>(p));
+  ConnGene q;
+  q.kin = x.x; q.kout = x.y; q.w = __uint_as_float(x.z); q.en = x.w;
+  return q;
+}
+
+__global__ void __launch_bounds__(256) k_distance(const NodeGene *__restrict__ ng,
+                                                  const ConnGene *__restrict__ cg,
+                                                  const int4 *__restrict__ counts, int P, int N,
+                                                  int C, float cd, float ch,
+                                                  float *__restrict__ dist) {
+  const int b = blockIdx.x * 16 + threadIdx.x, a = blockIdx.y * 16 + threadIdx.y;
+  if (a >= P || b >= P) return;
+  const int4 ca = __ldg(counts + a), cb = __ldg(counts + b);
+  float d = qnan();
+  if (!ca.z && !cb.z) {
+    // nodes: one step per key of either list (merge)
+    const NodeGene *A = ng + size_t(a) * N, *B = ng + size_t(b) * N;
+    int i = 0, j = 0, D = 0;
+    float H = 0.0f;
+    while (i < ca.x || j < cb.x) {
+      const NodeGene x = ld_ng(A + min(i, ca.x - 1 < 0 ? 0 : ca.x - 1));
+      const NodeGene y = ld_ng(B + min(j, cb.x - 1 < 0 ? 0 : cb.x - 1));
+      const uint32_t kx = i < ca.x ? x.key : KEY_END, ky = j < cb.x ? y.key : KEY_END;
+      if (kx == ky) {
+        if (!((x.meta | y.meta) & 0x10000u))
+          H += fabsf(x.bias - y.bias) + fabsf(x.resp - y.resp) +
+               float((x.meta & 0xffu) != (y.meta & 0xffu)) +
+               float(((x.meta >> 8) & 0xffu) != ((y.meta >> 8) & 0xffu));
+        ++i;
+        ++j;
+      } else {
+        ++D;
+        if (kx < ky) ++i; else ++j;
+      }
+    }
+    const int nmax = max(ca.x, cb.x);
+    d = nmax > 0 ? (cd * float(D) + ch * H) / float(nmax) : 0.0f;
+    // connections
+    const ConnGene *X = cg + size_t(a) * C, *Y = cg + size_t(b) * C;
+    i = 0; j = 0; D = 0; H = 0.0f;
+    while (i < ca.y || j < cb.y) {
+      const ConnGene x = ld_cg(X + min(i, ca.y - 1 < 0 ? 0 : ca.y - 1));
+      const ConnGene y = ld_cg(Y + min(j, cb.y - 1 < 0 ? 0 : cb.y - 1));
+      const uint64_t kx = i < ca.y ? (uint64_t(x.kin) << 32 | x.kout) : ~0ull;
+      const uint64_t ky = j < cb.y ? (uint64_t(y.kin) << 32 | y.kout) : ~0ull;
+      if (kx == ky) {
+        H += fabsf(x.w - y.w) + float(x.en != y.en);
+        ++i;
+        ++j;
+      } else {
+        ++D;
+        if (kx < ky) ++i; else ++j;
+      }
+    }
+    const int mmax = max(ca.y, cb.y);
+    if (mmax > 0) d += (cd * float(D) + ch * H) / float(mmax);
+  }
+  dist[size_t(a) * P + b] = d;
+}
+
+size_t prep_smem(int N, int C) {
+  int N2 = 1, C2 = 1;
+  while (N2 < N) N2 <<= 1;
+  while (C2 < C) C2 <<= 1;
+  return size_t(N2) * 8 + size_t(C2) * (8 + 4 + 4);
+}
+
+struct DistLayout {
+  size_t ng, cg, counts, total;
+};
+DistLayout dist_layout(int P, int N, int C) {
+  DistLayout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = (off + bytes + 255) / 256 * 256; return o; };
+  L.ng = take(sizeof(NodeGene) * size_t(P) * N);
+  L.cg = take(sizeof(ConnGene) * size_t(P) * C);
+  L.counts = take(sizeof(int4) * size_t(P));
+  L.total = off;
+  return L;
+}
+
+}  // namespace
+}  // namespace neat
+
+extern "C" size_t neat_distance_scratch_bytes(int P, int N, int C) {
+  if (P < 0 || N < 1 || N > NEAT_MAX_NODES || C < 1 || C > NEAT_MAX_CONNS) return 0;
+  return neat::dist_layout(P, N, C).total;
+}
+
+extern "C" neat_status neat_distance(const float *nodes, const float *conns,
+                                     const uint32_t *gstatus, int P, int N, int C, int I, int O,
+                                     float c_disjoint, float c_homologous, float *dist,
+                                     void *scratch, size_t scratch_bytes, cudaStream_t stream) {
+  if (P < 0 || N < 1 || N > NEAT_MAX_NODES || C < 1 || C > NEAT_MAX_CONNS || I < 1 || O < 1 ||
+      N < I + O)
+    return NEAT_ERR_UNSUPPORTED;
+  if (P == 0) return NEAT_OK;
+  if (int64_t(P) * P > (int64_t(1) << 40)) return NEAT_ERR_UNSUPPORTED;
+  if (nodes == nullptr || conns == nullptr || dist == nullptr || scratch == nullptr ||
+      (reinterpret_cast<uintptr_t>(nodes) % 4) != 0 || (reinterpret_cast<uintptr_t>(conns) % 4) != 0 ||
+      (reinterpret_cast<uintptr_t>(dist) % 4) != 0 ||
+      (reinterpret_cast<uintptr_t>(scratch) % 256) != 0 ||
+      (gstatus != nullptr && (reinterpret_cast<uintptr_t>(gstatus) % 4) != 0))
+    return NEAT_ERR_ARG;
+  const neat::DistLayout L = neat::dist_layout(P, N, C);
+  if (scratch_bytes < L.total) return NEAT_ERR_WORKSPACE;
+  char *base = static_cast<char *>(scratch);
+  auto *ng = reinterpret_cast<neat::NodeGene *>(base + L.ng);
+  auto *cg = reinterpret_cast<neat::ConnGene *>(base + L.cg);
+  auto *counts = reinterpret_cast<int4 *>(base + L.counts);
+  const size_t smem = neat::prep_smem(N, C);
+  if (cudaFuncSetAttribute(neat::k_dist_prep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           int(smem)) != cudaSuccess)
+    return NEAT_ERR_UNSUPPORTED;
+  neat::k_dist_prep<<<P, 256, smem, stream>>>(nodes, conns, gstatus, N, C, I, ng, cg, counts);
+  if (cudaGetLastError() != cudaSuccess) return NEAT_ERR_CUDA;
+  const dim3 grid(unsigned((P + 15) / 16), unsigned((P + 15) / 16)), block(16, 16);
+  neat::k_distance<<<grid, block, 0, stream>>>(ng, cg, counts, P, N, C, c_disjoint, c_homologous,
+                                               dist);
+  return cudaGetLastError() == cudaSuccess ? NEAT_OK : NEAT_ERR_CUDA;
+}
