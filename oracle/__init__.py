@@ -20,6 +20,9 @@ Parity status of each function (what pins it, in tests/test_oracle_*.py):
                 closed forms (one weight / one extra gene apart), symmetry,
                 zero self-distance, row-permutation invariance, NaN for
                 malformed genomes.
+  apply_ops  -- hand-written expected tensors of operation sequences (first
+                NaN row, reuse of a freed lower row, full tensors, ranges),
+                no-op invariance, transform of the result.
   forward_recurrent -- linear (identity, sum) recurrent genomes against numpy
                 matrix powers, a self-loop closed form, equality with the
                 feed-forward forward on DAGs once T reaches their depth,
@@ -69,6 +72,7 @@ def _load():
             lib.or_forward_recurrent.argtypes = [i32, i32, i32, i32, i32, P, P, P, i64, i32, i32,
                                                  P, P, P]
             lib.or_distance.argtypes = [i32, i32, i32, i32, i32, P, P, dbl, dbl, P]
+            lib.or_apply_ops.argtypes = [i32, i32, i32, P, P, P, i32, P]
             lib.or_hyperneat.argtypes = [i32, i32, i32, P, P, i32, dbl, P, i64, P, P, P]
             for f in (lib.or_transform, lib.or_forward, lib.or_backward, lib.or_hyperneat):
                 f.restype = ctypes.c_int
@@ -166,6 +170,20 @@ def distance(nodes, conns, I, O, c_disjoint=1.0, c_homologous=0.5):
                              float(c_homologous), _ptr(out))
     assert rc == 0, rc
     return out
+
+
+def apply_ops(nodes, conns, ops):
+    """Tensorized operations (reading R13) on copies of the population:
+    (nodes, conns, op_status [P] u32).  ops is [P, K, 8]."""
+    nodes, conns = _f64(nodes).copy(), _f64(conns).copy()
+    P, N, C = _shapes(nodes, conns)
+    ops = _f64(ops)
+    assert ops.ndim == 3 and ops.shape[0] == P and ops.shape[2] == 8
+    st = np.empty(P, np.uint32)
+    rc = _load().or_apply_ops(P, N, C, _ptr(nodes), _ptr(conns), _ptr(ops), ops.shape[1],
+                              _ptr(st))
+    assert rc == 0, rc
+    return nodes, conns, st
 
 
 def backward(nodes, conns, inputs, I, O, grad_out, want_inputs=True):

@@ -44,6 +44,18 @@
  *   R9 HyperNEAT query: cell c = j*G + i has coordinates
  *      (-1 + 2i/(G-1), -1 + 2j/(G-1)); query (s, d) feeds
  *      (x_s, y_s, x_d, y_d, 1); the stored weight is o if |o| > thresh else 0.
+ *   R13 tensorized operations (Sec. 3.2): a list of K operations per genome,
+ *      applied in order.  Each is 8 floats (kind, row, v0..v5):
+ *        1 add node:  nodes[r] = (v0..v4) at r = the first row whose key is NaN
+ *        2 remove node: nodes[row] = NaN (all columns)
+ *        3 add connection: conns[r] = (v0..v3) at r = the first row with a
+ *          NaN key column
+ *        4 remove connection: conns[row] = NaN
+ *        5 set node attribute: nodes[row][v0] = v1 (column 1..4)
+ *        6 set connection attribute: conns[row][v0] = v1 (column 2..3)
+ *        0 (or any other kind): nothing
+ *      An operation with no free row, a row out of range or a column out of
+ *      range changes nothing and sets bit k (k < 32) of the genome's op status.
  *   R12 compatibility distance (Alg. 1 divides the population by distances;
  *      App. A names the disjoint / homologous coefficients without the
  *      formula): delta(A,B) = node term + connection term, each
@@ -562,6 +574,51 @@ int or_forward_recurrent(int P, int N, int C, int I, int O, const double *nodes,
   free(v);
   free(x);
   g_free(&g);
+  return 0;
+}
+
+/* Tensorized operations (R13) on every genome, in place: nodes [P,N,5],
+ * conns [P,C,4], ops [P,K,8]; op_status [P] receives the failed-op bits. */
+int or_apply_ops(int P, int N, int C, double *nodes, double *conns, const double *ops, int K,
+                 uint32_t *op_status) {
+  if (P < 0 || N < 1 || C < 1 || K < 0) return -1;
+  for (int p = 0; p < P; ++p) {
+    double *gn = nodes + (size_t)p * N * 5, *gc = conns + (size_t)p * C * 4;
+    uint32_t st = 0;
+    for (int k = 0; k < K; ++k) {
+      const double *op = ops + ((size_t)p * K + k) * 8;
+      const double kind = op[0], rowf = op[1];
+      int ok = 1;
+      if (kind == 1.0 || kind == 3.0) {
+        const int cols = kind == 1.0 ? 5 : 4, rows = kind == 1.0 ? N : C;
+        double *t = kind == 1.0 ? gn : gc;
+        int r = -1;
+        for (int i = 0; i < rows && r < 0; ++i) {
+          const int pad = kind == 1.0 ? isnan(t[(size_t)i * 5]) : (isnan(t[(size_t)i * 4]) || isnan(t[(size_t)i * 4 + 1]));
+          if (pad) r = i;
+        }
+        if (r < 0) ok = 0;
+        else for (int c = 0; c < cols; ++c) t[(size_t)r * cols + c] = op[2 + c];
+      } else if (kind == 2.0 || kind == 4.0) {
+        const int cols = kind == 2.0 ? 5 : 4, rows = kind == 2.0 ? N : C;
+        double *t = kind == 2.0 ? gn : gc;
+        if (!(rowf >= 0 && rowf < rows && rowf == floor(rowf))) ok = 0;
+        else for (int c = 0; c < cols; ++c) t[(size_t)rowf * cols + c] = NAN;
+      } else if (kind == 5.0 || kind == 6.0) {
+        const int cols = kind == 5.0 ? 5 : 4, rows = kind == 5.0 ? N : C;
+        const int lo = kind == 5.0 ? 1 : 2, hi = cols - 1;
+        double *t = kind == 5.0 ? gn : gc;
+        const double col = op[2];
+        if (!(rowf >= 0 && rowf < rows && rowf == floor(rowf)) ||
+            !(col >= lo && col <= hi && col == floor(col)))
+          ok = 0;
+        else
+          t[(size_t)rowf * cols + (size_t)col] = op[3];
+      }
+      if (!ok && k < 32) st |= 1u << k;
+    }
+    if (op_status) op_status[p] = st;
+  }
   return 0;
 }
 
