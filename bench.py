@@ -115,7 +115,7 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="locomotion",
                     choices=["locomotion", "uneven", "differentiation", "hyperneat", "tiny",
-                             "recurrent", "distance"])
+                             "recurrent", "distance", "mutate"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -233,7 +233,7 @@ def enabled_counts(nodes, conns):
 def workload(name, seed, pop=None):
     from workloads import CONFIGS, make_population
     # the distance workload is the locomotion population, all pairs
-    cfg = dict(CONFIGS["locomotion" if name == "distance" else name])
+    cfg = dict(CONFIGS["locomotion" if name in ("distance", "mutate") else name])
     if pop is not None:
         cfg["P"] = pop
     spec = cfg["spec"]
@@ -254,6 +254,10 @@ def describe(name, cfg, spec):
                 f"{mode}")
     if name == "hyperneat":
         return f"HyperNEAT query: pop={cfg['P']} CPPNs, 32x32 substrate (2^20 queries each)"
+    if name == "mutate":
+        return (f"one generation's structural edits: pop={cfg['P']} locomotion genomes, "
+                f"16 Sec. 3.2 operations each, then the transform (population restored "
+                f"on the device before every step)")
     if name == "distance":
         return (f"compatibility distance of every pair: the locomotion population "
                 f"(pop={cfg['P']}, N={spec.N}, C={spec.C}), {cfg['P']}^2 pairs per step")
@@ -295,6 +299,17 @@ def cpu_baseline(name, cfg, spec, nodes, conns, seed, budget_steps=None):
         oracle.backward(nodes[:k], conns[:k], x, spec.I, spec.O, go[..., None], want_inputs=True)
         units = float(E[:k].sum()) * cfg["S"]
         sample = f"{k} of {cfg['P']} genomes, forward + backward at S={cfg['S']}"
+    elif name == "mutate":
+        from workloads import random_ops
+        k = budget_steps or 2000
+        ops = random_ops(seed, nodes[:k], conns[:k], spec.I, 16)
+        t0 = time.perf_counter()
+        n2, c2, _ = oracle.apply_ops(nodes[:k], conns[:k], ops)
+        oracle.transform(n2, c2, spec.I, spec.O)
+        dt = time.perf_counter() - t0
+        return {"value": k / dt, "unit": "genomes/s", "cores": 1, "kind": "oracle",
+                "sample": f"{k} of {cfg['P']} genomes: 16 operations + transform",
+                "seconds": round(dt, 3)}
     elif name == "distance":
         k = budget_steps or 300
         t0 = time.perf_counter()
@@ -413,6 +428,35 @@ def bench_ours(args, rank, world, local, pg):
         fwd_hbm = float((8 * E + 12 * Vn).sum() + 4 * S * spec.I + 4 * S * spec.O * P +
                         (0 if rec else 4 * S * Vn.sum()))
         fwd_chip = float(4 * S * (E + Vn).sum())
+    elif name == "mutate":
+        from workloads import random_ops
+        K = 16
+        ops = random_ops(args.seed + rank, nodes, conns, spec.I, K)
+        d_nodes0 = torch.from_numpy(nodes).to(dev)
+        d_conns0 = torch.from_numpy(conns).to(dev)
+        d_nodes = d_nodes0.clone()
+        d_conns = d_conns0.clone()
+        d_ops = torch.from_numpy(ops).to(dev)
+        tr, op_st = plan.mutate_transform(d_nodes, d_conns, d_ops)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))]
+
+        def run():
+            d_nodes.copy_(d_nodes0)
+            d_conns.copy_(d_conns0)
+            ev[0][0].record()
+            plan.mutate_transform(d_nodes, d_conns, d_ops, op_status=op_st, out=tr)
+            ev[0][1].record()
+
+        units_per_step = float(P)
+        launches_per_step = 1 + 4 + 3  # operations, transform pipeline, level batches
+        fwd_launches = 1
+        ro = None
+        # the operations list in; the population read by the operations and by
+        # the transform; order / layer and the packed programs written
+        pop_bytes = P * (spec.N * 5 + spec.C * 4) * 4
+        alg_bytes = float(P * K * 32 + 2 * pop_bytes + P * spec.N * 8 +
+                          (16 * Vn + 8 * E).sum())
+        chip_bytes = 0.0
     elif name == "distance":
         from paper_2504_08339_b300.api import distance
         d_nodes = torch.from_numpy(nodes).to(dev)
@@ -520,6 +564,8 @@ def bench_ours(args, rank, world, local, pg):
             kernel = "k_forward_rec"
         elif name == "distance":
             kernel = "k_distance"
+        elif name == "mutate":
+            kernel = "k_apply_ops + transform pipeline"
         elif name == "differentiation":
             kernel = "k_backward<recompute>" if cfg.get("recompute") else "k_backward"
             fwd_us = 1e3 * ev_f[0].elapsed_time(ev_f[1])
@@ -642,8 +688,9 @@ def bench_ours(args, rank, world, local, pg):
 
     gpu_launches = launches_per_step * args.steps
     line = {
-        "metric": METRIC if name != "distance" else "genome-pairs/s (compatibility distance)",
-        "value": value, "unit": UNIT if name != "distance" else "genome-pairs/s",
+        "metric": {"distance": "genome-pairs/s (compatibility distance)",
+                   "mutate": "genomes/s (operations + transform)"}.get(name, METRIC),
+        "value": value, "unit": {"distance": "genome-pairs/s", "mutate": "genomes/s"}.get(name, UNIT),
         "n_gpus": world, "steps": args.steps,
         "warmup": max(3, args.warmup), "ms_per_step": round(ms_max / args.steps, 4),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -671,7 +718,7 @@ def bench_reference(args, rank, world):
     name = args.config
     cfg, spec, nodes, conns = workload(name, args.seed, args.pop)
     budget = {"locomotion": 8, "uneven": 150, "differentiation": 4, "hyperneat": 1, "tiny": None,
-              "recurrent": 40, "distance": 200}[name]
+              "recurrent": 40, "distance": 200, "mutate": 2000}[name]
     for _ in range(max(3, args.warmup)):
         cpu_baseline(name, cfg, spec, nodes, conns, args.seed, budget)
     vals, secs = [], 0.0
@@ -685,8 +732,9 @@ def bench_reference(args, rank, world):
     del units
     line = {
         "impl": "reference",
-        "metric": METRIC if name != "distance" else "genome-pairs/s (compatibility distance)",
-        "value": value, "unit": UNIT if name != "distance" else "genome-pairs/s", "n_gpus": world,
+        "metric": {"distance": "genome-pairs/s (compatibility distance)",
+                   "mutate": "genomes/s (operations + transform)"}.get(name, METRIC),
+        "value": value, "unit": rec["unit"], "n_gpus": world,
         "steps": args.steps, "warmup": max(3, args.warmup),
         "ms_per_step": round(1e3 * secs / args.steps, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",

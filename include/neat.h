@@ -243,6 +243,30 @@ neat_status neat_forward_noalloc(const float *nodes, const float *conns, int P, 
                                  int I, int O, const float *inputs, int64_t in_pop_stride, int S,
                                  float *outputs, uint32_t *gstatus, cudaStream_t stream);
 
+/* Tensorized operations of Sec. 3.2 on the population tensors, in place (no
+ * counterpart needs a host round trip: the list is data).  ops [P, K, 8] f32:
+ * operation k of genome g is (kind, row, v0..v5), applied in order k = 0..K-1:
+ *   1 add node:        nodes[r] = (v0..v4), r = the first row whose key is NaN
+ *   2 remove node:     nodes[row] = NaN
+ *   3 add connection:  conns[r] = (v0..v3), r = the first row with a NaN key
+ *   4 remove connection: conns[row] = NaN
+ *   5 set node attribute: nodes[row][v0] = v1 (column v0 in 1..4)
+ *   6 set connection attribute: conns[row][v0] = v1 (column v0 in 2..3)
+ *   any other kind: nothing
+ * An operation with no free row, a row outside the table or a column outside
+ * its range changes nothing and sets bit k (k < 32) of op_status[g]
+ * (optional [P] u32 out).  Removing a node leaves its connections (remove
+ * them with their own operations).  One warp per genome, asynchronous. */
+neat_status neat_apply_ops(float *nodes, float *conns, int P, int N, int C, const float *ops,
+                           int K, uint32_t *op_status, cudaStream_t stream);
+
+/* neat_apply_ops on the plan's population sizes followed by neat_transform
+ * (same arguments), on one stream: one generation's structural edits and the
+ * new programs without a round trip to the host. */
+neat_status neat_mutate_transform(neat_plan *plan, float *nodes, float *conns, const float *ops,
+                                  int K, uint32_t *op_status, int32_t *order, int32_t *layer,
+                                  int32_t *n_layers, uint32_t *gstatus, cudaStream_t stream);
+
 /* Compatibility distance of every pair of P genomes (Alg. 1 speciates the
  * population by distances between networks; App. A names the disjoint and
  * homologous coefficients, 1.0 and 0.5 by default there).  For genomes A, B:

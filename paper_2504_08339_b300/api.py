@@ -102,6 +102,30 @@ class Plan:
                    "neat_transform")
         return out
 
+    def mutate_transform(self, nodes, conns, ops, op_status=None, out: Transformed | None = None,
+                         stream=None):
+        """Apply the Sec. 3.2 operation list ops [P, K, 8] to nodes / conns in
+        place, then transform; returns (Transformed, op_status [P])."""
+        P, N, C = self.P, self.N, self.C
+        _need(nodes, "nodes", torch.float32, (P, N, 5))
+        _need(conns, "conns", torch.float32, (P, C, 4))
+        _need(ops, "ops", torch.float32)
+        if ops.dim() != 3 or ops.shape[0] != P or ops.shape[2] != 8:
+            raise _lib.NeatError("ops must be [P, K, 8]")
+        dev = nodes.device
+        if op_status is None:
+            op_status = torch.empty((P,), dtype=torch.int32, device=dev)
+        if out is None:
+            out = Transformed(torch.empty((P, N), dtype=torch.int32, device=dev),
+                              torch.empty((P, N), dtype=torch.int32, device=dev),
+                              torch.empty((P,), dtype=torch.int32, device=dev),
+                              torch.empty((P,), dtype=torch.int32, device=dev))
+        _lib.check(self._lib.neat_mutate_transform(
+            self._h, _ptr(nodes), _ptr(conns), _ptr(ops), ops.shape[1], _ptr(op_status),
+            _ptr(out.order), _ptr(out.layer), _ptr(out.n_layers), _ptr(out.status),
+            _stream(stream)), "neat_mutate_transform")
+        return out, op_status
+
     def transform_recurrent(self, nodes, conns, status=None, stream=None):
         """Transformation for recurrent networks (cycles legal); returns the
         per-genome status words [P] (int32 view of the u32 bits)."""
@@ -184,6 +208,23 @@ class Plan:
         _lib.check(self._lib.neat_hyperneat_query(self._h, int(grid), float(thresh), _ptr(out),
                                                   _stream(stream)), "neat_hyperneat_query")
         return out
+
+
+def apply_ops(nodes, conns, ops, op_status=None, stream=None):
+    """Sec. 3.2 operations ops [P, K, 8] on nodes [P, N, 5] / conns [P, C, 4]
+    in place; returns op_status [P] (int32 view of the failed-op bits)."""
+    lib = _lib.load()
+    _need(nodes, "nodes", torch.float32)
+    _need(conns, "conns", torch.float32)
+    _need(ops, "ops", torch.float32)
+    P, N, C = nodes.shape[0], nodes.shape[1], conns.shape[1]
+    if ops.dim() != 3 or ops.shape[0] != P or ops.shape[2] != 8:
+        raise _lib.NeatError("ops must be [P, K, 8]")
+    if op_status is None:
+        op_status = torch.empty((P,), dtype=torch.int32, device=nodes.device)
+    _lib.check(lib.neat_apply_ops(_ptr(nodes), _ptr(conns), P, N, C, _ptr(ops), ops.shape[1],
+                                  _ptr(op_status), _stream(stream)), "neat_apply_ops")
+    return op_status
 
 
 def distance(nodes, conns, I, O, status=None, c_disjoint=1.0, c_homologous=0.5, out=None,

@@ -304,6 +304,23 @@ neat_status neat_hyperneat_query(neat_plan *plan, int grid, float thresh, float 
                                             plan->sm_count * occ, stream));
 }
 
+neat_status neat_mutate_transform(neat_plan *plan, float *nodes, float *conns, const float *ops,
+                                  int K, uint32_t *op_status, int32_t *order, int32_t *layer,
+                                  int32_t *n_layers, uint32_t *gstatus, cudaStream_t stream) {
+  if (plan == nullptr || K < 0) return NEAT_ERR_ARG;
+  if (plan->P > 0 && (K > 0 && ops == nullptr)) return NEAT_ERR_ARG;
+  if (plan->P > 0 && ((K > 0 && !aligned(ops, 4)) || (op_status && !aligned(op_status, 4))))
+    return NEAT_ERR_ARG;
+  if (plan->P > 0 && (nodes == nullptr || conns == nullptr)) return NEAT_ERR_ARG;
+  if (plan->P > 0 && K > 0) {
+    if (!aligned(nodes, 4) || !aligned(conns, 16)) return NEAT_ERR_ARG;
+    cudaError_t e = neat::launch_apply_ops(nodes, conns, plan->P, plan->N, plan->C, ops, K,
+                                           op_status, stream);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  return neat_transform(plan, nodes, conns, order, layer, n_layers, gstatus, stream);
+}
+
 neat_status neat_transform_recurrent(neat_plan *plan, const float *nodes, const float *conns,
                                      uint32_t *gstatus, cudaStream_t stream) {
   if (plan == nullptr) return NEAT_ERR_ARG;

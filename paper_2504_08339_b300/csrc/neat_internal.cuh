@@ -324,6 +324,9 @@ cudaError_t launch_forward_plain(const Ws &w, const float *inputs, int64_t strid
 cudaError_t launch_forward_recurrent(const Ws &w, const float *inputs, int64_t stride, int S,
                                      int T, float *outputs, int warps, int grid, cudaStream_t st);
 int forward_rec_occupancy(int warps);
+// tensorized operations (Sec. 3.2) in place, one warp per genome
+cudaError_t launch_apply_ops(float *nodes, float *conns, int P, int N, int C, const float *ops,
+                             int K, uint32_t *op_status, cudaStream_t st);
 // Backward: `warps` per CTA, `smem_bytes` of dynamic shared memory (at least
 // backward_smem(N, C, 1)); a genome runs on as many warps as blocks of its
 // size fit in smem_bytes.

@@ -9,5 +9,5 @@ library consume what it produces, and neither is imported here.
 from .generators import (  # noqa: F401
     ACT, AGG, GenomeSpec, random_genome, make_population, CONFIGS,
     population_for, xor_inputs, locomotion_inputs, uneven_inputs,
-    regression_batch,
+    regression_batch, random_ops,
 )

@@ -265,3 +265,58 @@ def regression_batch(seed: int, S: int):
     xd = x.astype(np.float64)
     y = (np.sin(xd[:, 0] * xd[:, 1]) + 0.5 * xd[:, 2] ** 2).astype(np.float32)
     return x[None], y
+
+
+def random_ops(seed: int, nodes: np.ndarray, conns: np.ndarray, I: int, K: int):
+    """Seeded operation lists ops [P, K, 8] for the Sec. 3.2 operation kernel
+    (kind, row, v0..v5), drawn like a NEAT generation: an enabled connection
+    split by a new node (disable it, add the node, add the two connections),
+    connections added between existing keys, connections removed or disabled,
+    fresh weights and biases (drawn, not computed from the old values), and a
+    few operations that must fail (no free row or a bad column).  Only input
+    generation: no network arithmetic."""
+    rng = np.random.default_rng([seed, 11])
+    P, N = nodes.shape[0], nodes.shape[1]
+    ops = np.zeros((P, K, 8), np.float32)
+    for g in range(P):
+        live = np.flatnonzero(~np.isnan(conns[g, :, 0]) & ~np.isnan(conns[g, :, 1]))
+        en = live[conns[g, live, 3] != 0]
+        keys = nodes[g, ~np.isnan(nodes[g, :, 0]), 0]
+        hid = np.flatnonzero(~np.isnan(nodes[g, :, 0]))
+        hid = hid[hid >= I]
+        new_key = float(8 * N + g % 1000)
+        k = 0
+
+        def put(kind, row=0.0, *v):
+            nonlocal k
+            if k < K:
+                ops[g, k, 0], ops[g, k, 1] = kind, row
+                ops[g, k, 2:2 + len(v)] = v
+                k += 1
+
+        if en.size and K - k >= 4:  # split an enabled connection
+            r = int(rng.choice(en))
+            a, b, w = conns[g, r, 0], conns[g, r, 1], conns[g, r, 2]
+            put(6, r, 3, 0.0)
+            put(1, 0, new_key, rng.normal(0, 0.5), 1.0, rng.integers(0, 5), rng.integers(0, 4))
+            put(3, 0, a, new_key, 1.0, 1.0)
+            put(3, 0, new_key, b, w, 1.0)
+        while k < K:
+            u = rng.random()
+            if u < 0.25 and live.size:
+                put(6, int(rng.choice(live)), 2, rng.normal())           # weight
+            elif u < 0.4 and hid.size:
+                put(5, int(rng.choice(hid)), 1, rng.normal(0, 0.5))      # bias
+            elif u < 0.55 and live.size:
+                put(4, int(rng.choice(live)))                            # remove a connection
+            elif u < 0.7 and keys.size >= 2 and hid.size:
+                a = rng.choice(keys)
+                b = nodes[g, int(rng.choice(hid)), 0]                    # not an input
+                put(3, 0, a, b, rng.normal(), 1.0)                       # add a connection
+            elif u < 0.8 and live.size:
+                put(6, int(rng.choice(live)), 3, 0.0)                    # disable
+            elif u < 0.9:
+                put(5, int(rng.integers(0, N)), 0, 1.0)                  # key column: fails
+            else:
+                put(2, float(N + rng.integers(0, 4)))                    # row out of range: fails
+    return ops
