@@ -20,6 +20,9 @@ Parity status of each function (what pins it, in tests/test_oracle_*.py):
                 closed forms (one weight / one extra gene apart), symmetry,
                 zero self-distance, row-permutation invariance, NaN for
                 malformed genomes.
+  substrate  -- the identity-activation case against numpy matmul, a single
+                connection closed form, the threshold pipeline with a
+                closed-form CPPN, the fp32 bound against float32 matmuls.
   apply_ops  -- hand-written expected tensors of operation sequences (first
                 NaN row, reuse of a freed lower row, full tensors, ranges),
                 no-op invariance, transform of the result.
@@ -73,6 +76,7 @@ def _load():
                                                  P, P, P]
             lib.or_distance.argtypes = [i32, i32, i32, i32, i32, P, P, dbl, dbl, P]
             lib.or_apply_ops.argtypes = [i32, i32, i32, P, P, P, i32, P]
+            lib.or_substrate.argtypes = [i32, i32, P, P, i64, i32, i32, P, P]
             lib.or_hyperneat.argtypes = [i32, i32, i32, P, P, i32, dbl, P, i64, P, P, P]
             for f in (lib.or_transform, lib.or_forward, lib.or_backward, lib.or_hyperneat):
                 f.restype = ctypes.c_int
@@ -184,6 +188,20 @@ def apply_ops(nodes, conns, ops):
                               _ptr(st))
     assert rc == 0, rc
     return nodes, conns, st
+
+
+def substrate(weights, inputs, act, with_bound=False):
+    """Sandwich substrate (reading R14): weights [P, K, K] (input cell, output
+    cell), inputs [P or 1, S, K] -> outputs [P, S, K] f64 (and the fp32 bound)."""
+    w = _f64(weights)
+    P, K = w.shape[0], w.shape[1]
+    assert w.shape == (P, K, K)
+    x, stride, S = _inputs(inputs, P, K)
+    out = np.empty((P, S, K), np.float64)
+    bnd = np.empty((P, S, K), np.float64) if with_bound else None
+    rc = _load().or_substrate(P, K, _ptr(w), _ptr(x), stride, S, int(act), _ptr(out), _ptr(bnd))
+    assert rc == 0, rc
+    return (out, bnd) if with_bound else out
 
 
 def backward(nodes, conns, inputs, I, O, grad_out, want_inputs=True):

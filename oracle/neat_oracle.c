@@ -44,6 +44,12 @@
  *   R9 HyperNEAT query: cell c = j*G + i has coordinates
  *      (-1 + 2i/(G-1), -1 + 2j/(G-1)); query (s, d) feeds
  *      (x_s, y_s, x_d, y_d, 1); the stored weight is o if |o| > thresh else 0.
+ *   R14 HyperNEAT substrate (the paper names HyperNEAT, Sec. 2 and Sec. 4,
+ *      without a substrate): the two-sheet ("sandwich") substrate of the
+ *      query's grid, an input sheet and an output sheet of G^2 cells each;
+ *      the query's weight w[s][t] connects input cell s to output cell t;
+ *      for an input pattern x, y_t = act(sum_s w[s][t] x_s) (no bias), with
+ *      the substrate activation act a parameter.
  *   R13 tensorized operations (Sec. 3.2): a list of K operations per genome,
  *      applied in order.  Each is 8 floats (kind, row, v0..v5):
  *        1 add node:  nodes[r] = (v0..v4) at r = the first row whose key is NaN
@@ -574,6 +580,42 @@ int or_forward_recurrent(int P, int N, int C, int I, int O, const double *nodes,
   free(v);
   free(x);
   g_free(&g);
+  return 0;
+}
+
+/* HyperNEAT substrate (R14): weights [P, K, K] (input cell, output cell),
+ * inputs x at inputs[p * in_pop_stride + s * K + c], outputs [P, S, K];
+ * bound (nullable) [P, S, K] first-order fp32 error bound of an evaluation
+ * with fp32 products and any summation order (inputs and weights exact). */
+int or_substrate(int P, int K, const double *w, const double *inputs, int64_t in_pop_stride,
+                 int S, int act, double *out, double *bound) {
+  if (P < 0 || K < 1 || S < 0 || act < 0 || act >= N_ACTS) return -1;
+  for (int p = 0; p < P; ++p) {
+    const double *wp = w + (size_t)p * K * K;
+    for (int s = 0; s < S; ++s) {
+      const double *x = inputs + (size_t)p * (size_t)in_pop_stride + (size_t)s * K;
+      double *y = out + ((size_t)p * S + s) * K;
+      for (int t = 0; t < K; ++t) {
+        double acc = 0.0, sabs = 0.0;
+        for (int c = 0; c < K; ++c) {
+          const double term = wp[(size_t)c * K + t] * x[c];
+          acc += term;
+          sabs += fabs(term);
+        }
+        y[t] = act_f(act, acc);
+        if (bound) {
+          const double eb = (K * U32 / (1.0 - K * U32)) * sabs + U32 * sabs;
+          double ef = 0.0;
+          switch (act) {
+            case A_SIGMOID: case A_TANH: case A_SIN: ef = 8.0 * U32 * fabs(y[t]); break;
+            case A_GAUSS: ef = (8.0 + acc * acc) * 2.0 * U32 * fabs(y[t]); break;
+            default: ef = 0.0;
+          }
+          bound[((size_t)p * S + s) * K + t] = act_lip(act, acc, eb) * eb + ef + 1e-300;
+        }
+      }
+    }
+  }
   return 0;
 }
 
