@@ -115,7 +115,7 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default="locomotion",
                     choices=["locomotion", "uneven", "differentiation", "hyperneat", "tiny",
-                             "recurrent", "distance", "mutate"])
+                             "recurrent", "distance", "mutate", "substrate"])
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -233,7 +233,8 @@ def enabled_counts(nodes, conns):
 def workload(name, seed, pop=None):
     from workloads import CONFIGS, make_population
     # the distance workload is the locomotion population, all pairs
-    cfg = dict(CONFIGS["locomotion" if name in ("distance", "mutate") else name])
+    base = {"distance": "locomotion", "mutate": "locomotion", "substrate": "hyperneat"}
+    cfg = dict(CONFIGS[base.get(name, name)])
     if pop is not None:
         cfg["P"] = pop
     spec = cfg["spec"]
@@ -254,6 +255,9 @@ def describe(name, cfg, spec):
                 f"{mode}")
     if name == "hyperneat":
         return f"HyperNEAT query: pop={cfg['P']} CPPNs, 32x32 substrate (2^20 queries each)"
+    if name == "substrate":
+        return (f"HyperNEAT query + two-sheet substrate: pop={cfg['P']} CPPNs, 32x32 grid "
+                f"(2^20 weights each), S=64 input patterns per substrate, tanh")
     if name == "mutate":
         return (f"one generation's structural edits: pop={cfg['P']} locomotion genomes, "
                 f"16 Sec. 3.2 operations each, then the transform (population restored "
@@ -299,6 +303,16 @@ def cpu_baseline(name, cfg, spec, nodes, conns, seed, budget_steps=None):
         oracle.backward(nodes[:k], conns[:k], x, spec.I, spec.O, go[..., None], want_inputs=True)
         units = float(E[:k].sum()) * cfg["S"]
         sample = f"{k} of {cfg['P']} genomes, forward + backward at S={cfg['S']}"
+    elif name == "substrate":
+        k = budget_steps or 1
+        G, S = 32, 64
+        q = np.arange(G ** 4)
+        t0 = time.perf_counter()
+        w = oracle.hyperneat(nodes[:k], conns[:k], grid=G, qidx=q).reshape(k, G * G, G * G)
+        x = np.random.default_rng(seed).standard_normal((k, S, G * G)).astype(np.float32)
+        oracle.substrate(w, x, 2)
+        units = float(E[:k].sum()) * G ** 4 + float(k) * S * G ** 4
+        sample = f"{k} of {cfg['P']} CPPNs: full query + substrate at S={S}"
     elif name == "mutate":
         from workloads import random_ops
         k = budget_steps or 2000
@@ -428,6 +442,35 @@ def bench_ours(args, rank, world, local, pg):
         fwd_hbm = float((8 * E + 12 * Vn).sum() + 4 * S * spec.I + 4 * S * spec.O * P +
                         (0 if rec else 4 * S * Vn.sum()))
         fwd_chip = float(4 * S * (E + Vn).sum())
+    elif name == "substrate":
+        G, S = 32, 64
+        K = G * G
+        d_nodes = torch.from_numpy(nodes).to(dev)
+        d_conns = torch.from_numpy(conns).to(dev)
+        tr = plan.transform(d_nodes, d_conns)
+        x = np.random.default_rng(args.seed + rank).standard_normal((P, S, K)).astype(np.float32)
+        d_x = torch.from_numpy(x).to(dev)
+        wts = torch.empty((P, K, K), device=dev)
+        sub_out = torch.empty((P, S, K), device=dev)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))]
+        ev_s = (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+        from paper_2504_08339_b300.api import substrate_forward
+
+        def run():
+            plan.transform(d_nodes, d_conns, out=tr)
+            ev[0][0].record()
+            plan.hyperneat(G, cfg["thresh"], out=wts)
+            ev[0][1].record()
+            ev_s[0].record()
+            substrate_forward(wts, d_x, act=2, out=sub_out)
+            ev_s[1].record()
+
+        units_per_step = float(E.sum()) * 2 ** 20 + float(P) * S * K * K
+        launches_per_step += 2
+        fwd_launches = 1
+        ro = None
+        alg_bytes = float((8 * E + 12 * Vn).sum() + 4.0 * 2 ** 20 * P)
+        chip_bytes = float(4.0 * 2 ** 20 * (E + Vn).sum())
     elif name == "mutate":
         from workloads import random_ops
         K = 16
@@ -566,6 +609,19 @@ def bench_ours(args, rank, world, local, pg):
             kernel = "k_distance"
         elif name == "mutate":
             kernel = "k_apply_ops + transform pipeline"
+        elif name == "substrate":
+            kernel = "k_hyperneat"
+            sub_us = 1e3 * ev_s[0].elapsed_time(ev_s[1])
+            flops = 2.0 * P * 64 * 1024 * 1024
+            sm_mhz = float((clk or {}).get("sm_mhz") or 2032.0)
+            sms = torch.cuda.get_device_properties(dev).multi_processor_count
+            peak = sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+            ach = flops / (sub_us * 1e-6) / 1e12
+            extra["substrate"] = {
+                "kernel": "k_substrate (fp32 SIMT, tanh fused)", "launch_us": round(sub_us, 3),
+                "bound": "alu", "achieved": round(ach, 2), "unit": "TFLOP/s",
+                "peak": round(peak, 2), "frac": round(ach / peak, 4),
+                "peak_source": f"derived: {sms} SMs x 128 fp32 lanes x 2 flop x {sm_mhz:.0f} MHz"}
         elif name == "differentiation":
             kernel = "k_backward<recompute>" if cfg.get("recompute") else "k_backward"
             fwd_us = 1e3 * ev_f[0].elapsed_time(ev_f[1])
@@ -718,7 +774,7 @@ def bench_reference(args, rank, world):
     name = args.config
     cfg, spec, nodes, conns = workload(name, args.seed, args.pop)
     budget = {"locomotion": 8, "uneven": 150, "differentiation": 4, "hyperneat": 1, "tiny": None,
-              "recurrent": 40, "distance": 200, "mutate": 2000}[name]
+              "recurrent": 40, "distance": 200, "mutate": 2000, "substrate": 1}[name]
     for _ in range(max(3, args.warmup)):
         cpu_baseline(name, cfg, spec, nodes, conns, args.seed, budget)
     vals, secs = [], 0.0

@@ -243,6 +243,27 @@ neat_status neat_forward_noalloc(const float *nodes, const float *conns, int P, 
                                  int I, int O, const float *inputs, int64_t in_pop_stride, int S,
                                  float *outputs, uint32_t *gstatus, cudaStream_t stream);
 
+/* HyperNEAT substrate evaluation (the paper names HyperNEAT but describes no
+ * substrate; this is the two-sheet substrate of the query grid): an input
+ * sheet and an output sheet of K = G^2 cells; weights[g][s][t] (the query's
+ * layout: source cell s, target cell t) connects input cell s to output cell
+ * t; for every input pattern, y_t = act(sum_s w[s][t] x_s), no bias.
+ *   weights [P, K, K] f32; inputs: pattern p of genome g, cell c at
+ *           inputs[g * in_pop_stride + p * K + c] (stride 0: one pattern set
+ *           shared by every genome, otherwise >= S * K)
+ *   act     activation id (NEAT_ACT_*); outputs [P, S, K] f32 out
+ * Sums run over s in ascending order in fp32 (deterministic).  Plan-free. */
+neat_status neat_substrate_forward(const float *weights, int P, int K, const float *inputs,
+                                   int64_t in_pop_stride, int S, int act, float *outputs,
+                                   cudaStream_t stream);
+
+/* neat_hyperneat_query into `weights` [P, grid^2, grid^2] followed by
+ * neat_substrate_forward of those weights on the same stream: every CPPN's
+ * substrate network evaluated on S input patterns without a host round trip. */
+neat_status neat_hyperneat_substrate(neat_plan *plan, int grid, float thresh, const float *inputs,
+                                     int64_t in_pop_stride, int S, int act, float *weights,
+                                     float *outputs, cudaStream_t stream);
+
 /* Tensorized operations of Sec. 3.2 on the population tensors, in place (no
  * counterpart needs a host round trip: the list is data).  ops [P, K, 8] f32:
  * operation k of genome g is (kind, row, v0..v5), applied in order k = 0..K-1:

@@ -26,7 +26,8 @@ SYMBOLS = ("neat_version", "neat_status_string", "neat_last_cuda_error",
            "neat_forward", "neat_forward_plain", "neat_backward", "neat_hyperneat_query",
            "neat_forward_noalloc", "neat_probe_smem_read", "neat_transform_recurrent",
            "neat_forward_recurrent", "neat_distance_scratch_bytes", "neat_distance",
-           "neat_apply_ops", "neat_mutate_transform")
+           "neat_apply_ops", "neat_mutate_transform", "neat_substrate_forward",
+           "neat_hyperneat_substrate")
 
 
 class NeatError(RuntimeError):
@@ -76,6 +77,8 @@ def load(path: str = LIB_PATH):
             "neat_forward_recurrent": (i32, [vp, vp, i64, i32, i32, vp, vp]),
             "neat_distance_scratch_bytes": (sz, [i32, i32, i32]),
             "neat_apply_ops": (i32, [vp, vp, i32, i32, i32, vp, i32, vp, vp]),
+            "neat_substrate_forward": (i32, [vp, i32, i32, vp, i64, i32, i32, vp, vp]),
+            "neat_hyperneat_substrate": (i32, [vp, i32, f32, vp, i64, i32, i32, vp, vp, vp]),
             "neat_mutate_transform": (i32, [vp, vp, vp, vp, i32, vp, vp, vp, vp, vp, vp]),
             "neat_distance": (i32, [vp, vp, vp, i32, i32, i32, i32, i32, f32, f32, vp, vp, sz, vp]),
         }

@@ -102,6 +102,28 @@ class Plan:
                    "neat_transform")
         return out
 
+    def hyperneat_substrate(self, inputs, grid=32, thresh=0.2, act=2, weights=None, out=None,
+                            stream=None):
+        """Query every CPPN on the grid, then evaluate its two-sheet substrate
+        on inputs [P or 1, S, grid^2]: (outputs [P, S, grid^2], weights)."""
+        K = grid * grid
+        _need(inputs, "inputs", torch.float32)
+        if inputs.dim() != 3 or inputs.shape[2] != K:
+            raise _lib.NeatError(f"inputs must be [P or 1, S, {K}]")
+        S = inputs.shape[1]
+        stride = 0 if inputs.shape[0] == 1 and self.P != 1 else S * K
+        dev = inputs.device
+        if weights is None:
+            weights = torch.empty((self.P, K, K), dtype=torch.float32, device=dev)
+        if out is None:
+            out = torch.empty((self.P, S, K), dtype=torch.float32, device=dev)
+        _need(weights, "weights", torch.float32, (self.P, K, K))
+        _need(out, "out", torch.float32, (self.P, S, K))
+        _lib.check(self._lib.neat_hyperneat_substrate(
+            self._h, int(grid), float(thresh), _ptr(inputs), stride, S, int(act),
+            _ptr(weights), _ptr(out), _stream(stream)), "neat_hyperneat_substrate")
+        return out, weights
+
     def mutate_transform(self, nodes, conns, ops, op_status=None, out: Transformed | None = None,
                          stream=None):
         """Apply the Sec. 3.2 operation list ops [P, K, 8] to nodes / conns in
@@ -208,6 +230,22 @@ class Plan:
         _lib.check(self._lib.neat_hyperneat_query(self._h, int(grid), float(thresh), _ptr(out),
                                                   _stream(stream)), "neat_hyperneat_query")
         return out
+
+
+def substrate_forward(weights, inputs, act=2, out=None, stream=None):
+    """Two-sheet substrate outputs [P, S, K] = act(inputs @ weights) per genome
+    (weights [P, K, K], inputs [P or 1, S, K])."""
+    lib = _lib.load()
+    _need(weights, "weights", torch.float32)
+    _need(inputs, "inputs", torch.float32)
+    P, K = weights.shape[0], weights.shape[1]
+    S = inputs.shape[1]
+    stride = 0 if inputs.shape[0] == 1 and P != 1 else S * K
+    if out is None:
+        out = torch.empty((P, S, K), dtype=torch.float32, device=weights.device)
+    _lib.check(lib.neat_substrate_forward(_ptr(weights), P, K, _ptr(inputs), stride, S, int(act),
+                                          _ptr(out), _stream(stream)), "neat_substrate_forward")
+    return out
 
 
 def apply_ops(nodes, conns, ops, op_status=None, stream=None):

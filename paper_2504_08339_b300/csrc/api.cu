@@ -304,6 +304,15 @@ neat_status neat_hyperneat_query(neat_plan *plan, int grid, float thresh, float 
                                             plan->sm_count * occ, stream));
 }
 
+neat_status neat_hyperneat_substrate(neat_plan *plan, int grid, float thresh, const float *inputs,
+                                     int64_t in_pop_stride, int S, int act, float *weights,
+                                     float *outputs, cudaStream_t stream) {
+  neat_status s = neat_hyperneat_query(plan, grid, thresh, weights, stream);
+  if (s != NEAT_OK) return s;
+  return neat_substrate_forward(weights, plan->P, grid * grid, inputs, in_pop_stride, S, act,
+                                outputs, stream);
+}
+
 neat_status neat_mutate_transform(neat_plan *plan, float *nodes, float *conns, const float *ops,
                                   int K, uint32_t *op_status, int32_t *order, int32_t *layer,
                                   int32_t *n_layers, uint32_t *gstatus, cudaStream_t stream) {

@@ -324,6 +324,9 @@ cudaError_t launch_forward_plain(const Ws &w, const float *inputs, int64_t strid
 cudaError_t launch_forward_recurrent(const Ws &w, const float *inputs, int64_t stride, int S,
                                      int T, float *outputs, int warps, int grid, cudaStream_t st);
 int forward_rec_occupancy(int warps);
+// HyperNEAT two-sheet substrate: y = act(x W) per genome
+cudaError_t launch_substrate(const float *w, int P, int K, const float *x, int64_t stride, int S,
+                             int act, float *y, cudaStream_t st);
 // tensorized operations (Sec. 3.2) in place, one warp per genome
 cudaError_t launch_apply_ops(float *nodes, float *conns, int P, int N, int C, const float *ops,
                              int K, uint32_t *op_status, cudaStream_t st);
