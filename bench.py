@@ -230,6 +230,37 @@ def enabled_counts(nodes, conns):
     return en.sum(axis=1).astype(np.int64), (~np.isnan(nodes[..., 0])).sum(axis=1).astype(np.int64)
 
 
+def live_counts(nodes, conns, I, O):
+    """Per genome, the enabled connections into and the non-input nodes of the
+    part of the network the outputs depend on (reverse reachability from the
+    output rows).  The HyperNEAT query evaluates only that part, so its
+    algorithmic traffic counts only that part."""
+    P = nodes.shape[0]
+    E_live = np.zeros(P, np.int64)
+    V_live = np.zeros(P, np.int64)
+    for g in range(P):
+        keys = nodes[g, :, 0]
+        row_of = {float(k): i for i, k in enumerate(keys) if not np.isnan(k)}
+        c = conns[g]
+        en = ~np.isnan(c[:, 0]) & ~np.isnan(c[:, 1]) & ~np.isnan(c[:, 3]) & (c[:, 3] != 0)
+        preds = {}
+        for a, b in c[en, :2]:
+            ra, rb = row_of.get(float(a)), row_of.get(float(b))
+            if ra is not None and rb is not None:
+                preds.setdefault(rb, []).append(ra)
+        live = set(range(I, I + O))
+        stack = list(live)
+        while stack:
+            x = stack.pop()
+            for a in preds.get(x, ()):
+                if a not in live:
+                    live.add(a)
+                    stack.append(a)
+        V_live[g] = sum(1 for r in live if r >= I)
+        E_live[g] = sum(len(preds.get(r, ())) for r in live if r >= I)
+    return E_live, V_live
+
+
 def workload(name, seed, pop=None):
     from workloads import CONFIGS, make_population
     # the distance workload is the locomotion population, all pairs
@@ -469,8 +500,9 @@ def bench_ours(args, rank, world, local, pg):
         launches_per_step += 2
         fwd_launches = 1
         ro = None
+        E_live, V_live = live_counts(nodes, conns, spec.I, spec.O)
         alg_bytes = float((8 * E + 12 * Vn).sum() + 4.0 * 2 ** 20 * P)
-        chip_bytes = float(4.0 * 2 ** 20 * (E + Vn).sum())
+        chip_bytes = float(4.0 * 2 ** 20 * (E_live + V_live).sum())
     elif name == "mutate":
         from workloads import random_ops
         K = 16
@@ -564,8 +596,16 @@ def bench_ours(args, rank, world, local, pg):
         launches_per_step += 1
         fwd_launches = 1
         ro = None
+        # the query evaluates only the nodes the output depends on: program
+        # bytes once, a weight written per query; on chip a value read per
+        # live connection and written per live node, per query
+        E_live, V_live = live_counts(nodes, conns, spec.I, spec.O)
+        extra["live_subgraph"] = {
+            "conns_per_genome_mean": round(float(E_live.mean()), 2),
+            "nodes_per_genome_mean": round(float(V_live.mean()), 2),
+            "note": "nodes the output does not depend on are not evaluated (same weights)"}
         alg_bytes = float((8 * E + 12 * Vn).sum() + 4.0 * 2 ** 20 * P)
-        chip_bytes = float(4.0 * 2 ** 20 * (E + Vn).sum())
+        chip_bytes = float(4.0 * 2 ** 20 * (E_live + V_live).sum())
 
     # ---- timed region (device-resident inputs)
     for _ in range(max(3, args.warmup)):

@@ -117,8 +117,9 @@ neat_status neat_plan_create(neat_plan **out, int P, int N, int C, int I, int O,
 neat_status neat_plan_destroy(neat_plan *plan);
 
 /* Tuning knobs picked by the autotuner (0 = library default).
- *   warps_per_cta    warps of a sample-parallel CTA (1..16)
- *   samples_per_lane samples one lane evaluates in the sample-parallel forward (1, 2, 4)
+ *   warps_per_cta    warps of a sample-parallel or HyperNEAT-query CTA (1..16)
+ *   samples_per_lane samples one lane evaluates in the sample-parallel forward,
+ *                    queries one lane evaluates in the HyperNEAT query (1, 2, 4)
  *   lvl_threads      threads of a level-synchronous (small-sample) CTA: 32..256,
  *                    a multiple of 32
  *   small_s_max      largest S that uses the level-synchronous forward (1..64,

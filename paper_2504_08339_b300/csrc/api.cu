@@ -42,16 +42,6 @@ neat_status cuda_status(cudaError_t e) {
   return NEAT_ERR_CUDA;
 }
 
-// warps of a HyperNEAT query CTA: as many [N][32] shared-memory value arrays
-// as fit in ~96 KB, 1..8
-int hn_warps(const neat_plan *p) {
-  const size_t per = size_t(p->N) * 32 * sizeof(float);
-  int w = p->tune.warps_per_cta > 0 ? p->tune.warps_per_cta
-                                    : std::max(1, std::min(8, int((96 * 1024) / per)));
-  while (w > 1 && neat::forward_sp_smem(p->N, w, 1) > size_t(p->smem_optin)) --w;
-  return w;
-}
-
 // Launch shape of the sample-parallel forward for S samples per genome.
 // Every genome's values live in its warp's workspace slot (measured faster
 // than shared-memory value arrays on every workload: the L1 caches them and
@@ -296,12 +286,35 @@ neat_status neat_hyperneat_query(neat_plan *plan, int grid, float thresh, float 
   if (grid < 2 || grid > 128) return NEAT_ERR_ARG;
   if (plan->P == 0) return NEAT_OK;
   if (weights == nullptr || !aligned(weights, 4)) return NEAT_ERR_ARG;
-  const int warps = hn_warps(plan);
-  const size_t smem = neat::forward_sp_smem(plan->N, warps, 1);
-  if (smem > size_t(plan->smem_optin)) return NEAT_ERR_UNSUPPORTED;
-  const int occ = std::max(1, neat::hyperneat_occupancy(warps, smem));
-  return cuda_status(neat::launch_hyperneat(plan->w, grid, thresh, weights, warps,
-                                            plan->sm_count * occ, stream));
+  const int spl = plan->tune.samples_per_lane > 0 ? plan->tune.samples_per_lane : 2;
+  const int warps = plan->tune.warps_per_cta > 0 ? plan->tune.warps_per_cta : 8;
+  // shared memory per CTA: an SM's share for about 32 resident warps (the
+  // staged program plus as many value arrays as fit), less the static part
+  int per_sm = 0, reserved = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor,
+                                         plan->device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, plan->device);
+  if (e != cudaSuccess) return cuda_status(e);
+  const int want = std::max(1, 32 / warps);
+  const int prog = neat::hn_prog_bytes(plan->N, plan->C);
+  int smem = std::min(plan->smem_optin, per_sm / want - reserved) - 1024;
+  // a CTA holds at least the program and the staging scratch of a full-size
+  // genome (fewer CTAs per SM for large N, C)
+  if (smem < prog + neat::hn_stage_bytes(plan->N, plan->C)) smem = plan->smem_optin - 1024;
+  if (smem < prog) return NEAT_ERR_UNSUPPORTED;
+  const int occ = std::max(1, neat::hyperneat_occupancy(spl, warps, size_t(smem)));
+  int64_t ctas = int64_t(plan->sm_count) * occ;
+  const int64_t stage_need = std::max<int64_t>(neat::hn_stage_bytes(plan->N, plan->C),
+                                               int64_t(plan->N + neat::HN_ROW_FIRST) * 32 * spl * 4);
+  const bool all_fit = stage_need + prog <= smem;
+  if (!all_fit) {  // some genomes may use workspace slots: one per warp
+    ctas = std::min<int64_t>(ctas, neat::sp_scratch_slots(plan->w, spl) / warps);
+    if (ctas >= plan->sm_count) ctas -= ctas % plan->sm_count;
+  }
+  if (ctas < 1) return NEAT_ERR_UNSUPPORTED;
+  return cuda_status(neat::launch_hyperneat(plan->w, grid, thresh, weights, spl, warps,
+                                            int(ctas), smem, stream));
 }
 
 neat_status neat_hyperneat_substrate(neat_plan *plan, int grid, float thresh, const float *inputs,

@@ -14,9 +14,11 @@
 //  k_forward_plain  one CTA per (genome, tile) over the padded programs,
 //                   visiting all N padded positions (the plain form).
 //  k_hyperneat      the batched form with inputs generated in the kernel
-//                   (substrate coordinates) and a threshold epilogue.
+//                   (substrate coordinates), several queries per lane and a
+//                   threshold epilogue.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "neat_internal.cuh"
@@ -423,51 +425,461 @@ __global__ void __launch_bounds__(32) k_forward_plain(Ws w, const float *__restr
     for (int j = 0; j < O; ++j) orow[j] = smv[io[I + j] * 32 + lane];
 }
 
-// HyperNEAT substrate query: item = (genome in queue order, chunk of 32-query
-// tiles).  Query q = s * G^2 + t; cell c = j * G + i sits at
-// (-1 + 2i/(G-1), -1 + 2j/(G-1)); inputs (x_s, y_s, x_t, y_t, 1).
-__global__ void k_hyperneat(Ws w, int G, float thresh, float *__restrict__ weights,
-                            int chunks_per_genome, int tiles_per_chunk) {
-  extern __shared__ __align__(16) float smv[];
+// ---- HyperNEAT substrate query ---------------------------------------------
+// Query q = s * G^2 + t; cell c = j * G + i sits at (-1 + 2i/(G-1),
+// -1 + 2j/(G-1)); the CPPN inputs are (x_s, y_s, x_t, y_t, 1).  G <= 128 keeps
+// every query index in 32 bits.
+//
+// Item = (genome in queue order, chunk of tiles), claimed by a whole CTA; tile =
+// 32 * SPL consecutive queries, lane l of its warp evaluating queries
+// tile * 32 * SPL + k * 32 + l, k < SPL (every program record loaded serves
+// SPL queries per lane).  The CTA first stages the genome's program in shared
+// memory in a form made for this walk (HnNode below): input positions dropped,
+// each node's incoming edges in pairs with value offsets precomputed, so the
+// walk issues one 16-byte broadcast load per two edges, one vector load of the
+// lane's SPL values per edge and one FMA per edge and query.  Node values live
+// in shared memory too, [row][32][SPL] per warp.  A genome whose values do not
+// fit falls back to the sample-parallel walk over the packed program with
+// values in the warp's workspace slot.
+
+// Staged node (16 B): non-input nodes in program order.
+//   pairs = byte offset of the node's first edge pair in the pair array
+//           [0, 17) | pair count << 17
+//   meta  = byte offset of the node's value row [0, 20) | activation << 20 |
+//           aggregation << 23 | (in-degree odd) << 25
+// A pair (uint4) is (offset0, w0, offset1, w1), the offsets being byte offsets
+// of the source rows in a warp's value array; each node's list is padded to an
+// even length with an edge that leaves the aggregate unchanged: weight 0 on the
+// zero row (rows V and V + 1 hold 0 and 1) for sum and mean, weight 1 on the
+// one row for product, a repeat of the last edge for max.
+struct __align__(16) HnNode {
+  float bias, resp;
+  uint32_t pairs;
+  uint32_t meta;
+};
+constexpr uint32_t HN_PAIR_BITS = 17, HN_ROW_BITS = 20;
+static_assert(((NEAT_MAX_CONNS + NEAT_MAX_NODES) / 2 + 1) * 16 <= (1 << HN_PAIR_BITS),
+              "pair offsets overflow their field");
+static_assert((NEAT_MAX_NODES + 7) * 32 * 4 * 4 <= (1 << HN_ROW_BITS), "row offsets overflow their field");
+
+// exclusive block-wide prefix sums of (a, b) and their totals; s: 64 ints
+__device__ __forceinline__ void block_scan2(int a, int b, int &ea, int &eb, int &ta, int &tb,
+                                            int *s) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int ia = a, ib = b;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int x = __shfl_up_sync(0xffffffffu, ia, o), y = __shfl_up_sync(0xffffffffu, ib, o);
+    if (lane >= o) {
+      ia += x;
+      ib += y;
+    }
+  }
+  if (lane == 31) {
+    s[wid] = ia;
+    s[32 + wid] = ib;
+  }
+  __syncthreads();
+  int oa = 0, ob = 0;
+  ta = 0;
+  tb = 0;
+  for (int i = 0; i < nw; ++i) {
+    const int x = s[i], y = s[32 + i];
+    if (i < wid) {
+      oa += x;
+      ob += y;
+    }
+    ta += x;
+    tb += y;
+  }
+  ea = oa + ia - a;
+  eb = ob + ib - b;
+  __syncthreads();  // s is reused by the next call
+}
+
+// the SPL values of one lane in a staged value row (one vector load / store)
+template <int SPL>
+struct HnVec;
+template <>
+struct HnVec<1> {
+  __device__ __forceinline__ static void ld(const char *p, float (&x)[1]) {
+    x[0] = *reinterpret_cast<const float *>(p);
+  }
+  __device__ __forceinline__ static void st(char *p, const float (&x)[1]) {
+    *reinterpret_cast<float *>(p) = x[0];
+  }
+};
+template <>
+struct HnVec<2> {
+  __device__ __forceinline__ static void ld(const char *p, float (&x)[2]) {
+    const float2 v = *reinterpret_cast<const float2 *>(p);
+    x[0] = v.x;
+    x[1] = v.y;
+  }
+  __device__ __forceinline__ static void st(char *p, const float (&x)[2]) {
+    *reinterpret_cast<float2 *>(p) = make_float2(x[0], x[1]);
+  }
+};
+template <>
+struct HnVec<4> {
+  __device__ __forceinline__ static void ld(const char *p, float (&x)[4]) {
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    x[0] = v.x;
+    x[1] = v.y;
+    x[2] = v.z;
+    x[3] = v.w;
+  }
+  __device__ __forceinline__ static void st(char *p, const float (&x)[4]) {
+    *reinterpret_cast<float4 *>(p) = make_float4(x[0], x[1], x[2], x[3]);
+  }
+};
+
+// Walk of a staged program for this lane's SPL queries; vb = the warp's value
+// array + lane * SPL floats (bytes), row stride 32 * SPL floats.
+// a[j] = fma(w, x[j], a[j]) for the SPL queries, two per instruction (the
+// paired fp32 FMA; each component rounds as fmaf)
+template <int SPL>
+__device__ __forceinline__ void hn_fma(float w, const float (&x)[SPL], float (&a)[SPL]) {
+  if constexpr (SPL == 1) {
+    a[0] = fmaf(w, x[0], a[0]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < SPL; j += 2) {
+      const float2 r = __ffma2_rn(make_float2(w, w), make_float2(x[j], x[j + 1]),
+                                  make_float2(a[j], a[j + 1]));
+      a[j] = r.x;
+      a[j + 1] = r.y;
+    }
+  }
+}
+
+template <int SPL>
+__device__ __forceinline__ void hn_walk(const HnNode *__restrict__ nodes, int nn,
+                                        const uint4 *__restrict__ pairs, char *vb) {
+  const char *pbase = reinterpret_cast<const char *>(pairs);
+  for (int c = 0; c < nn; ++c) {
+    const HnNode n = nodes[c];
+    const int np = int(n.pairs >> HN_PAIR_BITS);
+    const uint4 *pp =
+        reinterpret_cast<const uint4 *>(pbase + (n.pairs & ((1u << HN_PAIR_BITS) - 1u)));
+    const int agg = int(n.meta >> (HN_ROW_BITS + 3)) & 3;
+    float a[SPL];
+    if (agg == NEAT_AGG_SUM || agg == NEAT_AGG_MEAN) {
+      // even edges into a0, odd edges into a1 (the rounding order of the
+      // sample-parallel walk)
+      float a0[SPL], a1[SPL];
+#pragma unroll
+      for (int j = 0; j < SPL; ++j) a0[j] = a1[j] = 0.0f;
+#pragma unroll 2
+      for (int k = 0; k < np; ++k) {
+        const uint4 e = pp[k];
+        float x0[SPL], x1[SPL];
+        HnVec<SPL>::ld(vb + e.x, x0);
+        HnVec<SPL>::ld(vb + e.z, x1);
+        hn_fma<SPL>(__uint_as_float(e.y), x0, a0);
+        hn_fma<SPL>(__uint_as_float(e.w), x1, a1);
+      }
+#pragma unroll
+      for (int j = 0; j < SPL; ++j) a[j] = a0[j] + a1[j];
+      if (agg == NEAT_AGG_MEAN && np > 0) {
+        const float cnt = float(2 * np - int((n.meta >> (HN_ROW_BITS + 5)) & 1u));
+#pragma unroll
+        for (int j = 0; j < SPL; ++j) a[j] = a[j] / cnt;
+      }
+    } else if (np == 0) {
+#pragma unroll
+      for (int j = 0; j < SPL; ++j) a[j] = 0.0f;
+    } else if (agg == NEAT_AGG_MAX) {
+      const uint4 e = pp[0];
+      float x0[SPL], x1[SPL];
+      HnVec<SPL>::ld(vb + e.x, x0);
+      HnVec<SPL>::ld(vb + e.z, x1);
+#pragma unroll
+      for (int j = 0; j < SPL; ++j)
+        a[j] = fmaxf(__uint_as_float(e.y) * x0[j], __uint_as_float(e.w) * x1[j]);
+      for (int k = 1; k < np; ++k) {
+        const uint4 f = pp[k];
+        HnVec<SPL>::ld(vb + f.x, x0);
+        HnVec<SPL>::ld(vb + f.z, x1);
+#pragma unroll
+        for (int j = 0; j < SPL; ++j) {
+          a[j] = fmaxf(a[j], __uint_as_float(f.y) * x0[j]);
+          a[j] = fmaxf(a[j], __uint_as_float(f.w) * x1[j]);
+        }
+      }
+    } else {  // product
+#pragma unroll
+      for (int j = 0; j < SPL; ++j) a[j] = 1.0f;
+      for (int k = 0; k < np; ++k) {
+        const uint4 f = pp[k];
+        float x0[SPL], x1[SPL];
+        HnVec<SPL>::ld(vb + f.x, x0);
+        HnVec<SPL>::ld(vb + f.z, x1);
+#pragma unroll
+        for (int j = 0; j < SPL; ++j) {
+          a[j] = a[j] * (__uint_as_float(f.y) * x0[j]);
+          a[j] = a[j] * (__uint_as_float(f.w) * x1[j]);
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < SPL; ++j) a[j] = fmaf(n.resp, a[j], n.bias);
+    act_apply_n<SPL>(int(n.meta >> HN_ROW_BITS) & 7, a);
+    HnVec<SPL>::st(vb + (n.meta & ((1u << HN_ROW_BITS) - 1u)), a);
+  }
+}
+
+// Stage genome g's program for the query walk (every thread of the CTA calls
+// it; tmp = hn_stage_bytes(V, E) bytes of scratch, 16-byte aligned).
+//  1. copy its node and edge records into tmp;
+//  2. keep only the nodes the output depends on (one warp, reverse program
+//     order: a node is needed when a needed node reads it) - the others
+//     cannot change the output;
+//  3. give each kept node a value row by a linear scan in program order: a
+//     row is released at the last node that reads it (before that node's own
+//     row is taken; a node reads all its inputs before it writes), inputs keep
+//     rows 0-4, the output keeps its row to the end;
+//  4. write the node records and edge pairs (HnNode) with those rows.
+// info[0..2] = staged nodes, rows used, the output's row.
+template <int SPL>
+__device__ void hn_stage(const Ws &w, const GenomeHdr &h, const int32_t *io, HnNode *nodes,
+                         uint4 *pairs, int *s_scan, char *tmp, int *info) {
+  constexpr uint32_t ROWB = 32 * SPL * 4;  // bytes per value row
+  const int V = h.V, E = h.E;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  NodeRec *tn = reinterpret_cast<NodeRec *>(tmp);
+  int *need = reinterpret_cast<int *>(tmp + size_t(V) * 16);
+  int *last = need + V;
+  int *row = last + V;
+  int *fstack = row + V;
+  EdgeRec *te = reinterpret_cast<EdgeRec *>(fstack + V);
+  const NodeRec *nr = w.knode + h.node_off;
+  const EdgeRec *er = w.kedge + h.edge_off;
+  const int po = io[5];
+  for (int i = threadIdx.x; i < V; i += blockDim.x) {
+    tn[i] = ld_node(nr + i);
+    need[i] = i == po;
+    last[i] = -1;
+    row[i] = -1;
+  }
+  for (int i = threadIdx.x; i < E; i += blockDim.x) te[i] = ld_edge(er + i);
+  __syncthreads();
+  if (wid == 0) {
+    for (int p = V - 1; p >= 0; --p) {
+      const NodeRec n = tn[p];
+      if (need[p] && !(n.meta & META_INPUT))
+        for (int k = lane; k < meta_cnt(n.meta); k += 32) need[te[n.in_begin + k].src] = 1;
+      __syncwarp();
+    }
+    if (lane == 0) {
+      for (int i = 0; i < 5; ++i) row[io[i]] = i;
+      int c = 0;
+      for (int p = 0; p < V; ++p) {  // last reader of every value
+        const NodeRec n = tn[p];
+        if (!need[p] || (n.meta & META_INPUT)) continue;
+        for (int k = 0; k < meta_cnt(n.meta); ++k) last[te[n.in_begin + k].src] = c;
+        ++c;
+      }
+      int sp = 0, next = HN_ROW_FIRST;
+      c = 0;
+      for (int p = 0; p < V; ++p) {
+        const NodeRec n = tn[p];
+        if (!need[p] || (n.meta & META_INPUT)) continue;
+        for (int k = 0; k < meta_cnt(n.meta); ++k) {
+          const int src = te[n.in_begin + k].src;
+          if (last[src] == c && src != po && !(tn[src].meta & META_INPUT)) {
+            fstack[sp++] = row[src];
+            last[src] = -2;  // released once, whatever the duplicates
+          }
+        }
+        row[p] = sp > 0 ? fstack[--sp] : next++;
+        ++c;
+      }
+      info[0] = c;
+      info[1] = next;
+      info[2] = row[po];
+    }
+  }
+  __syncthreads();
+  int carry_n = 0, carry_p = 0;
+  for (int base = 0; base < V; base += blockDim.x) {
+    const int p = base + int(threadIdx.x);
+    NodeRec n{};
+    int keep = 0, np = 0;
+    if (p < V) {
+      n = tn[p];
+      keep = (need[p] && !(n.meta & META_INPUT)) ? 1 : 0;
+      np = keep ? (meta_cnt(n.meta) + 1) >> 1 : 0;
+    }
+    int en, ep, tk, tp;
+    block_scan2(keep, np, en, ep, tk, tp, s_scan);
+    if (keep) {
+      const int c = carry_n + en, pb = carry_p + ep;
+      const int cnt = meta_cnt(n.meta), agg = meta_agg(n.meta);
+      HnNode r;
+      r.bias = n.bias;
+      r.resp = n.resp;
+      r.pairs = uint32_t(pb) * 16u | (uint32_t(np) << HN_PAIR_BITS);
+      r.meta = uint32_t(row[p]) * ROWB | (uint32_t(meta_act(n.meta)) << HN_ROW_BITS) |
+               (uint32_t(agg) << (HN_ROW_BITS + 3)) | (uint32_t(cnt & 1) << (HN_ROW_BITS + 5));
+      nodes[c] = r;
+      const EdgeRec *e = te + n.in_begin;
+      for (int k = 0; k < np; ++k) {
+        const EdgeRec e0 = e[2 * k];
+        uint4 q;
+        q.x = uint32_t(row[e0.src]) * ROWB;
+        q.y = __float_as_uint(e0.w);
+        if (2 * k + 1 < cnt) {
+          const EdgeRec e1 = e[2 * k + 1];
+          q.z = uint32_t(row[e1.src]) * ROWB;
+          q.w = __float_as_uint(e1.w);
+        } else if (agg == NEAT_AGG_MAX) {
+          q.z = q.x;
+          q.w = q.y;
+        } else if (agg == NEAT_AGG_PRODUCT) {
+          q.z = HN_ROW_ONE * ROWB;
+          q.w = __float_as_uint(1.0f);
+        } else {
+          q.z = HN_ROW_ZERO * ROWB;
+          q.w = 0u;
+        }
+        pairs[pb + k] = q;
+      }
+    }
+    carry_n += tk;
+    carry_p += tp;
+  }
+}
+
+// Query geometry and output of one item
+struct HnTile {
+  int G, G2, G4;
+  float step, inv_g, thresh;
+  int px, py, pX, pY, pb, po;  // positions of the five inputs and the output
+  float *wg;                   // the genome's weights
+};
+
+// Tiles tile0, tile0 + stride, ... < tile1 of one warp: coordinates into the
+// input rows of the warp's value array v, walk(), thresholded outputs.  Value
+// (row, query k of this lane) sits at v[(row * 32 + lane) * SPL + k] when
+// LANE_MAJOR (the staged walk: one vector access per row), else at
+// v[(row * SPL + k) * 32 + lane] (the sample-parallel walk).
+template <int SPL, bool LANE_MAJOR, class Walk>
+__device__ __forceinline__ void hn_tiles(const HnTile &t, float *v, int tile0, int tile1,
+                                         int stride, Walk walk) {
+  constexpr int RS = 32 * SPL;
+  const int lane = threadIdx.x & 31;
+  auto at = [&](int row, int k) -> float & {
+    return LANE_MAJOR ? v[(row * 32 + lane) * SPL + k] : v[(row * SPL + k) * 32 + lane];
+  };
+#pragma unroll
+  for (int k = 0; k < SPL; ++k) at(t.pb, k) = 1.0f;
+  for (int tile = tile0; tile < tile1; tile += stride) {
+    const int q0 = tile * RS;
+    const int sc0 = q0 / t.G2, tc0 = q0 - sc0 * t.G2 + lane;
+#pragma unroll
+    for (int k = 0; k < SPL; ++k) {
+      int sc = sc0, tc = tc0 + k * 32;
+      if (tc >= t.G2) {
+        const int d = tc / t.G2;
+        sc += d;
+        tc -= d * t.G2;
+      }
+      const int sj = int((float(sc) + 0.5f) * t.inv_g), si = sc - sj * t.G;
+      const int tj = int((float(tc) + 0.5f) * t.inv_g), ti = tc - tj * t.G;
+      at(t.px, k) = -1.0f + t.step * float(si);
+      at(t.py, k) = -1.0f + t.step * float(sj);
+      at(t.pX, k) = -1.0f + t.step * float(ti);
+      at(t.pY, k) = -1.0f + t.step * float(tj);
+    }
+    walk();
+#pragma unroll
+    for (int k = 0; k < SPL; ++k) {
+      const int qi = q0 + k * 32 + lane;
+      const float o = at(t.po, k);
+      if (qi < t.G4) t.wg[qi] = fabsf(o) > t.thresh ? o : 0.0f;
+    }
+  }
+}
+
+template <int SPL>
+__global__ void __launch_bounds__(512) k_hyperneat(Ws w, int G, float thresh,
+                                                   float *__restrict__ weights,
+                                                   int chunks_per_genome, int tiles_per_chunk,
+                                                   int smem_bytes) {
+  constexpr int RS = 32 * SPL;
+  extern __shared__ __align__(16) unsigned char hsm[];
+  __shared__ int s_item, s_info[3];
+  __shared__ int s_scan[64];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int N = w.N;
-  float *v = smv + size_t(wid) * N * 32;
-  const int64_t G2 = int64_t(G) * G, G4 = G2 * G2;
+  const int prog_bytes = hn_prog_bytes(N, w.C);
+  HnNode *s_nodes = reinterpret_cast<HnNode *>(hsm);
+  uint4 *s_pairs = reinterpret_cast<uint4 *>(hsm + size_t(N) * sizeof(HnNode));
+  float *s_vals = reinterpret_cast<float *>(hsm + prog_bytes);
+  // workspace slots of every warp of this CTA (the fallback walk), or none
+  const bool slots_ok = w.sp_scratch != nullptr &&
+                        size_t(blockIdx.x + 1) * nw * N * RS <= w.sp_scratch_floats;
+  float *vg = slots_ok ? w.sp_scratch + (size_t(blockIdx.x) * nw + wid) * N * RS : nullptr;
+  const int G2 = G * G, G4 = G2 * G2;
+  const int tiles = (G4 + RS - 1) / RS;
   const int total = w.P * chunks_per_genome;
   const float step = 2.0f / float(G - 1);
+  // cell c < 2^14: c / G = floor((c + 1/2) / G), whose fractional part stays
+  // at least 1/(2G) away from an integer, far beyond the float rounding
+  const float inv_g = 1.0f / float(G);
   for (;;) {
-    int item = 0;
-    if (lane == 0) item = int(atomicAdd(w.counters + CTR_HN_ITEM, 1u));
-    item = __shfl_sync(0xffffffffu, item, 0);
+    if (threadIdx.x == 0) s_item = int(atomicAdd(w.counters + CTR_HN_ITEM, 1u));
+    __syncthreads();
+    const int item = s_item;
     if (item >= total) break;
     const int q = item / chunks_per_genome, chunk = item - q * chunks_per_genome;
     const int g = w.qorder[q];
     const GenomeHdr h = w.hdr[g];
     float *wg = weights + size_t(g) * G4;
+    const int t0 = chunk * tiles_per_chunk, t1 = min(t0 + tiles_per_chunk, tiles);
     const int32_t *io = w.pio + size_t(g) * 6;
-    const NodeRec *nr = w.knode + h.node_off;
-    const EdgeRec *er = w.kedge + h.edge_off;
-    const int64_t t0 = int64_t(chunk) * tiles_per_chunk;
-    for (int64_t tile = t0; tile < t0 + tiles_per_chunk; ++tile) {
-      const int64_t qi = tile * 32 + lane;
-      if (tile * 32 >= G4) break;
-      const bool active = qi < G4;
-      if (h.status != 0u) {
-        if (active) wg[qi] = qnan();
-        continue;
-      }
-      const int64_t sc = active ? qi / G2 : 0, tc = active ? qi - sc * G2 : 0;
-      const int si = int(sc % G), sj = int(sc / G), ti = int(tc % G), tj = int(tc / G);
-      v[io[0] * 32 + lane] = -1.0f + step * float(si);
-      v[io[1] * 32 + lane] = -1.0f + step * float(sj);
-      v[io[2] * 32 + lane] = -1.0f + step * float(ti);
-      v[io[3] * 32 + lane] = -1.0f + step * float(tj);
-      v[io[4] * 32 + lane] = 1.0f;
-      float *const scol[1] = {nullptr};
-      walk_program<false, 1>(nr, er, h.V, v + lane, scol, 0);
-      const float o = v[io[5] * 32 + lane];
-      if (active) wg[qi] = fabsf(o) > thresh ? o : 0.0f;
+    // stage when the scratch fits (CTA-uniform), then as many warps as have
+    // room for a value array take tiles
+    const bool can_stage =
+        h.status == 0u && hn_stage_bytes(h.V, h.E) <= smem_bytes - prog_bytes;
+    if (can_stage) hn_stage<SPL>(w, h, io, s_nodes, s_pairs, s_scan,
+                                   reinterpret_cast<char *>(hsm + prog_bytes), s_info);
+    __syncthreads();
+    const int rows = can_stage ? s_info[1] : 0;
+    const int vwarps = can_stage ? min(nw, (smem_bytes - prog_bytes) / (rows * RS * 4)) : 0;
+    if (h.status != 0u || (vwarps < 1 && !slots_ok)) {  // CTA-uniform
+      if (h.status == 0u && lane == 0) atomicOr(w.counters + CTR_ERR, ERR_SP_NO_SCRATCH);
+      for (int qi = t0 * RS + int(threadIdx.x); qi < min(t1 * RS, G4); qi += blockDim.x)
+        wg[qi] = qnan();
+      __syncthreads();  // s_item is rewritten by the next claim
+      continue;
     }
+    if (vwarps >= 1) {
+      if (wid < vwarps) {
+        const HnTile t{G, G2, G4, step, inv_g, thresh, 0, 1, 2, 3, 4, s_info[2], wg};
+        float *v = s_vals + size_t(wid) * rows * RS;  // shared memory
+        const int nn = s_info[0];
+#pragma unroll
+        for (int k = 0; k < SPL; ++k) {
+          v[(HN_ROW_ZERO * 32 + lane) * SPL + k] = 0.0f;
+          v[(HN_ROW_ONE * 32 + lane) * SPL + k] = 1.0f;
+        }
+        char *vb = reinterpret_cast<char *>(v + lane * SPL);
+        hn_tiles<SPL, true>(t, v, t0 + wid, t1, vwarps,
+                            [&]() { hn_walk<SPL>(s_nodes, nn, s_pairs, vb); });
+      }
+    } else {
+      const HnTile t{G, G2, G4, step, inv_g, thresh, io[0], io[1], io[2], io[3], io[4], io[5], wg};
+      const NodeRec *nr = w.knode + h.node_off;
+      const EdgeRec *er = w.kedge + h.edge_off;
+      float *vl = vg + lane;
+      hn_tiles<SPL, false>(t, vg, t0 + wid, t1, nw, [&]() {
+        float *const scol[SPL] = {};
+        walk_program<false, SPL>(nr, er, h.V, vl, scol, 0);
+      });
+    }
+    __syncthreads();  // the staged program and s_item are reused by the next item
   }
   grid_done_reset(w.counters + CTR_HN_ITEM, w.counters + CTR_HN_DONE);
 }
@@ -521,15 +933,26 @@ int forward_rec_occupancy(int warps) {
   return n;
 }
 
-cudaError_t launch_hyperneat(const Ws &w, int G, float thresh, float *weights, int warps,
-                             int ctas, cudaStream_t st) {
+cudaError_t launch_hyperneat(const Ws &w, int G, float thresh, float *weights, int spl,
+                             int warps, int ctas, int smem_bytes, cudaStream_t st) {
   if (w.P == 0) return cudaSuccess;
-  const size_t smem = forward_sp_smem(w.N, warps, 1);
   const int64_t G4 = int64_t(G) * G * G * G;
-  const int64_t tiles = (G4 + 31) / 32;
-  const int tiles_per_chunk = 16;
+  const int RS = 32 * spl;
+  const int64_t tiles = (G4 + RS - 1) / RS;
+  // about 16 K queries per item: staging is amortised, the tail stays short
+  const int tiles_per_chunk = std::max(1, 16384 / RS);
   const int chunks = int((tiles + tiles_per_chunk - 1) / tiles_per_chunk);
-  k_hyperneat<<<ctas, warps * 32, smem, st>>>(w, G, thresh, weights, chunks, tiles_per_chunk);
+  switch (spl) {
+#define NEAT_HN(L)                                                                          \
+  k_hyperneat<L><<<ctas, warps * 32, smem_bytes, st>>>(w, G, thresh, weights, chunks,       \
+                                                       tiles_per_chunk, smem_bytes);         \
+  break
+    case 1: NEAT_HN(1);
+    case 2: NEAT_HN(2);
+    case 4: NEAT_HN(4);
+#undef NEAT_HN
+    default: return cudaErrorInvalidValue;
+  }
   return cudaGetLastError();
 }
 
@@ -541,8 +964,10 @@ cudaError_t forward_set_smem_limit(int bytes) {
   if (e == cudaSuccess) e = set_dyn_smem_limit(k_forward_sp<2>, bytes);
   if (e == cudaSuccess) e = set_dyn_smem_limit(k_forward_sp<4>, bytes);
   if (e == cudaSuccess) e = set_dyn_smem_limit(k_forward_plain, bytes);
-  if (e != cudaSuccess) return e;
-  return set_dyn_smem_limit(k_hyperneat, bytes);
+  if (e == cudaSuccess) e = set_dyn_smem_limit(k_hyperneat<1>, bytes);
+  if (e == cudaSuccess) e = set_dyn_smem_limit(k_hyperneat<2>, bytes);
+  if (e == cudaSuccess) e = set_dyn_smem_limit(k_hyperneat<4>, bytes);
+  return e;
 }
 int forward_sp_occupancy(int warps, size_t smem, int spl) {
   int n = 0;
@@ -552,11 +977,14 @@ int forward_sp_occupancy(int warps, size_t smem, int spl) {
   if (spl == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_forward_sp<4>, warps * 32, smem);
   return e == cudaSuccess ? n : 0;
 }
-int hyperneat_occupancy(int warps, size_t smem) {
+int hyperneat_occupancy(int spl, int warps, size_t smem) {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hyperneat, warps * 32, smem) !=
-      cudaSuccess)
-    return 0;
-  return n;
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (spl) {
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hyperneat<1>, warps * 32, smem); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hyperneat<2>, warps * 32, smem); break;
+    case 4: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_hyperneat<4>, warps * 32, smem); break;
+  }
+  return e == cudaSuccess ? n : 0;
 }
 }  // namespace neat

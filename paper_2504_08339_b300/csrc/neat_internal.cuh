@@ -280,6 +280,40 @@ __device__ __forceinline__ float act_apply(int a, float z) {
   return __int_as_float(0x7fc00000);
 }
 
+// act applied to n values with one dispatch (the same functions as act_apply)
+template <int n>
+__device__ __forceinline__ void act_apply_n(int a, float (&z)[n]) {
+  switch (a) {
+    case NEAT_ACT_IDENTITY: return;
+    case NEAT_ACT_SIGMOID:
+#pragma unroll
+      for (int j = 0; j < n; ++j) z[j] = 1.0f / (1.0f + expf(-z[j]));
+      return;
+    case NEAT_ACT_TANH:
+#pragma unroll
+      for (int j = 0; j < n; ++j) z[j] = tanhf(z[j]);
+      return;
+    case NEAT_ACT_RELU:
+#pragma unroll
+      for (int j = 0; j < n; ++j) z[j] = fmaxf(z[j], 0.0f);
+      return;
+    case NEAT_ACT_SIN:
+#pragma unroll
+      for (int j = 0; j < n; ++j) z[j] = sinf(z[j]);
+      return;
+    case NEAT_ACT_GAUSSIAN:
+#pragma unroll
+      for (int j = 0; j < n; ++j) z[j] = expf(-(z[j] * z[j]));
+      return;
+    case NEAT_ACT_ABS:
+#pragma unroll
+      for (int j = 0; j < n; ++j) z[j] = fabsf(z[j]);
+      return;
+  }
+#pragma unroll
+  for (int j = 0; j < n; ++j) z[j] = __int_as_float(0x7fc00000);
+}
+
 // d act / dz given z and v = act(z)
 __device__ __forceinline__ float act_deriv(int a, float z, float v) {
   switch (a) {
@@ -337,15 +371,29 @@ cudaError_t launch_backward(const Ws &w, const float *inputs, int64_t stride, in
                             const float *grad_out, const float *saved, float *gw, float *gb,
                             float *gr, float *gi, int warps, int smem_bytes, cudaStream_t st);
 size_t backward_smem(int N, int C, int warps);
-cudaError_t launch_hyperneat(const Ws &w, int grid, float thresh, float *weights, int warps,
-                             int ctas, cudaStream_t st);
+// HyperNEAT query: spl queries per lane (1, 2 or 4), `ctas` CTAs of `warps`
+// warps with smem_bytes of dynamic shared memory (>= hn_prog_bytes(N, C)).  A
+// genome whose staging scratch or value array does not fit next to its staged
+// program uses the warp's workspace slot instead (unless every genome fits,
+// ctas * warps <= sp_scratch_slots(w, spl)).
+__host__ __device__ inline int hn_prog_bytes(int N, int C) {
+  return N * 16 + ((C + N) / 2 + 1) * 16;
+}
+// Rows of a staged value array: the five CPPN inputs, then constants 0 and 1,
+// then the rows the node values take (at most V - 5 of them).
+constexpr int HN_ROW_ZERO = 5, HN_ROW_ONE = 6, HN_ROW_FIRST = 7;
+// shared-memory scratch the staging needs for a genome of V positions and E
+// enabled connections (copies of its records, four ints per position)
+__host__ __device__ inline int hn_stage_bytes(int V, int E) { return V * 32 + E * 8; }
+cudaError_t launch_hyperneat(const Ws &w, int grid, float thresh, float *weights, int spl,
+                             int warps, int ctas, int smem_bytes, cudaStream_t st);
 // one-time kernel attributes and occupancy queries (host side)
 cudaError_t transform_set_smem_limit(int bytes);
 size_t transform_smem(int N, int C);
 cudaError_t forward_set_smem_limit(int bytes);
 cudaError_t backward_set_smem_limit(int bytes);
 int forward_sp_occupancy(int warps, size_t smem, int spl);
-int hyperneat_occupancy(int warps, size_t smem);
+int hyperneat_occupancy(int spl, int warps, size_t smem);
 // level-synchronous small-S form
 cudaError_t launch_lvl_build(const Ws &w, cudaStream_t st);
 size_t forward_lvl_smem(const Ws &w, int st_samples);

@@ -358,6 +358,62 @@ def _check_threshold(out, ref, raw, bnd):
     assert ok.all()
 
 
+def test_hyperneat_every_aggregation_and_shape():
+    """CPPNs with every activation and aggregation (the staged walk pads odd
+    in-degrees with an edge that leaves each aggregate unchanged) and many
+    nodes the output does not depend on (not evaluated): every launch shape
+    gives the same bits, and those match the oracle."""
+    from workloads import GenomeSpec, make_population
+    spec = GenomeSpec(I=5, O=1, N=48, C=160, hidden=(0, 40), E_uniform=(10, 160),
+                      acts=("identity", "sigmoid", "tanh", "relu", "sin", "gaussian", "abs"),
+                      aggs=("sum", "product", "max", "mean"), w_std=0.9, b_std=0.4)
+    P, G = 40, 7
+    nodes, conns = make_population(spec, P, seed=31)
+    plan = _plan(spec, P)
+    plan.transform(_dev(nodes), _dev(conns))
+    outs = []
+    for spl in (1, 2, 4):
+        for warps in (1, 4, 8, 16):
+            plan.set_tuning(samples_per_lane=spl, warps_per_cta=warps)
+            outs.append(plan.hyperneat(grid=G, thresh=0.2).view(torch.int32).clone())
+    for o in outs[1:]:
+        assert torch.equal(o, outs[0])
+    out = outs[0].view(torch.float32).cpu().numpy().reshape(P, -1)
+    ref, raw, bnd = oracle.hyperneat(nodes, conns, grid=G, thresh=0.2, with_raw=True,
+                                     with_bound=True)
+    _check_threshold(out, ref, raw, bnd)
+
+
+def test_hyperneat_maximum_sizes():
+    """N = 1024, C = 8192 CPPNs: the staged walk where a genome's value rows fit
+    in shared memory, the workspace-slot walk where they do not."""
+    from workloads import GenomeSpec, make_population
+    spec = GenomeSpec(I=5, O=1, N=1024, C=8192, V_loguniform=(20, 1024),
+                      E_loguniform=(30, 8192), acts=("tanh", "sin", "gaussian"),
+                      aggs=("sum", "mean", "max"), w_std=0.5, b_std=0.5)
+    P, G = 7, 5
+    nodes, conns = make_population(spec, P - 1, seed=12)
+    # plus one wide genome: 1000 hidden nodes between the inputs and the output,
+    # all live at once (more value rows than shared memory holds per warp)
+    from genome_builders import genome
+    H = 1000
+    rng = np.random.default_rng(4)
+    nl = [(r, r, 0.0, 1.0, 0, 0) for r in range(5)] + [(5, 5, 0.1, 1.0, 2, 0)]
+    nl += [(6 + h, 6 + h, float(rng.normal()), 1.0, int(rng.choice([2, 4, 5])), 0)
+           for h in range(H)]
+    cl = [(2 * h, h % 5, 6 + h, float(rng.normal()), 1.0) for h in range(H)]
+    cl += [(2 * h + 1, 6 + h, 5, float(rng.normal()) * 0.05, 1.0) for h in range(H)]
+    n1, c1 = genome(spec.N, spec.C, nl, cl)
+    nodes = np.concatenate([nodes, n1[None]])
+    conns = np.concatenate([conns, c1[None]])
+    plan = _plan(spec, P)
+    plan.transform(_dev(nodes), _dev(conns))
+    out = plan.hyperneat(grid=G, thresh=0.2).cpu().numpy().reshape(P, -1)
+    ref, raw, bnd = oracle.hyperneat(nodes, conns, grid=G, thresh=0.2, with_raw=True,
+                                     with_bound=True)
+    _check_threshold(out, ref, raw, bnd)
+
+
 def test_hyperneat_full_size_sampled():
     """All 256 CPPNs on the 32x32 substrate (268M queries, 1 GiB of weights);
     every query of 4 genomes and a 1% sample of 8 more are checked."""
