@@ -145,11 +145,12 @@ __device__ __forceinline__ void node_agg(const NodeRec &n, const EdgeRec *__rest
 }
 
 // Value (and saved aggregate) of the node at position p for this lane's SPL
-// samples; inputs are left alone.
+// samples; inputs are left alone, and so are nodes no output depends on
+// unless the aggregates are saved.
 template <bool SAVE, int SPL>
 __device__ __forceinline__ void eval_node(const NodeRec &n, int p, const EdgeRec *__restrict__ er,
                                           float *vl, float *const (&scol)[SPL], int S) {
-  if (n.meta & META_INPUT) return;
+  if (n.meta & (SAVE ? META_INPUT : META_INPUT | META_DEAD)) return;
   float a[SPL];
   node_agg<SPL>(n, er, vl, a);
   const int act = meta_act(n.meta);
@@ -192,7 +193,7 @@ __device__ __forceinline__ void grid_done_reset(uint32_t *item_ctr, uint32_t *do
 // slot of the workspace value array (L1/L2-resident while in use).
 //
 // With `coop`, the items of the queue's first counters[CTR_SP_NBIG] genomes
-// (the most expensive ones, E + 2V >= SP_COOP_COST) are taken by whole CTAs:
+// (the most expensive ones, sp_cost >= SP_COOP_COST) are taken by whole CTAs:
 // the CTA's warps split each frontier's positions (no position of a frontier
 // reads another's value) with a barrier between frontiers, in the slot of the
 // CTA's first warp.  One warp walking such a genome alone would finish long

@@ -8,8 +8,9 @@
 // of every genome in the batch.  A round has two fully packed phases: one
 // thread per 4-edge chunk of incoming connections (partial sum / product /
 // max), then one thread per node (combine the partials, bias, response,
-// activation).  Nodes are sorted by activation so a warp runs one activation
-// branch, and by descending in-degree.
+// activation).  Nodes no output depends on are not evaluated at all (this
+// form returns only the outputs).  Nodes are sorted by activation so a warp
+// runs one activation branch, and by descending in-degree.
 //
 // Transform time (k_lvl_plan, k_lvl_build): genomes in layer-sorted queue
 // order are cut into batches under a byte budget and each batch program is
@@ -45,7 +46,7 @@ __global__ void __launch_bounds__(1024) k_lvl_plan(Ws w) {
   auto pbw = [&](int q, int &pb, int &wt) {
     const GenomeHdr h = w.hdr[w.qlvl[q]];
     const bool ok = h.status == 0u;
-    pb = lvl_genome_bytes(h.V, h.nch, h.L, I, O, ok);
+    pb = lvl_genome_bytes(h.nlive + I, h.nch, h.L, I, O, ok);  // tasks: the live nodes
     wt = lvl_genome_weight(pb, ok ? h.V : 0, budget, sb);
   };
   long long sw = 0, sp = 0;
@@ -113,7 +114,7 @@ constexpr int BLD_THREADS = 256;
 __global__ void __launch_bounds__(BLD_THREADS) k_lvl_build(Ws w) {
   __shared__ int g_id[LVL_MAX_GENOMES + 1], g_V[LVL_MAX_GENOMES + 1], g_L[LVL_MAX_GENOMES + 1];
   __shared__ int g_noff[LVL_MAX_GENOMES + 1], g_eoff[LVL_MAX_GENOMES + 1];
-  __shared__ int g_slot[LVL_MAX_GENOMES + 1];
+  __shared__ int g_slot[LVL_MAX_GENOMES + 1], g_NL[LVL_MAX_GENOMES + 1];
   __shared__ int s_nslots, s_ntasks, s_nrounds, s_bad;
   __shared__ int wbuf[33];
   extern __shared__ __align__(16) unsigned char dsm[];
@@ -136,6 +137,7 @@ __global__ void __launch_bounds__(BLD_THREADS) k_lvl_build(Ws w) {
     g_id[k] = g;
     g_V[k] = ok ? h.V : 0;
     g_L[k] = ok ? h.L : 0;
+    g_NL[k] = ok ? h.nlive : 0;
     g_noff[k] = h.node_off;
     g_eoff[k] = h.edge_off;
   }
@@ -146,7 +148,7 @@ __global__ void __launch_bounds__(BLD_THREADS) k_lvl_build(Ws w) {
       g_slot[k] = s;
       s += g_V[k];
       nr = max(nr, g_L[k]);
-      nt += g_V[k] > 0 ? g_V[k] - I : 0;
+      nt += g_NL[k];
     }
     g_slot[ng] = s;
     s_nslots = s;
@@ -157,7 +159,8 @@ __global__ void __launch_bounds__(BLD_THREADS) k_lvl_build(Ws w) {
   const int nslots = s_nslots, ntasks = s_ntasks;
   if (nslots > LVL_MAX_SLOTS) return;  // cannot happen by construction of the weights
   const int n2 = pow2_ceil_d(max(nslots, 1));
-  // task keys: (layer, act, -cnt, genome, position); inputs sort last
+  // task keys: (layer, act, -cnt, genome, position); inputs and the nodes no
+  // output depends on sort last (they are not tasks)
   for (int i = tid; i < n2; i += T) {
     uint64_t key = ~0ull;
     if (i < nslots) {
@@ -165,7 +168,7 @@ __global__ void __launch_bounds__(BLD_THREADS) k_lvl_build(Ws w) {
       while (g_slot[k + 1] <= i) ++k;
       const int p = i - g_slot[k];
       const NodeRec n = w.knode[g_noff[k] + p];
-      if (!(n.meta & META_INPUT)) {
+      if (!(n.meta & (META_INPUT | META_DEAD))) {
         const uint64_t lay = uint64_t(w.player[size_t(g_id[k]) * w.N + p]);
         key = (lay << 33) | (uint64_t(meta_act(n.meta)) << 30) |
               (uint64_t(16383 - meta_cnt(n.meta)) << 16) | (uint64_t(k) << 10) | uint64_t(p);

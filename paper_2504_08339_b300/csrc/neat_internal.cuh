@@ -17,10 +17,13 @@ namespace neat {
 
 // -- node record (16 B) -------------------------------------------------------
 // meta bits: [0,14) in-degree, [16,20) activation id, [20,24) aggregation id,
-// bit 24 = input node, bit 25 = valid position.
+// bit 24 = input node, bit 25 = valid position, bit 26 = a non-input node no
+// output depends on (feed-forward transform only): a forward that returns
+// only the outputs need not evaluate it.
 constexpr uint32_t META_CNT_MASK = 0x3fffu;
 constexpr uint32_t META_INPUT = 1u << 24;
 constexpr uint32_t META_VALID = 1u << 25;
+constexpr uint32_t META_DEAD = 1u << 26;
 struct __align__(16) NodeRec {
   float bias;
   float resp;
@@ -37,7 +40,7 @@ struct __align__(8) EdgeRec {
   float w;
 };
 
-// -- per-genome header (32 B) ---------------------------------------------------
+// -- per-genome header (48 B) ---------------------------------------------------
 struct __align__(16) GenomeHdr {
   int V;         // valid nodes (0 for a rejected genome)
   int E;         // enabled connections
@@ -45,8 +48,11 @@ struct __align__(16) GenomeHdr {
   uint32_t status;
   int node_off;  // ragged-packed offsets (queue order)
   int edge_off;
-  int lvl_off;   // unused (reserved)
-  int nch;       // 4-edge chunks of the level-synchronous form: sum of ceil(indeg/4)
+  int nlive;     // non-input nodes some output depends on (the others: META_DEAD)
+  int nch;       // 4-edge chunks of the level-synchronous form over those nodes:
+                 // sum of ceil(indeg/4)
+  int elive;     // enabled connections into those nodes
+  int pad[3];
 };
 
 // -- level-synchronous batches (small-S form) --------------------------------------
@@ -257,12 +263,17 @@ inline Ws make_ws(void *base, const Layout &L, int P, int N, int C, int I, int O
 constexpr int CTR_FWD_ITEM = 0, CTR_FWD_DONE = 1, CTR_HN_ITEM = 2, CTR_HN_DONE = 3,
               CTR_LVL_ITEM = 4, CTR_LVL_DONE = 5, CTR_FWD_BIG = 6, CTR_SP_NBIG = 7,
               CTR_NBATCH = 8, CTR_ERR = 9, CTR_REC_ITEM = 10, CTR_REC_DONE = 11;
-// genomes of at least this cost (E + 2V) are evaluated by a whole CTA in the
+// genomes of at least this cost (sp_cost) are evaluated by a whole CTA in the
 // sample-parallel forward (counters[CTR_SP_NBIG] of them, a queue prefix)
 #ifndef NEAT_SP_COOP_COST
 #define NEAT_SP_COOP_COST 2048
 #endif
 constexpr int SP_COOP_COST = NEAT_SP_COOP_COST;
+// cost of a genome in the sample-parallel forward: edges + 2 * nodes of the
+// part some output depends on, plus a quarter per skipped position
+__host__ __device__ inline int sp_cost(const GenomeHdr &h) {
+  return h.elive + 2 * h.nlive + (h.V - h.nlive) / 4;
+}
 // error bits in counters[CTR_ERR]
 constexpr uint32_t ERR_TMA_TIMEOUT = 1u, ERR_SP_NO_SCRATCH = 2u;
 

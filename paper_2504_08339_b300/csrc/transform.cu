@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(256) k_transform(Ws w, const float *__restrict
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ int wbuf[33];
   __shared__ unsigned s_status;
-  __shared__ int s_V, s_E, s_nch;
+  __shared__ int s_V, s_E, s_nch, s_nlive, s_elive;
 
   const int N = w.N, C = w.C, I = w.I, O = w.O;
   const int g = blockIdx.x, tid = threadIdx.x, T = blockDim.x;
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(256) k_transform(Ws w, const float *__restrict
   const float *gn = nodes + size_t(g) * N * 5;
   const float *gc = conns + size_t(g) * C * 4;
 
-  if (tid == 0) { s_status = 0u; s_V = 0; s_E = 0; s_nch = 0; }
+  if (tid == 0) { s_status = 0u; s_V = 0; s_E = 0; s_nch = 0; s_nlive = 0; s_elive = 0; }
   __syncthreads();
 
   // 1. node rows: validity, attribute checks, (key,row) sort keys
@@ -339,18 +339,52 @@ __global__ void __launch_bounds__(256) k_transform(Ws w, const float *__restrict
   // 7. padded program (valid genomes only)
   GenomeHdr h;
   h.V = 0; h.E = 0; h.L = 0; h.status = status; h.node_off = 0; h.edge_off = 0;
-  h.lvl_off = -1; h.nch = 0;
+  h.nlive = 0; h.nch = 0; h.elive = 0; h.pad[0] = h.pad[1] = h.pad[2] = 0;
   if (status == 0u) {
     h.V = V; h.E = E; h.L = t;
-    // edge begin per position; 4-edge chunk count of the level-synchronous form
-    int my_nch = 0;
+    // nodes some output depends on: the outputs, then frontier by frontier
+    // from the last, the sources of every such node (feed-forward only; in a
+    // recurrent network every node counts)
+    int *live = ready;     // free after the sort
+    int *fstart = outbeg;  // first position of each frontier (N + 1 entries)
+    for (int s = tid; s < V; s += T) live[s] = recurrent ? 1 : 0;
+    __syncthreads();
+    if (!recurrent) {
+      for (int p = tid; p < V; p += T)
+        if (p == 0 || layer_s[order_s[p]] != layer_s[order_s[p - 1]])
+          fstart[layer_s[order_s[p]]] = p;
+      if (tid == 0) fstart[t] = V;
+      for (int i = tid; i < O; i += T) live[s_of_row[I + i]] = 1;
+      __syncthreads();
+      for (int l = t - 1; l >= 0; --l) {
+        for (int p = fstart[l] + tid; p < fstart[l + 1]; p += T) {
+          const int s = order_s[p];
+          if (live[s])
+            for (int k = inbeg[s]; k < inbeg[s] + indeg[s]; ++k)
+              live[int((ek[k] >> 20) & 0xfffffu)] = 1;
+        }
+        __syncthreads();
+      }
+    }
+    // edge begin per position; 4-edge chunk count of the level-synchronous
+    // form, live nodes and their connections
+    int my_nch = 0, my_nl = 0, my_el = 0;
     for (int p = tid; p < V; p += T) {
-      tmp[p] = indeg[order_s[p]];
-      my_nch += (tmp[p] + 3) >> 2;
+      const int s = order_s[p];
+      tmp[p] = indeg[s];
+      if (live[s] && row_of_s[s] >= I) {
+        my_nch += (indeg[s] + 3) >> 2;
+        ++my_nl;
+        my_el += indeg[s];
+      }
     }
     if (my_nch) atomicAdd(&s_nch, my_nch);
+    if (my_nl) atomicAdd(&s_nlive, my_nl);
+    if (my_el) atomicAdd(&s_elive, my_el);
     __syncthreads();
     h.nch = s_nch;
+    h.nlive = s_nlive;
+    h.elive = s_elive;
     block_exclusive_scan(tmp, V, wbuf);
     NodeRec *pn = w.pnode + size_t(g) * N;
     int32_t *prow = w.prow + size_t(g) * N;
@@ -368,6 +402,7 @@ __global__ void __launch_bounds__(256) k_transform(Ws w, const float *__restrict
           rec.resp = 1.0f;
         } else {
           meta |= (uint32_t(nr[3]) << 16) | (uint32_t(nr[4]) << 20);
+          if (!live[s]) meta |= META_DEAD;
           rec.bias = nr[1];
           rec.resp = nr[2];
         }
@@ -400,11 +435,12 @@ __global__ void __launch_bounds__(256) k_transform(Ws w, const float *__restrict
 }
 
 // Work-queue order: genomes by descending cost (ties: lower id first).
-// mode 0: cost = E + 2V (sample-parallel forward); mode 1: layers first, then E.
+// mode 0: cost = the live part's E + 2V (sample-parallel forward); mode 1:
+// layers first, then E.
 __device__ __forceinline__ uint64_t cost_key(const GenomeHdr &h, int mode, int g) {
   uint32_t cost;
   if (h.status != 0u) cost = 0u;
-  else if (mode == 0) cost = uint32_t(h.E + 2 * h.V + 1);
+  else if (mode == 0) cost = uint32_t(sp_cost(h) + 1);
   else cost = (uint32_t(h.L) << 16) | uint32_t(min(h.E, 0xffff));
   return (uint64_t(cost) << 32) | uint64_t(0xffffffffu - uint32_t(g));
 }
@@ -442,7 +478,7 @@ __global__ void __launch_bounds__(1024) k_offsets(Ws w) {
     se += h.E;
     // the most expensive genomes (a prefix of the cost-sorted queue) go to
     // whole CTAs in the sample-parallel forward
-    sb += (h.status == 0u && h.E + 2 * h.V >= SP_COOP_COST) ? 1 : 0;
+    sb += (h.status == 0u && sp_cost(h) >= SP_COOP_COST) ? 1 : 0;
   }
   if (sb) atomicAdd(&nbig, sb);
   int xv = sv, xe = se;
