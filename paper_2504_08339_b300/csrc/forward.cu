@@ -187,10 +187,151 @@ __device__ __forceinline__ void grid_done_reset(uint32_t *item_ctr, uint32_t *do
   }
 }
 
+// the SPL values of one lane in a staged value row (one vector load / store)
+template <int SPL>
+struct HnVec;
+template <>
+struct HnVec<1> {
+  __device__ __forceinline__ static void ld(const char *p, float (&x)[1]) {
+    x[0] = *reinterpret_cast<const float *>(p);
+  }
+  __device__ __forceinline__ static void st(char *p, const float (&x)[1]) {
+    *reinterpret_cast<float *>(p) = x[0];
+  }
+};
+template <>
+struct HnVec<2> {
+  __device__ __forceinline__ static void ld(const char *p, float (&x)[2]) {
+    const float2 v = *reinterpret_cast<const float2 *>(p);
+    x[0] = v.x;
+    x[1] = v.y;
+  }
+  __device__ __forceinline__ static void st(char *p, const float (&x)[2]) {
+    *reinterpret_cast<float2 *>(p) = make_float2(x[0], x[1]);
+  }
+};
+template <>
+struct HnVec<4> {
+  __device__ __forceinline__ static void ld(const char *p, float (&x)[4]) {
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    x[0] = v.x;
+    x[1] = v.y;
+    x[2] = v.z;
+    x[3] = v.w;
+  }
+  __device__ __forceinline__ static void st(char *p, const float (&x)[4]) {
+    *reinterpret_cast<float4 *>(p) = make_float4(x[0], x[1], x[2], x[3]);
+  }
+};
+
+// a[j] = fma(w, x[j], a[j]) for the SPL queries, two per instruction (the
+// paired fp32 FMA; each component rounds as fmaf)
+template <int SPL>
+__device__ __forceinline__ void hn_fma(float w, const float (&x)[SPL], float (&a)[SPL]) {
+  if constexpr (SPL == 1) {
+    a[0] = fmaf(w, x[0], a[0]);
+  } else {
+#pragma unroll
+    for (int j = 0; j < SPL; j += 2) {
+      const float2 r = __ffma2_rn(make_float2(w, w), make_float2(x[j], x[j + 1]),
+                                  make_float2(a[j], a[j + 1]));
+      a[j] = r.x;
+      a[j + 1] = r.y;
+    }
+  }
+}
+
+// Walk of a compiled program (CNode records and edge pairs; see
+// neat_internal.cuh) for this lane's SPL samples.  vb = the warp's value array
+// + lane * SPL floats (bytes); value row r of it at vb + r * 128 * SPL
+// ([row][32 lanes][SPL]: one vector access per row and lane).  GLOBAL: the
+// records come from global memory (read-only path), else from shared memory.
+// Per node: a 16-byte record; per two edges: one 16-byte pair; per edge and
+// sample: one value and one FMA.  Sum and mean keep even edges in a0 and odd
+// edges in a1, the rounding order of the position walk.
+template <int SPL, bool GLOBAL>
+__device__ __forceinline__ void cwalk(const CNode *__restrict__ nodes, int nn,
+                                      const uint4 *__restrict__ pairs, char *vb) {
+  constexpr int SH = 7 + (SPL == 4 ? 2 : (SPL == 2 ? 1 : 0));
+  auto ldp = [](const uint4 *p) { return GLOBAL ? __ldg(p) : *p; };
+  for (int c = 0; c < nn; ++c) {
+    const uint4 nraw = ldp(reinterpret_cast<const uint4 *>(nodes + c));
+    const float bias = __uint_as_float(nraw.x), resp = __uint_as_float(nraw.y);
+    const uint32_t meta = nraw.w;
+    const int np = int(nraw.z >> CN_PAIR_BITS);
+    const uint4 *pp = pairs + (nraw.z & ((1u << CN_PAIR_BITS) - 1u));
+    const int agg = int(meta >> (CN_ROW_BITS + 3)) & 3;
+    float a[SPL];
+    if (agg == NEAT_AGG_SUM || agg == NEAT_AGG_MEAN) {
+      float a0[SPL], a1[SPL];
+#pragma unroll
+      for (int j = 0; j < SPL; ++j) a0[j] = a1[j] = 0.0f;
+#pragma unroll 2
+      for (int k = 0; k < np; ++k) {
+        const uint4 e = ldp(pp + k);
+        float x0[SPL], x1[SPL];
+        HnVec<SPL>::ld(vb + (e.x << SH), x0);
+        HnVec<SPL>::ld(vb + (e.z << SH), x1);
+        hn_fma<SPL>(__uint_as_float(e.y), x0, a0);
+        hn_fma<SPL>(__uint_as_float(e.w), x1, a1);
+      }
+#pragma unroll
+      for (int j = 0; j < SPL; ++j) a[j] = a0[j] + a1[j];
+      if (agg == NEAT_AGG_MEAN && np > 0) {
+        const float cnt = float(2 * np - int((meta >> (CN_ROW_BITS + 5)) & 1u));
+#pragma unroll
+        for (int j = 0; j < SPL; ++j) a[j] = a[j] / cnt;
+      }
+    } else if (np == 0) {
+#pragma unroll
+      for (int j = 0; j < SPL; ++j) a[j] = 0.0f;
+    } else if (agg == NEAT_AGG_MAX) {
+      const uint4 e = ldp(pp);
+      float x0[SPL], x1[SPL];
+      HnVec<SPL>::ld(vb + (e.x << SH), x0);
+      HnVec<SPL>::ld(vb + (e.z << SH), x1);
+#pragma unroll
+      for (int j = 0; j < SPL; ++j)
+        a[j] = fmaxf(__uint_as_float(e.y) * x0[j], __uint_as_float(e.w) * x1[j]);
+      for (int k = 1; k < np; ++k) {
+        const uint4 f = ldp(pp + k);
+        HnVec<SPL>::ld(vb + (f.x << SH), x0);
+        HnVec<SPL>::ld(vb + (f.z << SH), x1);
+#pragma unroll
+        for (int j = 0; j < SPL; ++j) {
+          a[j] = fmaxf(a[j], __uint_as_float(f.y) * x0[j]);
+          a[j] = fmaxf(a[j], __uint_as_float(f.w) * x1[j]);
+        }
+      }
+    } else {  // product
+#pragma unroll
+      for (int j = 0; j < SPL; ++j) a[j] = 1.0f;
+      for (int k = 0; k < np; ++k) {
+        const uint4 f = ldp(pp + k);
+        float x0[SPL], x1[SPL];
+        HnVec<SPL>::ld(vb + (f.x << SH), x0);
+        HnVec<SPL>::ld(vb + (f.z << SH), x1);
+#pragma unroll
+        for (int j = 0; j < SPL; ++j) {
+          a[j] = a[j] * (__uint_as_float(f.y) * x0[j]);
+          a[j] = a[j] * (__uint_as_float(f.w) * x1[j]);
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < SPL; ++j) a[j] = fmaf(resp, a[j], bias);
+    act_apply_n<SPL>(int(meta >> CN_ROW_BITS) & 7, a);
+    HnVec<SPL>::st(vb + ((meta & ((1u << CN_ROW_BITS) - 1u)) << SH), a);
+  }
+}
+
 // Item = (genome in queue order, tile of 32 * SPL samples); lane l evaluates
-// samples tile * 32 * SPL + j * 32 + l, j < SPL.  The values of a genome with
-// V <= vcap live in this warp's shared-memory array, the others in the warp's
-// slot of the workspace value array (L1/L2-resident while in use).
+// samples tile * 32 * SPL + j * 32 + l, j < SPL.  A call without saved
+// aggregates walks the genome's compiled program (value rows, only the nodes
+// the outputs depend on), one that saves them the position program.  Values
+// needing at most vcap rows live in this warp's shared-memory array, the
+// others in the warp's slot of the workspace value array (N + 2 rows;
+// L1/L2-resident while in use).
 //
 // With `coop`, the items of the queue's first counters[CTR_SP_NBIG] genomes
 // (the most expensive ones, sp_cost >= SP_COOP_COST) are taken by whole CTAs:
@@ -198,7 +339,7 @@ __device__ __forceinline__ void grid_done_reset(uint32_t *item_ctr, uint32_t *do
 // reads another's value) with a barrier between frontiers, in the slot of the
 // CTA's first warp.  One warp walking such a genome alone would finish long
 // after the rest of the grid.  The remaining items are claimed per warp.
-template <int SPL>
+template <int SPL, bool COMP>
 __global__ void __launch_bounds__(512, 3)
     k_forward_sp(Ws w, const float *__restrict__ inputs, int64_t stride, int S,
                              float *__restrict__ out, float *__restrict__ saved, int tiles,
@@ -210,9 +351,9 @@ __global__ void __launch_bounds__(512, 3)
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int N = w.N, I = w.I, O = w.O;
   float *vs = smv + size_t(wid) * vcap * RS;
-  const size_t slot = size_t(blockIdx.x) * nw + wid;
-  float *vg = (w.sp_scratch != nullptr && (slot + 1) * size_t(N) * RS <= w.sp_scratch_floats)
-                  ? w.sp_scratch + slot * size_t(N) * RS
+  const size_t slot = size_t(blockIdx.x) * nw + wid, SLOT = size_t(N + 2) * RS;
+  float *vg = (w.sp_scratch != nullptr && (slot + 1) * SLOT <= w.sp_scratch_floats)
+                  ? w.sp_scratch + slot * SLOT
                   : nullptr;
   const int total = w.P * tiles;
   const int big_items = coop ? min(total, int(w.counters[CTR_SP_NBIG]) * tiles) : 0;
@@ -220,8 +361,8 @@ __global__ void __launch_bounds__(512, 3)
   // ---- CTA-wide items (vg of warp 0 is the CTA's slot: the grid is sized
   // so that every warp of it has one)
   float *vc = (w.sp_scratch != nullptr &&
-               (size_t(blockIdx.x) * nw + 1) * size_t(N) * RS <= w.sp_scratch_floats)
-                  ? w.sp_scratch + size_t(blockIdx.x) * nw * size_t(N) * RS
+               (size_t(blockIdx.x) * nw + 1) * SLOT <= w.sp_scratch_floats)
+                  ? w.sp_scratch + size_t(blockIdx.x) * nw * SLOT
                   : nullptr;
   while (big_items > 0) {
     if (threadIdx.x == 0) s_item = int(atomicAdd(w.counters + CTR_FWD_BIG, 1u));
@@ -267,7 +408,7 @@ __global__ void __launch_bounds__(512, 3)
     for (int l = 0; l < h.L; ++l) {
       const int p1 = s_lstart[l + 1];
       for (int p = s_lstart[l] + wid; p < p1; p += nw) {
-        if (saved != nullptr)
+        if (!COMP && saved != nullptr)
           eval_node<true, SPL>(ld_node(nr + p), p, er, vl, scol, S);
         else
           eval_node<false, SPL>(ld_node(nr + p), p, er, vl, scol, S);
@@ -290,18 +431,51 @@ __global__ void __launch_bounds__(512, 3)
     const int q = item / tiles, tile = item - q * tiles;
     const int g = w.qorder[q];
     const GenomeHdr h = w.hdr[g];
-    float *v = h.V <= vcap ? vs : vg;
+    // COMP: a call without saved aggregates on a plan with compiled programs
+    const bool comp = COMP && h.crows > 0;
+    const int need = comp ? h.crows : h.V;  // rows of the value array
     int sj[SPL];
 #pragma unroll
     for (int j = 0; j < SPL; ++j) sj[j] = tile * RS + j * 32 + lane;
-    if (h.status != 0u || v == nullptr) {
-      if (v == nullptr && lane == 0) atomicOr(w.counters + CTR_ERR, ERR_SP_NO_SCRATCH);
+    if (h.status != 0u || (need > vcap && vg == nullptr)) {
+      if (h.status == 0u && lane == 0) atomicOr(w.counters + CTR_ERR, ERR_SP_NO_SCRATCH);
 #pragma unroll
       for (int j = 0; j < SPL; ++j)
         if (sj[j] < S)
           for (int o = 0; o < O; ++o) out[(size_t(g) * S + sj[j]) * O + o] = qnan();
       continue;
     }
+    if constexpr (COMP) {
+      // compiled program, values [row][32][SPL]: rows 0..I-1 the inputs, I and
+      // I+1 the constants 0 and 1
+      const CNode *cn = w.cnode + size_t(g) * N;
+      const uint4 *cp = w.cpair + size_t(g) * cpair_cap(N, w.C);
+      const int32_t *orow = w.cout + size_t(g) * O;
+      auto run = [&](float *v) {
+#pragma unroll
+        for (int j = 0; j < SPL; ++j) {
+          const bool active = sj[j] < S;
+          const float *in = inputs + size_t(g) * stride + size_t(active ? sj[j] : 0) * I;
+          for (int i = 0; i < I; ++i) v[(i * 32 + lane) * SPL + j] = active ? __ldg(in + i) : 0.0f;
+          v[(I * 32 + lane) * SPL + j] = 0.0f;
+          v[((I + 1) * 32 + lane) * SPL + j] = 1.0f;
+        }
+        cwalk<SPL, true>(cn, h.nlive, cp, reinterpret_cast<char *>(v + lane * SPL));
+#pragma unroll
+        for (int j = 0; j < SPL; ++j)
+          if (sj[j] < S)
+            for (int o = 0; o < O; ++o)
+              out[(size_t(g) * S + sj[j]) * O + o] = v[(orow[o] * 32 + lane) * SPL + j];
+      };
+      if (comp) {
+        if (need <= vcap)
+          run(vs);  // shared memory
+        else
+          run(vg);
+        continue;
+      }
+    }
+    float *v = need <= vcap ? vs : vg;
     float *vl = v + lane;
     const int32_t *io = w.pio + size_t(g) * (I + O);
 #pragma unroll
@@ -312,7 +486,7 @@ __global__ void __launch_bounds__(512, 3)
     }
     const NodeRec *nr = w.knode + h.node_off;
     const EdgeRec *er = w.kedge + h.edge_off;
-    if (saved != nullptr) {
+    if (!COMP && saved != nullptr) {
       float *scol[SPL];
 #pragma unroll
       for (int j = 0; j < SPL; ++j)
@@ -498,62 +672,8 @@ __device__ __forceinline__ void block_scan2(int a, int b, int &ea, int &eb, int 
   __syncthreads();  // s is reused by the next call
 }
 
-// the SPL values of one lane in a staged value row (one vector load / store)
-template <int SPL>
-struct HnVec;
-template <>
-struct HnVec<1> {
-  __device__ __forceinline__ static void ld(const char *p, float (&x)[1]) {
-    x[0] = *reinterpret_cast<const float *>(p);
-  }
-  __device__ __forceinline__ static void st(char *p, const float (&x)[1]) {
-    *reinterpret_cast<float *>(p) = x[0];
-  }
-};
-template <>
-struct HnVec<2> {
-  __device__ __forceinline__ static void ld(const char *p, float (&x)[2]) {
-    const float2 v = *reinterpret_cast<const float2 *>(p);
-    x[0] = v.x;
-    x[1] = v.y;
-  }
-  __device__ __forceinline__ static void st(char *p, const float (&x)[2]) {
-    *reinterpret_cast<float2 *>(p) = make_float2(x[0], x[1]);
-  }
-};
-template <>
-struct HnVec<4> {
-  __device__ __forceinline__ static void ld(const char *p, float (&x)[4]) {
-    const float4 v = *reinterpret_cast<const float4 *>(p);
-    x[0] = v.x;
-    x[1] = v.y;
-    x[2] = v.z;
-    x[3] = v.w;
-  }
-  __device__ __forceinline__ static void st(char *p, const float (&x)[4]) {
-    *reinterpret_cast<float4 *>(p) = make_float4(x[0], x[1], x[2], x[3]);
-  }
-};
-
 // Walk of a staged program for this lane's SPL queries; vb = the warp's value
 // array + lane * SPL floats (bytes), row stride 32 * SPL floats.
-// a[j] = fma(w, x[j], a[j]) for the SPL queries, two per instruction (the
-// paired fp32 FMA; each component rounds as fmaf)
-template <int SPL>
-__device__ __forceinline__ void hn_fma(float w, const float (&x)[SPL], float (&a)[SPL]) {
-  if constexpr (SPL == 1) {
-    a[0] = fmaf(w, x[0], a[0]);
-  } else {
-#pragma unroll
-    for (int j = 0; j < SPL; j += 2) {
-      const float2 r = __ffma2_rn(make_float2(w, w), make_float2(x[j], x[j + 1]),
-                                  make_float2(a[j], a[j + 1]));
-      a[j] = r.x;
-      a[j + 1] = r.y;
-    }
-  }
-}
-
 template <int SPL>
 __device__ __forceinline__ void hn_walk(const HnNode *__restrict__ nodes, int nn,
                                         const uint4 *__restrict__ pairs, char *vb) {
@@ -897,15 +1017,21 @@ cudaError_t launch_forward_sp(const Ws &w, const float *inputs, int64_t stride, 
   const size_t smem = forward_sp_smem(sh.vcap, sh.warps, sh.spl);
   const int tiles = (S + 32 * sh.spl - 1) / (32 * sh.spl);
   const dim3 grid(unsigned(sh.grid)), block(unsigned(sh.warps * 32));
-  switch (sh.spl) {
-    case 1: k_forward_sp<1><<<grid, block, smem, st>>>(w, inputs, stride, S, outputs, saved, tiles,
-                                                       sh.vcap, sh.coop); break;
-    case 2: k_forward_sp<2><<<grid, block, smem, st>>>(w, inputs, stride, S, outputs, saved, tiles,
-                                                       sh.vcap, sh.coop); break;
-    case 4: k_forward_sp<4><<<grid, block, smem, st>>>(w, inputs, stride, S, outputs, saved, tiles,
-                                                       sh.vcap, sh.coop); break;
+  // outputs only on a plan with compiled programs: the compiled walk
+  const bool comp = saved == nullptr && w.cnode != nullptr;
+#define NEAT_SP(L, C)                                                                     \
+  k_forward_sp<L, C><<<grid, block, smem, st>>>(w, inputs, stride, S, outputs, saved, tiles, \
+                                                sh.vcap, sh.coop)
+  switch (sh.spl * 2 + (comp ? 1 : 0)) {
+    case 2: NEAT_SP(1, false); break;
+    case 3: NEAT_SP(1, true); break;
+    case 4: NEAT_SP(2, false); break;
+    case 5: NEAT_SP(2, true); break;
+    case 8: NEAT_SP(4, false); break;
+    case 9: NEAT_SP(4, true); break;
     default: return cudaErrorInvalidValue;
   }
+#undef NEAT_SP
   return cudaGetLastError();
 }
 
@@ -961,9 +1087,12 @@ cudaError_t launch_hyperneat(const Ws &w, int G, float thresh, float *weights, i
 
 namespace neat {
 cudaError_t forward_set_smem_limit(int bytes) {
-  cudaError_t e = set_dyn_smem_limit(k_forward_sp<1>, bytes);
-  if (e == cudaSuccess) e = set_dyn_smem_limit(k_forward_sp<2>, bytes);
-  if (e == cudaSuccess) e = set_dyn_smem_limit(k_forward_sp<4>, bytes);
+  cudaError_t e = set_dyn_smem_limit(k_forward_sp<1, false>, bytes);
+  if (e == cudaSuccess) e = set_dyn_smem_limit(k_forward_sp<2, false>, bytes);
+  if (e == cudaSuccess) e = set_dyn_smem_limit(k_forward_sp<4, false>, bytes);
+  if (e == cudaSuccess) e = set_dyn_smem_limit(k_forward_sp<1, true>, bytes);
+  if (e == cudaSuccess) e = set_dyn_smem_limit(k_forward_sp<2, true>, bytes);
+  if (e == cudaSuccess) e = set_dyn_smem_limit(k_forward_sp<4, true>, bytes);
   if (e == cudaSuccess) e = set_dyn_smem_limit(k_forward_plain, bytes);
   if (e == cudaSuccess) e = set_dyn_smem_limit(k_hyperneat<1>, bytes);
   if (e == cudaSuccess) e = set_dyn_smem_limit(k_hyperneat<2>, bytes);
@@ -973,9 +1102,9 @@ cudaError_t forward_set_smem_limit(int bytes) {
 int forward_sp_occupancy(int warps, size_t smem, int spl) {
   int n = 0;
   cudaError_t e = cudaErrorInvalidValue;
-  if (spl == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_forward_sp<1>, warps * 32, smem);
-  if (spl == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_forward_sp<2>, warps * 32, smem);
-  if (spl == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_forward_sp<4>, warps * 32, smem);
+  if (spl == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_forward_sp<1, false>, warps * 32, smem);
+  if (spl == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_forward_sp<2, false>, warps * 32, smem);
+  if (spl == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_forward_sp<4, false>, warps * 32, smem);
   return e == cudaSuccess ? n : 0;
 }
 int hyperneat_occupancy(int spl, int warps, size_t smem) {

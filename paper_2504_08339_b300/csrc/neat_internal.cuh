@@ -52,8 +52,33 @@ struct __align__(16) GenomeHdr {
   int nch;       // 4-edge chunks of the level-synchronous form over those nodes:
                  // sum of ceil(indeg/4)
   int elive;     // enabled connections into those nodes
-  int pad[3];
+  int crows;     // value rows of the compiled program (0: none)
+  int pad[2];
 };
+
+// -- compiled program (outputs-only walks) -----------------------------------------
+// Built by the feed-forward transform for every valid genome: the nodes some
+// output depends on, in canonical order, with their incoming edges in pairs,
+// and a VALUE ROW per value instead of a position: rows 0..I-1 hold the
+// inputs, rows I and I+1 the constants 0 and 1, and the node values take rows
+// from I+2 on, a row being reused once the last node that reads it has read
+// it (a linear scan in canonical order; a node reads all its inputs before it
+// writes, so it may take a row it releases).  The outputs keep their rows.
+// Each node's edge list is padded to an even length with an edge that leaves
+// the aggregate unchanged: weight 0 on the zero row for sum and mean, weight 1
+// on the one row for product, a repeat of the last edge for max.
+//   CNode.pairs = first pair (within the genome) | pair count << CN_PAIR_BITS
+//   CNode.meta  = value row | activation << 20 | aggregation << 23 |
+//                 (in-degree odd) << 25
+//   pair (uint4) = (source row 0, w0, source row 1, w1)
+struct __align__(16) CNode {
+  float bias, resp;
+  uint32_t pairs;
+  uint32_t meta;
+};
+constexpr uint32_t CN_PAIR_BITS = 17, CN_ROW_BITS = 20;
+// pair capacity per genome: sum over nodes of ceil(in-degree / 2) <= (C + N) / 2
+__host__ __device__ inline int cpair_cap(int N, int C) { return (C + N) / 2 + 1; }
 
 // -- level-synchronous batches (small-S form) --------------------------------------
 // Consecutive genomes of a layer-sorted queue are packed into batches.  A batch
@@ -158,6 +183,7 @@ struct Layout {
   size_t lvl_arena_bytes;
   int lvl_max_batches;
   size_t core;                       // bytes of everything above
+  size_t cnode, cpair, cout;            // compiled program (after core)
   size_t sp_scratch, sp_scratch_bytes;  // per-warp node value slots
   size_t total;
 };
@@ -200,6 +226,9 @@ inline Layout make_layout(int P, int N, int C, int I, int O) {
   L.lvl_arena_bytes = p * size_t(lvl_pb_max(N, C, I, O)) + 256;
   L.lvl_arena = take(L.lvl_arena_bytes);
   L.core = off;
+  L.cnode = take(sizeof(CNode) * p * N);
+  L.cpair = take(sizeof(uint4) * p * size_t(cpair_cap(N, C)));
+  L.cout = take(sizeof(int32_t) * p * O);
   L.sp_scratch_bytes = sp_scratch_bytes(N);
   L.sp_scratch = take(L.sp_scratch_bytes);
   L.total = off;
@@ -225,6 +254,9 @@ struct Ws {
   int32_t *lvl_first;
   BatchLoc *lvl_loc;
   unsigned char *lvl_arena;
+  CNode *cnode;       // compiled program [P][N], pairs [P][cpair_cap], output
+  uint4 *cpair;       // rows [P][O] (nullptr: none)
+  int32_t *cout;
   float *sp_scratch;  // per-warp node value slots (nullptr: none)
   size_t sp_scratch_floats;
   int lvl_budget, lvl_max_batches;
@@ -251,6 +283,9 @@ inline Ws make_ws(void *base, const Layout &L, int P, int N, int C, int I, int O
   w.lvl_first = reinterpret_cast<int32_t *>(b + L.lvl_first);
   w.lvl_loc = reinterpret_cast<BatchLoc *>(b + L.lvl_loc);
   w.lvl_arena = reinterpret_cast<unsigned char *>(b + L.lvl_arena);
+  w.cnode = reinterpret_cast<CNode *>(b + L.cnode);
+  w.cpair = reinterpret_cast<uint4 *>(b + L.cpair);
+  w.cout = reinterpret_cast<int32_t *>(b + L.cout);
   w.sp_scratch = L.sp_scratch_bytes ? reinterpret_cast<float *>(b + L.sp_scratch) : nullptr;
   w.sp_scratch_floats = L.sp_scratch_bytes / sizeof(float);
   w.lvl_budget = lvl_budget(N, C, I, O);
@@ -359,8 +394,8 @@ cudaError_t launch_forward_sp(const Ws &w, const float *inputs, int64_t stride, 
                               float *outputs, float *saved, const SpShape &sh, cudaStream_t st);
 size_t forward_sp_smem(int vcap, int warps, int spl);
 // warp slots of the workspace value array for `spl` samples per lane
-inline int sp_scratch_slots(const Ws &w, int spl) {
-  return w.sp_scratch ? int(w.sp_scratch_floats / (size_t(w.N) * 32 * spl)) : 0;
+inline int sp_scratch_slots(const Ws &w, int spl) {  // slots of N + 2 rows
+  return w.sp_scratch ? int(w.sp_scratch_floats / (size_t(w.N + 2) * 32 * spl)) : 0;
 }
 cudaError_t launch_forward_plain(const Ws &w, const float *inputs, int64_t stride, int S,
                                  float *outputs, cudaStream_t st);

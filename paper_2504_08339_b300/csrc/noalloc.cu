@@ -96,6 +96,9 @@ extern "C" neat_status neat_forward_noalloc(const float *nodes, const float *con
   unsigned char *base = g_scratch_ptr[dev];
   const neat::Layout L = neat::make_layout(P, N, C, I, O);
   neat::Ws w = neat::make_ws(base, L, P, N, C, I, O);
+  w.cnode = nullptr;  // only the core part of the layout lives in the array
+  w.cpair = nullptr;
+  w.cout = nullptr;
   w.sp_scratch = nullptr;
   w.sp_scratch_floats = 0;
   int32_t *order = reinterpret_cast<int32_t *>(base + align256(L.core));

@@ -85,7 +85,7 @@ __host__ __device__ inline int pow2_ceil(int x) {
 struct TSmem {
   // byte offsets into dynamic shared memory
   int sk, ek, key_s, row_of_s, s_of_row, indeg, rem, inbeg, outbeg, outfill, order_s, layer_s,
-      pos_of, tmp, ready, outlist, total;
+      pos_of, tmp, ready, outlist, cst, total;
 };
 
 __host__ __device__ inline TSmem tsmem_layout(int N, int C) {
@@ -109,6 +109,7 @@ __host__ __device__ inline TSmem tsmem_layout(int N, int C) {
   L.tmp = take(4 * (N + 1));
   L.ready = take(4 * N);
   L.outlist = take(4 * C);
+  L.cst = take(4 * N);
   L.total = off;
   return L;
 }
@@ -123,7 +124,7 @@ __global__ void __launch_bounds__(256) k_transform(Ws w, const float *__restrict
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ int wbuf[33];
   __shared__ unsigned s_status;
-  __shared__ int s_V, s_E, s_nch, s_nlive, s_elive;
+  __shared__ int s_V, s_E, s_nch, s_nlive, s_elive, s_crows;
 
   const int N = w.N, C = w.C, I = w.I, O = w.O;
   const int g = blockIdx.x, tid = threadIdx.x, T = blockDim.x;
@@ -339,7 +340,7 @@ __global__ void __launch_bounds__(256) k_transform(Ws w, const float *__restrict
   // 7. padded program (valid genomes only)
   GenomeHdr h;
   h.V = 0; h.E = 0; h.L = 0; h.status = status; h.node_off = 0; h.edge_off = 0;
-  h.nlive = 0; h.nch = 0; h.elive = 0; h.pad[0] = h.pad[1] = h.pad[2] = 0;
+  h.nlive = 0; h.nch = 0; h.elive = 0; h.crows = 0; h.pad[0] = h.pad[1] = 0;
   if (status == 0u) {
     h.V = V; h.E = E; h.L = t;
     // nodes some output depends on: the outputs, then frontier by frontier
@@ -430,6 +431,98 @@ __global__ void __launch_bounds__(256) k_transform(Ws w, const float *__restrict
     }
     int32_t *io = w.pio + size_t(g) * (I + O);
     for (int i = tid; i < I + O; i += T) io[i] = pos_of[s_of_row[i]];
+
+    // 8. compiled program (feed-forward only): value rows by a linear scan
+    if (!recurrent && w.cnode != nullptr) {
+      int *cidx = tmp;       // compact index of each kept position (free again)
+      int *pbeg = outbeg;    // first pair of each kept position
+      int *clast = rem;      // last reader (compact index) of each value
+      int *crow = outfill;   // value row of each sorted node
+      int *cst = reinterpret_cast<int *>(sm + L.cst);  // released rows
+      __syncthreads();  // tmp and outbeg are free once step 7 is done with them
+      for (int p = tid; p < V; p += T) {
+        const int s = order_s[p];
+        const bool keep = live[s] && row_of_s[s] >= I;
+        cidx[p] = keep ? 1 : 0;
+        pbeg[p] = keep ? (indeg[s] + 1) >> 1 : 0;
+      }
+      for (int s = tid; s < V; s += T) {
+        clast[s] = -1;
+        crow[s] = -1;
+      }
+      __syncthreads();
+      block_exclusive_scan(cidx, V, wbuf);
+      block_exclusive_scan(pbeg, V, wbuf);
+      // the outputs keep their rows; every other value is released at its
+      // last reader
+      for (int i = tid; i < O; i += T) clast[s_of_row[I + i]] = 0x7fffffff;
+      __syncthreads();
+      for (int p = tid; p < V; p += T) {
+        const int s = order_s[p];
+        if (!live[s] || row_of_s[s] < I) continue;
+        for (int k = inbeg[s]; k < inbeg[s] + indeg[s]; ++k)
+          atomicMax(&clast[int((ek[k] >> 20) & 0xfffffu)], cidx[p]);
+      }
+      __syncthreads();
+      if (tid == 0) {
+        for (int i = 0; i < I; ++i) crow[s_of_row[i]] = i;
+        int sp = 0, next = I + 2;
+        for (int p = 0; p < V; ++p) {
+          const int s = order_s[p];
+          if (!live[s] || row_of_s[s] < I) continue;
+          const int c = cidx[p];
+          for (int k = inbeg[s]; k < inbeg[s] + indeg[s]; ++k) {
+            const int src = int((ek[k] >> 20) & 0xfffffu);
+            if (clast[src] == c && row_of_s[src] >= I) {
+              cst[sp++] = crow[src];
+              clast[src] = -2;  // released once, whatever the duplicates
+            }
+          }
+          crow[s] = sp > 0 ? cst[--sp] : next++;
+        }
+        s_crows = next;
+      }
+      __syncthreads();
+      h.crows = s_crows;
+      CNode *cn = w.cnode + size_t(g) * N;
+      uint4 *cp = w.cpair + size_t(g) * cpair_cap(N, C);
+      for (int p = tid; p < V; p += T) {
+        const int s = order_s[p];
+        if (!live[s] || row_of_s[s] < I) continue;
+        const float *nr = gn + row_of_s[s] * 5;
+        const int cnt = indeg[s], act = int(nr[3]), agg = int(nr[4]), np = (cnt + 1) >> 1;
+        const int pb = pbeg[p];
+        CNode r;
+        r.bias = nr[1];
+        r.resp = nr[2];
+        r.pairs = uint32_t(pb) | (uint32_t(np) << CN_PAIR_BITS);
+        r.meta = uint32_t(crow[s]) | (uint32_t(act) << CN_ROW_BITS) |
+                 (uint32_t(agg) << (CN_ROW_BITS + 3)) | (uint32_t(cnt & 1) << (CN_ROW_BITS + 5));
+        cn[cidx[p]] = r;
+        for (int q = 0; q < np; ++q) {
+          const uint64_t x0 = ek[inbeg[s] + 2 * q];
+          uint4 e;
+          e.x = uint32_t(crow[int((x0 >> 20) & 0xfffffu)]);
+          e.y = __float_as_uint(gc[int(x0 & 0xfffffu) * 4 + 2]);
+          if (2 * q + 1 < cnt) {
+            const uint64_t x1 = ek[inbeg[s] + 2 * q + 1];
+            e.z = uint32_t(crow[int((x1 >> 20) & 0xfffffu)]);
+            e.w = __float_as_uint(gc[int(x1 & 0xfffffu) * 4 + 2]);
+          } else if (agg == NEAT_AGG_MAX) {
+            e.z = e.x;
+            e.w = e.y;
+          } else if (agg == NEAT_AGG_PRODUCT) {
+            e.z = uint32_t(I + 1);
+            e.w = __float_as_uint(1.0f);
+          } else {
+            e.z = uint32_t(I);
+            e.w = 0u;
+          }
+          cp[pb + q] = e;
+        }
+      }
+      for (int i = tid; i < O; i += T) w.cout[size_t(g) * O + i] = crow[s_of_row[I + i]];
+    }
   }
   if (tid == 0) w.hdr[g] = h;
 }
