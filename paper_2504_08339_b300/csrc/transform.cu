@@ -528,12 +528,13 @@ __global__ void __launch_bounds__(256) k_transform(Ws w, const float *__restrict
 }
 
 // Work-queue order: genomes by descending cost (ties: lower id first).
-// mode 0: cost = the live part's E + 2V (sample-parallel forward); mode 1:
-// layers first, then E.
+// mode 0: cost = E + 2V of the whole genome (sample-parallel forms and the
+// backward; measured better than the live part's cost for the compiled walk
+// too); mode 1: layers first, then E.
 __device__ __forceinline__ uint64_t cost_key(const GenomeHdr &h, int mode, int g) {
   uint32_t cost;
   if (h.status != 0u) cost = 0u;
-  else if (mode == 0) cost = uint32_t(sp_cost(h) + 1);
+  else if (mode == 0) cost = uint32_t(h.E + 2 * h.V + 1);
   else cost = (uint32_t(h.L) << 16) | uint32_t(min(h.E, 0xffff));
   return (uint64_t(cost) << 32) | uint64_t(0xffffffffu - uint32_t(g));
 }
