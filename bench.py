@@ -496,11 +496,18 @@ def bench_ours(args, rank, world, local, pg):
         # backward: program again, grads out, saved aggregates in, dL/dO in,
         # dL/dx out, the shared inputs in; on chip 12 S E + 8 S V
         # (recompute: no saved aggregates; the forward's on-chip traffic again)
+        # The backward visits only the nodes some output depends on (the others
+        # have a zero adjoint): its program, saved-aggregate and on-chip terms
+        # count that part; the gradients of every row are written.
         rec = saved is None
-        alg_bytes = float((8 * E + 12 * Vn).sum() + (4 * E + 8 * Vn).sum() +
-                          (0 if rec else 4 * S * Vn.sum()) +
+        E_live, V_live = live_counts(nodes, conns, spec.I, spec.O)
+        extra["live_subgraph"] = live_note(E, E_live, V_live)
+        Vl = V_live + spec.I
+        alg_bytes = float((8 * E_live + 12 * Vl).sum() + (4 * E + 8 * Vn).sum() +
+                          (0 if rec else 4 * S * V_live.sum()) +
                           4 * S * spec.O * P + 4 * S * spec.I * P + 4 * S * spec.I)
-        chip_bytes = float((12 * S * E + 8 * S * Vn).sum() + (4 * S * (E + Vn).sum() if rec else 0))
+        chip_bytes = float((12 * S * E_live + 8 * S * Vl).sum() +
+                           (4 * S * (E_live + V_live).sum() if rec else 0))
         fwd_hbm = float((8 * E + 12 * Vn).sum() + 4 * S * spec.I + 4 * S * spec.O * P +
                         (0 if rec else 4 * S * Vn.sum()))
         fwd_chip = float(4 * S * (E + Vn).sum())

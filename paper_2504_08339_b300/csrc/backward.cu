@@ -16,6 +16,9 @@
 // frontiers, so never before those sources are visited) and sum dL/dw with
 // warp butterflies.  Pulling keeps the walk free of read-modify-write chains.
 //
+// Nodes no output depends on (META_DEAD) have a zero adjoint: they are not
+// visited, and their parameters' gradients stay 0.
+//
 // The cross-sample sums of a tile then run lane-parallel: lane per node for
 // dL/db = sum_s u and dL/dr = sum_s u a, lane per sum/mean edge for
 // dL/dw_e = c_e sum_s u_dst v_src, each into a lane-owned per-warp
@@ -173,11 +176,13 @@ __global__ void k_backward(Ws w, const float *__restrict__ inputs, int64_t strid
     const NodeRec n = w.knode[h.node_off + p];
     if (n.meta & META_INPUT) continue;
     const int cnt = meta_cnt(n.meta), agg = meta_agg(n.meta);
-    const bool lin = agg == NEAT_AGG_SUM || agg == NEAT_AGG_MEAN;
+    // a node no output depends on has a zero adjoint: its edges carry nothing
+    const bool dead = (n.meta & META_DEAD) != 0;
+    const bool lin = !dead && (agg == NEAT_AGG_SUM || agg == NEAT_AGG_MEAN);
     const float c = agg == NEAT_AGG_MEAN ? n.resp / float(cnt) : n.resp;
     for (int k = 0; k < cnt; ++k) {
       edst[n.in_begin + k] = lin ? p : -1;
-      ecoef[n.in_begin + k] = c;
+      ecoef[n.in_begin + k] = dead ? 0.0f : c;
     }
   }
   __syncthreads();
@@ -209,7 +214,8 @@ __global__ void k_backward(Ws w, const float *__restrict__ inputs, int64_t strid
       // into shared memory
       const float *col = saved + size_t(g) * N * S + s;
       if (active) {
-        for (int p = 0; p < V; ++p) cp_async4(av + p * RS, col + size_t(p) * S);
+        for (int p = 0; p < V; ++p)
+          if (!(nr[p].meta & META_DEAD)) cp_async4(av + p * RS, col + size_t(p) * S);
       } else {
         for (int p = 0; p < V; ++p) av[p * RS] = 0.0f;
       }
@@ -234,12 +240,12 @@ __global__ void k_backward(Ws w, const float *__restrict__ inputs, int64_t strid
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-          if (p + q < V && !(n[q].meta & META_INPUT)) v[(p + q) * RS] = z[q];
+          if (p + q < V && !(n[q].meta & (META_INPUT | META_DEAD))) v[(p + q) * RS] = z[q];
       }
     } else {
       for (int p = 0; p < V; ++p) {
         const NodeRec n = nr[p];
-        if (n.meta & META_INPUT) continue;
+        if (n.meta & (META_INPUT | META_DEAD)) continue;
         const int cnt = meta_cnt(n.meta), agg = meta_agg(n.meta);
         const EdgeRec *e = er + n.in_begin;
         float a;
@@ -274,6 +280,7 @@ __global__ void k_backward(Ws w, const float *__restrict__ inputs, int64_t strid
       dv[io[I + o] * RS] += active ? __ldg(gout + (size_t(g) * S + s) * O + o) : 0.0f;
     for (int p = V - 1; p >= 0; --p) {
       const NodeRec n = nr[p];
+      if (n.meta & META_DEAD) continue;  // zero adjoint, nothing to pass on
       // pulled part: sum over this position's sum/mean consumers
       const int b = pbeg[p], en = pend[p];
       float d0 = dv[p * RS], d1 = 0.0f;
@@ -357,7 +364,7 @@ __global__ void k_backward(Ws w, const float *__restrict__ inputs, int64_t strid
     // edges (inactive samples have u = 0 and add nothing)
     const float *vw = v - lane, *aww = av - lane, *dw = dv - lane;  // warp arrays
     for (int p = lane; p < V; p += 32) {
-      if (nr[p].meta & META_INPUT) continue;
+      if (nr[p].meta & (META_INPUT | META_DEAD)) continue;
       const float *up = dw + p * RS, *ap = aww + p * RS;
       float sb0 = 0.0f, sb1 = 0.0f, sr0 = 0.0f, sr1 = 0.0f;
 #pragma unroll 8
