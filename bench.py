@@ -49,14 +49,14 @@ PEAKS_FALLBACK = {"hbm_gbs": 6400.0, "source": "fallback"}
 # on).  A capture on a smaller population is scaled by population (the
 # traffic grows with the genomes processed); the figure is reported only
 # while those sources are unchanged.
-_INTERNAL = ("paper_2504_08339_b300/csrc/neat_internal.cuh", "cae31d2d0b3f29d1")
+_INTERNAL = ("paper_2504_08339_b300/csrc/neat_internal.cuh", "f19c17ac26b67c1a")
 TRAFFIC = {
-    ("locomotion", "k_forward_lvl"): (32599296, 10000, dict([
-        ("paper_2504_08339_b300/csrc/level.cu", "d3c4990b7be89b2e"), _INTERNAL])),
-    ("uneven", "k_forward_sp"): (116634112, 2048, dict([
-        ("paper_2504_08339_b300/csrc/forward.cu", "7cdea6ff82e6aa42"), _INTERNAL])),
-    ("differentiation", "k_backward"): (359581440, 512, dict([
-        ("paper_2504_08339_b300/csrc/backward.cu", "8524e28e5af10c82"), _INTERNAL])),
+    ("locomotion", "k_forward_lvl"): (5360384, 2000, dict([
+        ("paper_2504_08339_b300/csrc/level.cu", "baa052d1a865fb8f"), _INTERNAL])),
+    ("uneven", "k_forward_sp"): (19611648, 2048, dict([
+        ("paper_2504_08339_b300/csrc/forward.cu", "91a3f6ceb766ac2b"), _INTERNAL])),
+    ("differentiation", "k_backward"): (244054528, 512, dict([
+        ("paper_2504_08339_b300/csrc/backward.cu", "2dfc15dfe5646f08"), _INTERNAL])),
 }
 
 
