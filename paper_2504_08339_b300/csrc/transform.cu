@@ -464,20 +464,41 @@ __global__ void __launch_bounds__(256) k_transform(Ws w, const float *__restrict
           atomicMax(&clast[int((ek[k] >> 20) & 0xfffffu)], cidx[p]);
       }
       __syncthreads();
+      // the values each kept position releases (its sources whose last
+      // reader it is; a source feeds a node at most once), gathered in
+      // parallel so that the scan itself only moves rows
+      int *roff = pos_of;  // free after step 7
+      int *rlist = key_s;  // free after step 2
+      for (int p = tid; p < V; p += T) {
+        const int s = order_s[p];
+        int n = 0;
+        if (live[s] && row_of_s[s] >= I)
+          for (int k = inbeg[s]; k < inbeg[s] + indeg[s]; ++k) {
+            const int src = int((ek[k] >> 20) & 0xfffffu);
+            n += (clast[src] == cidx[p] && row_of_s[src] >= I) ? 1 : 0;
+          }
+        roff[p] = n;
+      }
+      __syncthreads();
+      const int nrel = block_exclusive_scan(roff, V, wbuf);
+      for (int p = tid; p < V; p += T) {
+        const int s = order_s[p];
+        if (!live[s] || row_of_s[s] < I) continue;
+        int j = roff[p];
+        for (int k = inbeg[s]; k < inbeg[s] + indeg[s]; ++k) {
+          const int src = int((ek[k] >> 20) & 0xfffffu);
+          if (clast[src] == cidx[p] && row_of_s[src] >= I) rlist[j++] = src;
+        }
+      }
+      __syncthreads();
       if (tid == 0) {
         for (int i = 0; i < I; ++i) crow[s_of_row[i]] = i;
         int sp = 0, next = I + 2;
         for (int p = 0; p < V; ++p) {
           const int s = order_s[p];
           if (!live[s] || row_of_s[s] < I) continue;
-          const int c = cidx[p];
-          for (int k = inbeg[s]; k < inbeg[s] + indeg[s]; ++k) {
-            const int src = int((ek[k] >> 20) & 0xfffffu);
-            if (clast[src] == c && row_of_s[src] >= I) {
-              cst[sp++] = crow[src];
-              clast[src] = -2;  // released once, whatever the duplicates
-            }
-          }
+          const int j1 = p + 1 < V ? roff[p + 1] : nrel;
+          for (int j = roff[p]; j < j1; ++j) cst[sp++] = crow[rlist[j]];
           crow[s] = sp > 0 ? cst[--sp] : next++;
         }
         s_crows = next;
