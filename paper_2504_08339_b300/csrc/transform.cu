@@ -85,7 +85,7 @@ __host__ __device__ inline int pow2_ceil(int x) {
 struct TSmem {
   // byte offsets into dynamic shared memory
   int sk, ek, key_s, row_of_s, s_of_row, indeg, rem, inbeg, outbeg, outfill, order_s, layer_s,
-      pos_of, tmp, ready, outlist, cst, total;
+      pos_of, tmp, ready, outlist, total;
 };
 
 __host__ __device__ inline TSmem tsmem_layout(int N, int C) {
@@ -109,7 +109,6 @@ __host__ __device__ inline TSmem tsmem_layout(int N, int C) {
   L.tmp = take(4 * (N + 1));
   L.ready = take(4 * N);
   L.outlist = take(4 * C);
-  L.cst = take(4 * N);
   L.total = off;
   return L;
 }
@@ -145,7 +144,6 @@ __global__ void __launch_bounds__(256) k_transform(Ws w, const float *__restrict
   int *tmp = reinterpret_cast<int *>(sm + L.tmp);
   int *ready = reinterpret_cast<int *>(sm + L.ready);
   int *outlist = reinterpret_cast<int *>(sm + L.outlist);
-  const int N2 = pow2_ceil(N), C2 = pow2_ceil(C);
 
   const float *gn = nodes + size_t(g) * N * 5;
   const float *gc = conns + size_t(g) * C * 4;
@@ -153,16 +151,15 @@ __global__ void __launch_bounds__(256) k_transform(Ws w, const float *__restrict
   if (tid == 0) { s_status = 0u; s_V = 0; s_E = 0; s_nch = 0; s_nlive = 0; s_elive = 0; }
   __syncthreads();
 
-  // 1. node rows: validity, attribute checks, (key,row) sort keys
+  // 1. node rows: validity, attribute checks, (key,row) sort keys of the
+  // valid rows, gathered at the front (the sort then covers pow2(V) entries)
   unsigned st = 0u;
-  int nvalid = 0;
-  for (int i = tid; i < N2; i += T) {
+  for (int i = tid; i < N; i += T) {
     uint64_t key = ~0ull;
-    if (i < N) {
+    {
       const float k = gn[i * 5 + 0];
       s_of_row[i] = -1;
       if (k == k) {
-        ++nvalid;
         uint32_t ku = 0xffffffffu;
         if (is_int_in(k, 0.0f, KEY_LIMIT)) ku = uint32_t(k); else st |= NEAT_G_BAD_ATTR;
         if (i >= I) {
@@ -175,13 +172,17 @@ __global__ void __launch_bounds__(256) k_transform(Ws w, const float *__restrict
         st |= NEAT_G_IO_ROW_INVALID;
       }
     }
-    sk[i] = key;
+    if (key != ~0ull) sk[atomicAdd(&s_V, 1)] = key;
   }
   if (st) atomicOr(&s_status, st);
-  if (nvalid) atomicAdd(&s_V, nvalid);
   __syncthreads();
   const int V = s_V;
-  bitonic_sort_u64(sk, N2);
+  {
+    const int v2 = pow2_ceil(max(V, 1));
+    for (int i = V + tid; i < v2; i += T) sk[i] = ~0ull;
+    __syncthreads();
+    bitonic_sort_u64(sk, v2);
+  }
 
   // 2. sorted key table, duplicate keys
   st = 0u;
@@ -200,12 +201,12 @@ __global__ void __launch_bounds__(256) k_transform(Ws w, const float *__restrict
   if (st) atomicOr(&s_status, st);
   __syncthreads();
 
-  // 3. connection rows: enabled ones resolved to sorted node indices
+  // 3. connection rows: enabled ones resolved to sorted node indices,
+  // gathered at the front (the sort then covers pow2(E) entries)
   st = 0u;
-  int nen = 0;
-  for (int j = tid; j < C2; j += T) {
+  for (int j = tid; j < C; j += T) {
     uint64_t key = ~0ull;
-    if (j < C) {
+    {
       const float4 c = reinterpret_cast<const float4 *>(gc)[j];
       const bool valid = (c.x == c.x) && (c.y == c.y);
       const bool enabled = valid && (c.w == c.w) && c.w != 0.0f;
@@ -233,17 +234,20 @@ __global__ void __launch_bounds__(256) k_transform(Ws w, const float *__restrict
           if (row_of_s[dst] < I) st |= NEAT_G_EDGE_INTO_INPUT;
           if (c.z != c.z) st |= NEAT_G_BAD_ATTR;
           key = (uint64_t(dst) << 40) | (uint64_t(src) << 20) | uint64_t(j);
-          ++nen;
         }
       }
     }
-    ek[j] = key;
+    if (key != ~0ull) ek[atomicAdd(&s_E, 1)] = key;
   }
   if (st) atomicOr(&s_status, st);
-  if (nen) atomicAdd(&s_E, nen);
   __syncthreads();
   const int E = s_E;
-  bitonic_sort_u64(ek, C2);
+  {
+    const int e2 = pow2_ceil(max(E, 1));
+    for (int i = E + tid; i < e2; i += T) ek[i] = ~0ull;
+    __syncthreads();
+    bitonic_sort_u64(ek, e2);
+  }
 
   // 4. in-degrees, incoming segments, duplicate edges, out-degree counts
   st = 0u;
@@ -438,7 +442,7 @@ __global__ void __launch_bounds__(256) k_transform(Ws w, const float *__restrict
       int *pbeg = outbeg;    // first pair of each kept position
       int *clast = rem;      // last reader (compact index) of each value
       int *crow = outfill;   // value row of each sorted node
-      int *cst = reinterpret_cast<int *>(sm + L.cst);  // released rows
+      int *cst = reinterpret_cast<int *>(sm + L.sk);  // released rows (sk is free)
       __syncthreads();  // tmp and outbeg are free once step 7 is done with them
       for (int p = tid; p < V; p += T) {
         const int s = order_s[p];
