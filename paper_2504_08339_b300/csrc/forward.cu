@@ -250,79 +250,98 @@ __device__ __forceinline__ void hn_fma(float w, const float (&x)[SPL], float (&a
 // sample: one value and one FMA.  Sum and mean keep even edges in a0 and odd
 // edges in a1, the rounding order of the position walk.
 template <int SPL, bool GLOBAL>
-__device__ __forceinline__ void cwalk(const CNode *__restrict__ nodes, int nn,
-                                      const uint4 *__restrict__ pairs, char *vb) {
+__device__ __forceinline__ uint4 ld_rec(const uint4 *p) {
+  if constexpr (GLOBAL) return __ldg(p);
+  return *p;
+}
+
+// One compiled node (its 16-byte record nraw) for this lane's SPL samples.
+template <int SPL, bool GLOBAL>
+__device__ __forceinline__ void cnode_eval(const uint4 nraw, const uint4 *__restrict__ pairs,
+                                           char *vb) {
   constexpr int SH = 7 + (SPL == 4 ? 2 : (SPL == 2 ? 1 : 0));
-  auto ldp = [](const uint4 *p) { return GLOBAL ? __ldg(p) : *p; };
-  for (int c = 0; c < nn; ++c) {
-    const uint4 nraw = ldp(reinterpret_cast<const uint4 *>(nodes + c));
-    const float bias = __uint_as_float(nraw.x), resp = __uint_as_float(nraw.y);
-    const uint32_t meta = nraw.w;
-    const int np = int(nraw.z >> CN_PAIR_BITS);
-    const uint4 *pp = pairs + (nraw.z & ((1u << CN_PAIR_BITS) - 1u));
-    const int agg = int(meta >> (CN_ROW_BITS + 3)) & 3;
-    float a[SPL];
-    if (agg == NEAT_AGG_SUM || agg == NEAT_AGG_MEAN) {
-      float a0[SPL], a1[SPL];
+  const float bias = __uint_as_float(nraw.x), resp = __uint_as_float(nraw.y);
+  const uint32_t meta = nraw.w;
+  const int np = int(nraw.z >> CN_PAIR_BITS);
+  const uint4 *pp = pairs + (nraw.z & ((1u << CN_PAIR_BITS) - 1u));
+  const int agg = int(meta >> (CN_ROW_BITS + 3)) & 3;
+  float a[SPL];
+  if (agg == NEAT_AGG_SUM || agg == NEAT_AGG_MEAN) {
+    float a0[SPL], a1[SPL];
 #pragma unroll
-      for (int j = 0; j < SPL; ++j) a0[j] = a1[j] = 0.0f;
+    for (int j = 0; j < SPL; ++j) a0[j] = a1[j] = 0.0f;
 #pragma unroll 2
-      for (int k = 0; k < np; ++k) {
-        const uint4 e = ldp(pp + k);
-        float x0[SPL], x1[SPL];
-        HnVec<SPL>::ld(vb + (e.x << SH), x0);
-        HnVec<SPL>::ld(vb + (e.z << SH), x1);
-        hn_fma<SPL>(__uint_as_float(e.y), x0, a0);
-        hn_fma<SPL>(__uint_as_float(e.w), x1, a1);
-      }
-#pragma unroll
-      for (int j = 0; j < SPL; ++j) a[j] = a0[j] + a1[j];
-      if (agg == NEAT_AGG_MEAN && np > 0) {
-        const float cnt = float(2 * np - int((meta >> (CN_ROW_BITS + 5)) & 1u));
-#pragma unroll
-        for (int j = 0; j < SPL; ++j) a[j] = a[j] / cnt;
-      }
-    } else if (np == 0) {
-#pragma unroll
-      for (int j = 0; j < SPL; ++j) a[j] = 0.0f;
-    } else if (agg == NEAT_AGG_MAX) {
-      const uint4 e = ldp(pp);
+    for (int k = 0; k < np; ++k) {
+      const uint4 e = ld_rec<SPL, GLOBAL>(pp + k);
       float x0[SPL], x1[SPL];
       HnVec<SPL>::ld(vb + (e.x << SH), x0);
       HnVec<SPL>::ld(vb + (e.z << SH), x1);
-#pragma unroll
-      for (int j = 0; j < SPL; ++j)
-        a[j] = fmaxf(__uint_as_float(e.y) * x0[j], __uint_as_float(e.w) * x1[j]);
-      for (int k = 1; k < np; ++k) {
-        const uint4 f = ldp(pp + k);
-        HnVec<SPL>::ld(vb + (f.x << SH), x0);
-        HnVec<SPL>::ld(vb + (f.z << SH), x1);
-#pragma unroll
-        for (int j = 0; j < SPL; ++j) {
-          a[j] = fmaxf(a[j], __uint_as_float(f.y) * x0[j]);
-          a[j] = fmaxf(a[j], __uint_as_float(f.w) * x1[j]);
-        }
-      }
-    } else {  // product
-#pragma unroll
-      for (int j = 0; j < SPL; ++j) a[j] = 1.0f;
-      for (int k = 0; k < np; ++k) {
-        const uint4 f = ldp(pp + k);
-        float x0[SPL], x1[SPL];
-        HnVec<SPL>::ld(vb + (f.x << SH), x0);
-        HnVec<SPL>::ld(vb + (f.z << SH), x1);
-#pragma unroll
-        for (int j = 0; j < SPL; ++j) {
-          a[j] = a[j] * (__uint_as_float(f.y) * x0[j]);
-          a[j] = a[j] * (__uint_as_float(f.w) * x1[j]);
-        }
-      }
+      hn_fma<SPL>(__uint_as_float(e.y), x0, a0);
+      hn_fma<SPL>(__uint_as_float(e.w), x1, a1);
     }
 #pragma unroll
-    for (int j = 0; j < SPL; ++j) a[j] = fmaf(resp, a[j], bias);
-    act_apply_n<SPL>(int(meta >> CN_ROW_BITS) & 7, a);
-    HnVec<SPL>::st(vb + ((meta & ((1u << CN_ROW_BITS) - 1u)) << SH), a);
+    for (int j = 0; j < SPL; ++j) a[j] = a0[j] + a1[j];
+    if (agg == NEAT_AGG_MEAN && np > 0) {
+      const float cnt = float(2 * np - int((meta >> (CN_ROW_BITS + 5)) & 1u));
+#pragma unroll
+      for (int j = 0; j < SPL; ++j) a[j] = a[j] / cnt;
+    }
+  } else if (np == 0) {
+#pragma unroll
+    for (int j = 0; j < SPL; ++j) a[j] = 0.0f;
+  } else if (agg == NEAT_AGG_MAX) {
+    const uint4 e = ld_rec<SPL, GLOBAL>(pp);
+    float x0[SPL], x1[SPL];
+    HnVec<SPL>::ld(vb + (e.x << SH), x0);
+    HnVec<SPL>::ld(vb + (e.z << SH), x1);
+#pragma unroll
+    for (int j = 0; j < SPL; ++j)
+      a[j] = fmaxf(__uint_as_float(e.y) * x0[j], __uint_as_float(e.w) * x1[j]);
+    for (int k = 1; k < np; ++k) {
+      const uint4 f = ld_rec<SPL, GLOBAL>(pp + k);
+      HnVec<SPL>::ld(vb + (f.x << SH), x0);
+      HnVec<SPL>::ld(vb + (f.z << SH), x1);
+#pragma unroll
+      for (int j = 0; j < SPL; ++j) {
+        a[j] = fmaxf(a[j], __uint_as_float(f.y) * x0[j]);
+        a[j] = fmaxf(a[j], __uint_as_float(f.w) * x1[j]);
+      }
+    }
+  } else {  // product
+#pragma unroll
+    for (int j = 0; j < SPL; ++j) a[j] = 1.0f;
+    for (int k = 0; k < np; ++k) {
+      const uint4 f = ld_rec<SPL, GLOBAL>(pp + k);
+      float x0[SPL], x1[SPL];
+      HnVec<SPL>::ld(vb + (f.x << SH), x0);
+      HnVec<SPL>::ld(vb + (f.z << SH), x1);
+#pragma unroll
+      for (int j = 0; j < SPL; ++j) {
+        a[j] = a[j] * (__uint_as_float(f.y) * x0[j]);
+        a[j] = a[j] * (__uint_as_float(f.w) * x1[j]);
+      }
+    }
   }
+#pragma unroll
+  for (int j = 0; j < SPL; ++j) a[j] = fmaf(resp, a[j], bias);
+  act_apply_n<SPL>(int(meta >> CN_ROW_BITS) & 7, a);
+  HnVec<SPL>::st(vb + ((meta & ((1u << CN_ROW_BITS) - 1u)) << SH), a);
+}
+
+// Walk of a compiled program (CNode records and edge pairs; see
+// neat_internal.cuh) for this lane's SPL samples.  vb = the warp's value array
+// + lane * SPL floats (bytes); value row r of it at vb + r * 128 * SPL
+// ([row][32 lanes][SPL]: one vector access per row and lane).  GLOBAL: the
+// records come from global memory (read-only path), else from shared memory.
+// Per node: a 16-byte record; per two edges: one 16-byte pair; per edge and
+// sample: one value and one FMA.  Sum and mean keep even edges in a0 and odd
+// edges in a1, the rounding order of the position walk.
+template <int SPL, bool GLOBAL>
+__device__ __forceinline__ void cwalk(const CNode *__restrict__ nodes, int nn,
+                                      const uint4 *__restrict__ pairs, char *vb) {
+  for (int c = 0; c < nn; ++c)
+    cnode_eval<SPL, GLOBAL>(ld_rec<SPL, GLOBAL>(reinterpret_cast<const uint4 *>(nodes + c)), pairs,
+                            vb);
 }
 
 // Item = (genome in queue order, tile of 32 * SPL samples); lane l evaluates
@@ -385,40 +404,73 @@ __global__ void __launch_bounds__(512, 3)
             for (int o = 0; o < O; ++o) out[(size_t(g) * S + sj[j]) * O + o] = qnan();
       continue;
     }
-    const int32_t *lay = w.player + size_t(g) * N;
-    for (int p = threadIdx.x; p < h.V; p += blockDim.x)
-      if (p == 0 || lay[p - 1] != lay[p]) s_lstart[lay[p]] = p;
-    if (threadIdx.x == 0) s_lstart[h.L] = h.V;
-    float *vl = vc + lane;
-    const int32_t *io = w.pio + size_t(g) * (I + O);
-    for (int i = wid; i < I; i += nw)
+    if constexpr (COMP) {  // every valid genome of such a plan has its compiled program
+      {
+        // compiled program: the CTA's warps split each layer's compiled nodes,
+        // values [row][32][SPL] in the CTA's slot
+        const CNode *cn = w.cnode + size_t(g) * N;
+        const uint4 *cp = w.cpair + size_t(g) * cpair_cap(N, w.C);
+        const int32_t *cl = w.clay + size_t(g) * (N + 1);
+        for (int i = wid; i < I + 2; i += nw)
 #pragma unroll
-      for (int j = 0; j < SPL; ++j) {
-        const bool active = sj[j] < S;
-        const float *in = inputs + size_t(g) * stride + size_t(active ? sj[j] : 0) * I;
-        vl[(io[i] * SPL + j) * 32] = active ? __ldg(in + i) : 0.0f;
-      }
-    __syncthreads();
-    const NodeRec *nr = w.knode + h.node_off;
-    const EdgeRec *er = w.kedge + h.edge_off;
-    float *scol[SPL];
+          for (int j = 0; j < SPL; ++j) {
+            const bool active = sj[j] < S;
+            const float *in = inputs + size_t(g) * stride + size_t(active ? sj[j] : 0) * I;
+            vc[(i * 32 + lane) * SPL + j] =
+                i < I ? (active ? __ldg(in + i) : 0.0f) : (i == I ? 0.0f : 1.0f);
+          }
+        __syncthreads();
+        char *vb = reinterpret_cast<char *>(vc + lane * SPL);
+        for (int k = 0; k < h.clayers; ++k) {
+          const int c1 = cl[k + 1];
+          for (int c = cl[k] + wid; c < c1; c += nw)
+            cnode_eval<SPL, true>(__ldg(reinterpret_cast<const uint4 *>(cn + c)), cp, vb);
+          __syncthreads();
+        }
+        const int32_t *orow = w.cout + size_t(g) * O;
+        for (int o = wid; o < O; o += nw)
 #pragma unroll
-    for (int j = 0; j < SPL; ++j)
-      scol[j] = (saved != nullptr && sj[j] < S) ? saved + size_t(g) * N * S + sj[j] : nullptr;
-    for (int l = 0; l < h.L; ++l) {
-      const int p1 = s_lstart[l + 1];
-      for (int p = s_lstart[l] + wid; p < p1; p += nw) {
-        if (!COMP && saved != nullptr)
-          eval_node<true, SPL>(ld_node(nr + p), p, er, vl, scol, S);
-        else
-          eval_node<false, SPL>(ld_node(nr + p), p, er, vl, scol, S);
+          for (int j = 0; j < SPL; ++j)
+            if (sj[j] < S) out[(size_t(g) * S + sj[j]) * O + o] = vc[(orow[o] * 32 + lane) * SPL + j];
+        __syncthreads();  // the slot is reused by the next item
+        continue;
       }
+    } else {
+      const int32_t *lay = w.player + size_t(g) * N;
+      for (int p = threadIdx.x; p < h.V; p += blockDim.x)
+        if (p == 0 || lay[p - 1] != lay[p]) s_lstart[lay[p]] = p;
+      if (threadIdx.x == 0) s_lstart[h.L] = h.V;
+      float *vl = vc + lane;
+      const int32_t *io = w.pio + size_t(g) * (I + O);
+      for (int i = wid; i < I; i += nw)
+#pragma unroll
+        for (int j = 0; j < SPL; ++j) {
+          const bool active = sj[j] < S;
+          const float *in = inputs + size_t(g) * stride + size_t(active ? sj[j] : 0) * I;
+          vl[(io[i] * SPL + j) * 32] = active ? __ldg(in + i) : 0.0f;
+        }
       __syncthreads();
-    }
-    for (int o = wid; o < O; o += nw)
+      const NodeRec *nr = w.knode + h.node_off;
+      const EdgeRec *er = w.kedge + h.edge_off;
+      float *scol[SPL];
 #pragma unroll
       for (int j = 0; j < SPL; ++j)
-        if (sj[j] < S) out[(size_t(g) * S + sj[j]) * O + o] = vl[(io[I + o] * SPL + j) * 32];
+        scol[j] = (saved != nullptr && sj[j] < S) ? saved + size_t(g) * N * S + sj[j] : nullptr;
+      for (int l = 0; l < h.L; ++l) {
+        const int p1 = s_lstart[l + 1];
+        for (int p = s_lstart[l] + wid; p < p1; p += nw) {
+          if (!COMP && saved != nullptr)
+            eval_node<true, SPL>(ld_node(nr + p), p, er, vl, scol, S);
+          else
+            eval_node<false, SPL>(ld_node(nr + p), p, er, vl, scol, S);
+        }
+        __syncthreads();
+      }
+      for (int o = wid; o < O; o += nw)
+#pragma unroll
+        for (int j = 0; j < SPL; ++j)
+          if (sj[j] < S) out[(size_t(g) * S + sj[j]) * O + o] = vl[(io[I + o] * SPL + j) * 32];
+    }
     __syncthreads();  // the slot and s_lstart are reused by the next item
   }
 
@@ -432,8 +484,8 @@ __global__ void __launch_bounds__(512, 3)
     const int g = w.qorder[q];
     const GenomeHdr h = w.hdr[g];
     // COMP: a call without saved aggregates on a plan with compiled programs
-    const bool comp = COMP && h.crows > 0;
-    const int need = comp ? h.crows : h.V;  // rows of the value array
+    // (every valid genome of such a plan has one)
+    const int need = COMP ? h.crows : h.V;  // rows of the value array
     int sj[SPL];
 #pragma unroll
     for (int j = 0; j < SPL; ++j) sj[j] = tile * RS + j * 32 + lane;
@@ -467,40 +519,38 @@ __global__ void __launch_bounds__(512, 3)
             for (int o = 0; o < O; ++o)
               out[(size_t(g) * S + sj[j]) * O + o] = v[(orow[o] * 32 + lane) * SPL + j];
       };
-      if (comp) {
-        if (need <= vcap)
-          run(vs);  // shared memory
-        else
-          run(vg);
-        continue;
-      }
-    }
-    float *v = need <= vcap ? vs : vg;
-    float *vl = v + lane;
-    const int32_t *io = w.pio + size_t(g) * (I + O);
+      if (need <= vcap)
+        run(vs);  // shared memory
+      else
+        run(vg);
+    } else {
+      float *v = need <= vcap ? vs : vg;
+      float *vl = v + lane;
+      const int32_t *io = w.pio + size_t(g) * (I + O);
 #pragma unroll
-    for (int j = 0; j < SPL; ++j) {
-      const bool active = sj[j] < S;
-      const float *in = inputs + size_t(g) * stride + size_t(active ? sj[j] : 0) * I;
-      for (int i = 0; i < I; ++i) vl[(io[i] * SPL + j) * 32] = active ? __ldg(in + i) : 0.0f;
-    }
-    const NodeRec *nr = w.knode + h.node_off;
-    const EdgeRec *er = w.kedge + h.edge_off;
-    if (!COMP && saved != nullptr) {
-      float *scol[SPL];
+      for (int j = 0; j < SPL; ++j) {
+        const bool active = sj[j] < S;
+        const float *in = inputs + size_t(g) * stride + size_t(active ? sj[j] : 0) * I;
+        for (int i = 0; i < I; ++i) vl[(io[i] * SPL + j) * 32] = active ? __ldg(in + i) : 0.0f;
+      }
+      const NodeRec *nr = w.knode + h.node_off;
+      const EdgeRec *er = w.kedge + h.edge_off;
+      if (!COMP && saved != nullptr) {
+        float *scol[SPL];
+#pragma unroll
+        for (int j = 0; j < SPL; ++j)
+          scol[j] = sj[j] < S ? saved + size_t(g) * N * S + sj[j] : nullptr;
+        walk_program<true, SPL>(nr, er, h.V, vl, scol, S);
+      } else {
+        float *const scol[SPL] = {};
+        walk_program<false, SPL>(nr, er, h.V, vl, scol, S);
+      }
 #pragma unroll
       for (int j = 0; j < SPL; ++j)
-        scol[j] = sj[j] < S ? saved + size_t(g) * N * S + sj[j] : nullptr;
-      walk_program<true, SPL>(nr, er, h.V, vl, scol, S);
-    } else {
-      float *const scol[SPL] = {};
-      walk_program<false, SPL>(nr, er, h.V, vl, scol, S);
+        if (sj[j] < S)
+          for (int o = 0; o < O; ++o)
+            out[(size_t(g) * S + sj[j]) * O + o] = vl[(io[I + o] * SPL + j) * 32];
     }
-#pragma unroll
-    for (int j = 0; j < SPL; ++j)
-      if (sj[j] < S)
-        for (int o = 0; o < O; ++o)
-          out[(size_t(g) * S + sj[j]) * O + o] = vl[(io[I + o] * SPL + j) * 32];
   }
   grid_done_reset(w.counters + CTR_FWD_ITEM, w.counters + CTR_FWD_DONE, w.counters + CTR_FWD_BIG);
 }

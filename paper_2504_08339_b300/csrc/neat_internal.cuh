@@ -53,7 +53,8 @@ struct __align__(16) GenomeHdr {
                  // sum of ceil(indeg/4)
   int elive;     // enabled connections into those nodes
   int crows;     // value rows of the compiled program (0: none)
-  int pad[2];
+  int clayers;   // layers holding compiled nodes (their first nodes: Ws::clay)
+  int pad;
 };
 
 // -- compiled program (outputs-only walks) -----------------------------------------
@@ -61,9 +62,10 @@ struct __align__(16) GenomeHdr {
 // output depends on, in canonical order, with their incoming edges in pairs,
 // and a VALUE ROW per value instead of a position: rows 0..I-1 hold the
 // inputs, rows I and I+1 the constants 0 and 1, and the node values take rows
-// from I+2 on, a row being reused once the last node that reads it has read
-// it (a linear scan in canonical order; a node reads all its inputs before it
-// writes, so it may take a row it releases).  The outputs keep their rows.
+// from I+2 on, a row being reused once the layer of the last node that reads
+// it is done (a linear scan in canonical order, releases deferred to the end
+// of each layer, so that the nodes of one layer may run concurrently).  The
+// outputs keep their rows.
 // Each node's edge list is padded to an even length with an edge that leaves
 // the aggregate unchanged: weight 0 on the zero row for sum and mean, weight 1
 // on the one row for product, a repeat of the last edge for max.
@@ -71,6 +73,8 @@ struct __align__(16) GenomeHdr {
 //   CNode.meta  = value row | activation << 20 | aggregation << 23 |
 //                 (in-degree odd) << 25
 //   pair (uint4) = (source row 0, w0, source row 1, w1)
+// clay[g][k] = the first compiled node of the k-th layer that holds any
+// (k < clayers), clay[g][clayers] = the compiled node count.
 struct __align__(16) CNode {
   float bias, resp;
   uint32_t pairs;
@@ -183,7 +187,7 @@ struct Layout {
   size_t lvl_arena_bytes;
   int lvl_max_batches;
   size_t core;                       // bytes of everything above
-  size_t cnode, cpair, cout;            // compiled program (after core)
+  size_t cnode, cpair, cout, clay;      // compiled program (after core)
   size_t sp_scratch, sp_scratch_bytes;  // per-warp node value slots
   size_t total;
 };
@@ -229,6 +233,7 @@ inline Layout make_layout(int P, int N, int C, int I, int O) {
   L.cnode = take(sizeof(CNode) * p * N);
   L.cpair = take(sizeof(uint4) * p * size_t(cpair_cap(N, C)));
   L.cout = take(sizeof(int32_t) * p * O);
+  L.clay = take(sizeof(int32_t) * p * (N + 1));
   L.sp_scratch_bytes = sp_scratch_bytes(N);
   L.sp_scratch = take(L.sp_scratch_bytes);
   L.total = off;
@@ -255,8 +260,9 @@ struct Ws {
   BatchLoc *lvl_loc;
   unsigned char *lvl_arena;
   CNode *cnode;       // compiled program [P][N], pairs [P][cpair_cap], output
-  uint4 *cpair;       // rows [P][O] (nullptr: none)
+  uint4 *cpair;       // rows [P][O], layer starts [P][N + 1] (nullptr: none)
   int32_t *cout;
+  int32_t *clay;
   float *sp_scratch;  // per-warp node value slots (nullptr: none)
   size_t sp_scratch_floats;
   int lvl_budget, lvl_max_batches;
@@ -286,6 +292,7 @@ inline Ws make_ws(void *base, const Layout &L, int P, int N, int C, int I, int O
   w.cnode = reinterpret_cast<CNode *>(b + L.cnode);
   w.cpair = reinterpret_cast<uint4 *>(b + L.cpair);
   w.cout = reinterpret_cast<int32_t *>(b + L.cout);
+  w.clay = reinterpret_cast<int32_t *>(b + L.clay);
   w.sp_scratch = L.sp_scratch_bytes ? reinterpret_cast<float *>(b + L.sp_scratch) : nullptr;
   w.sp_scratch_floats = L.sp_scratch_bytes / sizeof(float);
   w.lvl_budget = lvl_budget(N, C, I, O);
@@ -301,7 +308,7 @@ constexpr int CTR_FWD_ITEM = 0, CTR_FWD_DONE = 1, CTR_HN_ITEM = 2, CTR_HN_DONE =
 // genomes of at least this cost (sp_cost) are evaluated by a whole CTA in the
 // sample-parallel forward (counters[CTR_SP_NBIG] of them, a queue prefix)
 #ifndef NEAT_SP_COOP_COST
-#define NEAT_SP_COOP_COST 2048
+#define NEAT_SP_COOP_COST 512
 #endif
 constexpr int SP_COOP_COST = NEAT_SP_COOP_COST;
 // cost of a genome in the sample-parallel forward: edges + 2 * nodes of the

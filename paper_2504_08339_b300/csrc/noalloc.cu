@@ -99,6 +99,7 @@ extern "C" neat_status neat_forward_noalloc(const float *nodes, const float *con
   w.cnode = nullptr;  // only the core part of the layout lives in the array
   w.cpair = nullptr;
   w.cout = nullptr;
+  w.clay = nullptr;
   w.sp_scratch = nullptr;
   w.sp_scratch_floats = 0;
   int32_t *order = reinterpret_cast<int32_t *>(base + align256(L.core));

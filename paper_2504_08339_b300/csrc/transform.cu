@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(256) k_transform(Ws w, const float *__restrict
   // 7. padded program (valid genomes only)
   GenomeHdr h;
   h.V = 0; h.E = 0; h.L = 0; h.status = status; h.node_off = 0; h.edge_off = 0;
-  h.nlive = 0; h.nch = 0; h.elive = 0; h.crows = 0; h.pad[0] = h.pad[1] = 0;
+  h.nlive = 0; h.nch = 0; h.elive = 0; h.crows = 0; h.clayers = 0; h.pad = 0;
   if (status == 0u) {
     h.V = V; h.E = E; h.L = t;
     // nodes some output depends on: the outputs, then frontier by frontier
@@ -496,14 +496,23 @@ __global__ void __launch_bounds__(256) k_transform(Ws w, const float *__restrict
       }
       __syncthreads();
       if (tid == 0) {
+        // rows released by a layer's nodes become free only for later layers:
+        // the nodes of one layer may then run at the same time (the CTA-wide
+        // walk), none writing a row another one of them still reads
+        int *pend = clast;  // free again
         for (int i = 0; i < I; ++i) crow[s_of_row[i]] = i;
-        int sp = 0, next = I + 2;
+        int sp = 0, np = 0, next = I + 2, cur = -1;
         for (int p = 0; p < V; ++p) {
           const int s = order_s[p];
           if (!live[s] || row_of_s[s] < I) continue;
-          const int j1 = p + 1 < V ? roff[p + 1] : nrel;
-          for (int j = roff[p]; j < j1; ++j) cst[sp++] = crow[rlist[j]];
+          if (layer_s[s] != cur) {
+            for (int j = 0; j < np; ++j) cst[sp++] = pend[j];
+            np = 0;
+            cur = layer_s[s];
+          }
           crow[s] = sp > 0 ? cst[--sp] : next++;
+          const int j1 = p + 1 < V ? roff[p + 1] : nrel;
+          for (int j = roff[p]; j < j1; ++j) pend[np++] = crow[rlist[j]];
         }
         s_crows = next;
       }
@@ -547,6 +556,25 @@ __global__ void __launch_bounds__(256) k_transform(Ws w, const float *__restrict
         }
       }
       for (int i = tid; i < O; i += T) w.cout[size_t(g) * O + i] = crow[s_of_row[I + i]];
+      // first compiled node of each layer that holds any (compact indices
+      // follow the canonical order, so a layer's nodes are contiguous)
+      const int nn = h.nlive;
+      int *lay_c = clast;  // layer of each compiled node (clast is free)
+      int *bnd = roff;     // layer-start flags, then their index (roff is free)
+      __syncthreads();
+      for (int p = tid; p < V; p += T) {
+        const int s = order_s[p];
+        if (live[s] && row_of_s[s] >= I) lay_c[cidx[p]] = layer_s[s];
+      }
+      __syncthreads();
+      for (int c = tid; c < nn; c += T) bnd[c] = (c == 0 || lay_c[c - 1] != lay_c[c]) ? 1 : 0;
+      __syncthreads();
+      const int nl = block_exclusive_scan(bnd, nn, wbuf);
+      int32_t *cl = w.clay + size_t(g) * (N + 1);
+      for (int c = tid; c < nn; c += T)
+        if (c == 0 || lay_c[c - 1] != lay_c[c]) cl[bnd[c]] = c;
+      if (tid == 0) cl[nl] = nn;
+      h.clayers = nl;
     }
   }
   if (tid == 0) w.hdr[g] = h;

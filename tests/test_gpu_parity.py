@@ -138,6 +138,23 @@ def test_forward_parity(name, P, S, path):
         assert stats["ill_conditioned"] == 0, stats
 
 
+def _live_cost(n, c, I, O):
+    """Enabled connections into, plus twice the count of, the non-input nodes
+    some output depends on (reverse reachability from the output rows)."""
+    row = {float(k): r for r, k in enumerate(n[:, 0]) if not np.isnan(k)}
+    en = ~np.isnan(c[:, 0]) & ~np.isnan(c[:, 1]) & ~np.isnan(c[:, 3]) & (c[:, 3] != 0)
+    preds = {}
+    for a, b in c[en, :2]:
+        preds.setdefault(row[float(b)], []).append(row[float(a)])
+    live, stack = set(range(I, I + O)), list(range(I, I + O))
+    while stack:
+        for a in preds.get(stack.pop(), ()):
+            if a not in live:
+                live.add(a)
+                stack.append(a)
+    return sum(len(preds.get(r, ())) + 2 for r in live if r >= I)
+
+
 @pytest.mark.parametrize("name,P,S", [("uneven", 300, 77), ("locomotion", 200, 45),
                                       ("differentiation", 128, 100)])
 def test_sample_parallel_shapes_agree_bitwise(name, P, S):
@@ -147,13 +164,11 @@ def test_sample_parallel_shapes_agree_bitwise(name, P, S):
     tile for 1, 2 and 4 samples per lane."""
     nodes, conns, spec, x = _fwd_case(name, P, S)
     if name == "uneven":
-        # genomes with E + 2V >= 2048 are evaluated by whole CTAs (frontier by
-        # frontier); the others by single warps: both run here
-        valid = ~np.isnan(nodes[:, :, 0])
-        enabled = (~np.isnan(conns[:, :, 0]) & ~np.isnan(conns[:, :, 1]) &
-                   ~np.isnan(conns[:, :, 3]) & (conns[:, :, 3] != 0))
-        cost = enabled.sum(1) + 2 * valid.sum(1)
-        assert (cost >= 2048).sum() >= 10 and (cost < 2048).sum() >= 10
+        # genomes whose part the outputs depend on costs E + 2V >= 512 are
+        # evaluated by whole CTAs (layer by layer); the others by single
+        # warps: both run here
+        cost = np.array([_live_cost(nodes[g], conns[g], spec.I, spec.O) for g in range(P)])
+        assert (cost >= 512).sum() >= 10 and (cost < 512).sum() >= 10
     plan = _plan(spec, P)
     plan.set_tuning(small_s_max=-1)
     plan.transform(_dev(nodes), _dev(conns))
