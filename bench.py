@@ -120,6 +120,9 @@ def parse_args():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--prune", action="store_true",
+                    help="skip the nodes no output depends on (prune_dead = 1): the same "
+                         "outputs; the value still counts every enabled connection")
     ap.add_argument("--recompute", action="store_true",
                     help="differentiation at S = 65,536 with the forward values recomputed in the "
                          "backward (no saved aggregates)")
@@ -277,12 +280,24 @@ def _rows(skeys, order, g, key):
     return np.where(hit, order.ravel()[pos] % N, -1)
 
 
+def walked_counts(prune, nodes, conns, spec, E, Vn, extra):
+    """Connections and non-input nodes an evaluation visits, per genome: all
+    of them, or with pruning the part some output depends on (noted in the
+    line's extra)."""
+    if not prune:
+        return E, Vn - spec.I
+    E_live, V_live = live_counts(nodes, conns, spec.I, spec.O)
+    extra["live_subgraph"] = live_note(E, E_live, V_live)
+    return E_live, V_live
+
+
 def live_note(E, E_live, V_live):
     return {"conns_per_genome_mean": round(float(E_live.mean()), 2),
             "conns_fraction_of_enabled": round(float(E_live.sum() / max(1, E.sum())), 4),
             "nodes_per_genome_mean": round(float(V_live.mean()), 2),
-            "note": "nodes no output depends on are not evaluated (identical outputs); "
-                    "value counts every enabled connection, the roofline only the live part"}
+            "note": "--prune: nodes no output depends on are not evaluated (identical "
+                    "outputs); value counts every enabled connection, the roofline only "
+                    "the live part"}
 
 
 def workload(name, seed, pop=None):
@@ -431,6 +446,8 @@ def bench_ours(args, rank, world, local, pg):
     P = cfg["P"]
     E, Vn = enabled_counts(nodes, conns)
     plan = Plan(P, spec.N, spec.C, spec.I, spec.O, device=dev)
+    if args.prune:
+        plan.set_tuning(prune_dead=1)
     launches_per_step = 4  # transform, rank, offsets, pack
     extra = {}
 
@@ -457,8 +474,7 @@ def bench_ours(args, rank, world, local, pg):
         # on: its algorithmic traffic counts that part (program: 8 B per edge,
         # 12 B per node; inputs and outputs; on chip a value read per edge and
         # written per node, per sample)
-        E_live, V_live = live_counts(nodes, conns, spec.I, spec.O)
-        extra["live_subgraph"] = live_note(E, E_live, V_live)
+        E_live, V_live = walked_counts(args.prune, nodes, conns, spec, E, Vn, extra)
         alg_bytes = float((8 * E_live + 12 * (V_live + spec.I)).sum() +
                           4 * S * (spec.I + spec.O) * P)
         chip_bytes = float(4 * S * (E_live + V_live).sum())
@@ -500,8 +516,7 @@ def bench_ours(args, rank, world, local, pg):
         # have a zero adjoint): its program, saved-aggregate and on-chip terms
         # count that part; the gradients of every row are written.
         rec = saved is None
-        E_live, V_live = live_counts(nodes, conns, spec.I, spec.O)
-        extra["live_subgraph"] = live_note(E, E_live, V_live)
+        E_live, V_live = walked_counts(args.prune, nodes, conns, spec, E, Vn, extra)
         Vl = V_live + spec.I
         alg_bytes = float((8 * E_live + 12 * Vl).sum() + (4 * E + 8 * Vn).sum() +
                           (0 if rec else 4 * S * V_live.sum()) +
@@ -538,7 +553,7 @@ def bench_ours(args, rank, world, local, pg):
         launches_per_step += 2
         fwd_launches = 1
         ro = None
-        E_live, V_live = live_counts(nodes, conns, spec.I, spec.O)
+        E_live, V_live = walked_counts(args.prune, nodes, conns, spec, E, Vn, extra)
         alg_bytes = float((8 * E + 12 * Vn).sum() + 4.0 * 2 ** 20 * P)
         chip_bytes = float(4.0 * 2 ** 20 * (E_live + V_live).sum())
     elif name == "mutate":
@@ -637,8 +652,7 @@ def bench_ours(args, rank, world, local, pg):
         # the query evaluates only the nodes the output depends on: program
         # bytes once, a weight written per query; on chip a value read per
         # live connection and written per live node, per query
-        E_live, V_live = live_counts(nodes, conns, spec.I, spec.O)
-        extra["live_subgraph"] = live_note(E, E_live, V_live)
+        E_live, V_live = walked_counts(args.prune, nodes, conns, spec, E, Vn, extra)
         alg_bytes = float((8 * E + 12 * Vn).sum() + 4.0 * 2 ** 20 * P)
         chip_bytes = float(4.0 * 2 ** 20 * (E_live + V_live).sum())
 
@@ -828,6 +842,7 @@ def bench_ours(args, rank, world, local, pg):
         "data": "synthetic (seeded generators; random genomes shaped like the workload)",
         "config": {"workload": describe(name, cfg, spec), "name": name, "pop": P,
                    "pop_override": args.pop is not None,
+                   "prune_dead": bool(args.prune),
                    "enabled_conns_per_genome_mean": round(float(E.mean()), 2),
                    "valid_nodes_per_genome_mean": round(float(Vn.mean()), 2),
                    "form": "batched: persistent size-sorted queue over ragged-packed programs, "

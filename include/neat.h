@@ -127,13 +127,20 @@ neat_status neat_plan_destroy(neat_plan *plan);
  *                    saved aggregates, and batches that do not fit in shared
  *                    memory use the sample-parallel forward
  *   lvl_budget_kb    program bytes (KiB, 8..160) per level-synchronous batch;
- *                    applied by the next neat_transform */
+ *                    applied by the next neat_transform
+ *   prune_dead       0 (default): every valid node is evaluated, as the
+ *                    paper's calculation does; 1: forwards that return only the
+ *                    outputs, the HyperNEAT query and the backward skip the
+ *                    nodes no output depends on (the same outputs; their
+ *                    parameters' gradients are 0); applied by the next
+ *                    neat_transform */
 typedef struct {
   int warps_per_cta;
   int samples_per_lane;
   int lvl_threads;
   int small_s_max;
   int lvl_budget_kb;
+  int prune_dead;
 } neat_tuning;
 neat_status neat_plan_set_tuning(neat_plan *plan, const neat_tuning *t);
 neat_status neat_plan_get_tuning(const neat_plan *plan, neat_tuning *t);

@@ -37,7 +37,8 @@ class NeatError(RuntimeError):
 class neat_tuning(ctypes.Structure):
     _fields_ = [("warps_per_cta", ctypes.c_int), ("samples_per_lane", ctypes.c_int),
                 ("lvl_threads", ctypes.c_int), ("small_s_max", ctypes.c_int),
-                ("lvl_budget_kb", ctypes.c_int)]
+                ("lvl_budget_kb", ctypes.c_int),
+                ("prune_dead", ctypes.c_int)]
 
 
 _lock = threading.Lock()

@@ -174,6 +174,7 @@ neat_status neat_plan_set_tuning(neat_plan *plan, const neat_tuning *t) {
   if (t->lvl_budget_kb != 0 && (t->lvl_budget_kb * 1024 < neat::LVL_MIN_BUDGET ||
                                 t->lvl_budget_kb * 1024 > neat::LVL_MAX_BUDGET))
     return NEAT_ERR_ARG;
+  if (t->prune_dead != 0 && t->prune_dead != 1) return NEAT_ERR_ARG;
   plan->tune = *t;
   return NEAT_OK;
 }
@@ -203,6 +204,7 @@ neat_status neat_transform(neat_plan *plan, const float *nodes, const float *con
       return NEAT_ERR_ARG;
   }
   // the batch budget is fixed by the transform that builds the batches
+  plan->w.prune = plan->tune.prune_dead == 1 ? 1 : 0;
   plan->w.lvl_budget = plan->tune.lvl_budget_kb > 0
                            ? plan->tune.lvl_budget_kb * 1024
                            : neat::lvl_budget(plan->N, plan->C, plan->I, plan->O);

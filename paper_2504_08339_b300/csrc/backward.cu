@@ -176,13 +176,13 @@ __global__ void k_backward(Ws w, const float *__restrict__ inputs, int64_t strid
     const NodeRec n = w.knode[h.node_off + p];
     if (n.meta & META_INPUT) continue;
     const int cnt = meta_cnt(n.meta), agg = meta_agg(n.meta);
-    // a node no output depends on has a zero adjoint: its edges carry nothing
-    const bool dead = (n.meta & META_DEAD) != 0;
-    const bool lin = !dead && (agg == NEAT_AGG_SUM || agg == NEAT_AGG_MEAN);
+    // (a node no output depends on keeps its pull entries: it adds its zero
+    // adjoint in the same place of each source's sum as without pruning)
+    const bool lin = agg == NEAT_AGG_SUM || agg == NEAT_AGG_MEAN;
     const float c = agg == NEAT_AGG_MEAN ? n.resp / float(cnt) : n.resp;
     for (int k = 0; k < cnt; ++k) {
       edst[n.in_begin + k] = lin ? p : -1;
-      ecoef[n.in_begin + k] = dead ? 0.0f : c;
+      ecoef[n.in_begin + k] = c;
     }
   }
   __syncthreads();

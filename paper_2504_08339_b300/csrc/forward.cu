@@ -829,7 +829,7 @@ __device__ void hn_stage(const Ws &w, const GenomeHdr &h, const int32_t *io, HnN
   const int po = io[5];
   for (int i = threadIdx.x; i < V; i += blockDim.x) {
     tn[i] = ld_node(nr + i);
-    need[i] = i == po;
+    need[i] = w.prune ? i == po : 1;  // without pruning every node is evaluated
     last[i] = -1;
     row[i] = -1;
   }

@@ -266,6 +266,7 @@ struct Ws {
   float *sp_scratch;  // per-warp node value slots (nullptr: none)
   size_t sp_scratch_floats;
   int lvl_budget, lvl_max_batches;
+  int prune;  // skip the nodes no output depends on (set at transform time)
   int P, N, C, I, O;
 };
 
@@ -296,6 +297,7 @@ inline Ws make_ws(void *base, const Layout &L, int P, int N, int C, int I, int O
   w.sp_scratch = L.sp_scratch_bytes ? reinterpret_cast<float *>(b + L.sp_scratch) : nullptr;
   w.sp_scratch_floats = L.sp_scratch_bytes / sizeof(float);
   w.lvl_budget = lvl_budget(N, C, I, O);
+  w.prune = 0;
   w.lvl_max_batches = L.lvl_max_batches;
   w.P = P; w.N = N; w.C = C; w.I = I; w.O = O;
   return w;

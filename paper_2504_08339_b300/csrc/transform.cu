@@ -347,14 +347,15 @@ __global__ void __launch_bounds__(256) k_transform(Ws w, const float *__restrict
   h.nlive = 0; h.nch = 0; h.elive = 0; h.crows = 0; h.clayers = 0; h.pad = 0;
   if (status == 0u) {
     h.V = V; h.E = E; h.L = t;
-    // nodes some output depends on: the outputs, then frontier by frontier
-    // from the last, the sources of every such node (feed-forward only; in a
-    // recurrent network every node counts)
+    // nodes some output depends on (with pruning on, feed-forward only): the
+    // outputs, then frontier by frontier from the last, the sources of every
+    // such node; otherwise every node counts
     int *live = ready;     // free after the sort
     int *fstart = outbeg;  // first position of each frontier (N + 1 entries)
-    for (int s = tid; s < V; s += T) live[s] = recurrent ? 1 : 0;
+    const bool sweep = !recurrent && w.prune;  // else every node counts
+    for (int s = tid; s < V; s += T) live[s] = sweep ? 0 : 1;
     __syncthreads();
-    if (!recurrent) {
+    if (sweep) {
       for (int p = tid; p < V; p += T)
         if (p == 0 || layer_s[order_s[p]] != layer_s[order_s[p - 1]])
           fstart[layer_s[order_s[p]]] = p;

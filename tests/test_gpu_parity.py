@@ -155,22 +155,30 @@ def _live_cost(n, c, I, O):
     return sum(len(preds.get(r, ())) + 2 for r in live if r >= I)
 
 
+@pytest.mark.parametrize("prune", [0, 1])
 @pytest.mark.parametrize("name,P,S", [("uneven", 300, 77), ("locomotion", 200, 45),
                                       ("differentiation", 128, 100)])
-def test_sample_parallel_shapes_agree_bitwise(name, P, S):
+def test_sample_parallel_shapes_agree_bitwise(name, P, S, prune):
     """Samples per lane and warps per CTA change which lane and which value
     slot evaluate a sample, not the arithmetic: every shape gives the same
-    bits, and the saved aggregates too.  S = 77, 45, 100 leave a ragged last
-    tile for 1, 2 and 4 samples per lane."""
+    bits, and the saved aggregates too; the outputs-only calls (compiled
+    programs, with or without the nodes no output depends on) give the bits
+    of the position walk.  S = 77, 45, 100 leave a ragged last tile for 1, 2
+    and 4 samples per lane."""
     nodes, conns, spec, x = _fwd_case(name, P, S)
     if name == "uneven":
-        # genomes whose part the outputs depend on costs E + 2V >= 512 are
-        # evaluated by whole CTAs (layer by layer); the others by single
-        # warps: both run here
-        cost = np.array([_live_cost(nodes[g], conns[g], spec.I, spec.O) for g in range(P)])
+        # genomes of cost E + 2V >= 512 (the part the outputs depend on, with
+        # pruning) are evaluated by whole CTAs (layer by layer); the others by
+        # single warps: both run here
+        if prune:
+            cost = np.array([_live_cost(nodes[g], conns[g], spec.I, spec.O) for g in range(P)])
+        else:
+            en = (~np.isnan(conns[:, :, 0]) & ~np.isnan(conns[:, :, 1]) &
+                  ~np.isnan(conns[:, :, 3]) & (conns[:, :, 3] != 0))
+            cost = en.sum(1) + 2 * ((~np.isnan(nodes[:, :, 0])).sum(1) - spec.I)
         assert (cost >= 512).sum() >= 10 and (cost < 512).sum() >= 10
     plan = _plan(spec, P)
-    plan.set_tuning(small_s_max=-1)
+    plan.set_tuning(small_s_max=-1, prune_dead=prune)
     plan.transform(_dev(nodes), _dev(conns))
     dx = _dev(x)
     base_saved = torch.full((P, spec.N, S), float("nan"), device="cuda")
@@ -183,7 +191,7 @@ def test_sample_parallel_shapes_agree_bitwise(name, P, S):
               dict(samples_per_lane=4, warps_per_cta=16),
               dict(samples_per_lane=1, warps_per_cta=16)]
     for sh in shapes:
-        plan.set_tuning(small_s_max=-1, **sh)
+        plan.set_tuning(small_s_max=-1, prune_dead=prune, **sh)
         saved = torch.full((P, spec.N, S), float("nan"), device="cuda")
         out = plan.forward(dx, saved=saved)
         bits = lambda t: t.view(torch.int32)  # noqa: E731  (NaN-safe equality)
@@ -191,6 +199,48 @@ def test_sample_parallel_shapes_agree_bitwise(name, P, S):
         # (positions the forward does not write stay NaN on both sides)
         assert torch.equal(bits(saved), bits(base_saved)), sh
         assert torch.equal(bits(plan.forward(dx)), bits(base)), sh
+
+
+@pytest.mark.parametrize("name,P,S", [("locomotion", 500, 1), ("uneven", 200, 64),
+                                      ("differentiation", 64, 100), ("tiny", 100, 4)])
+def test_pruning_changes_no_result(name, P, S):
+    """Skipping the nodes no output depends on (prune_dead = 1) gives the
+    bits of evaluating every node: the level-synchronous, compiled
+    sample-parallel and HyperNEAT paths, and the gradients' values (the
+    skipped nodes' gradients are 0 either way)."""
+    nodes, conns, spec, x = _fwd_case(name, P, S)
+    dn, dc, dx = _dev(nodes), _dev(conns), _dev(x)
+    res = []
+    for prune in (0, 1):
+        plan = _plan(spec, P)
+        plan.set_tuning(prune_dead=prune)
+        plan.transform(dn, dc)
+        out = plan.forward(dx)
+        plan.set_tuning(prune_dead=prune, small_s_max=-1)
+        out_sp = plan.forward(dx)
+        go = torch.ones((P, S, spec.O), device="cuda")
+        # (the backward keeps a genome's records in shared memory: up to
+        # N = 1024, C = 4096 it does not fit, and says so)
+        grads = plan.backward(dx, go) if name != "uneven" else ()
+        res.append((out, out_sp, grads))
+    bits = lambda t: t.view(torch.int32)  # noqa: E731
+    assert torch.equal(bits(res[0][0]), bits(res[1][0]))
+    assert torch.equal(bits(res[0][1]), bits(res[1][1]))
+    for a, b in zip(res[0][2], res[1][2]):
+        assert torch.equal(a, b)
+    ref, bnd = oracle.forward(nodes, conns, x, spec.I, spec.O, with_bound=True)
+    compare_outputs(res[1][0].cpu().numpy(), ref, bnd)
+
+
+def test_pruning_changes_no_hyperneat_weight():
+    nodes, conns, spec = population_for("hyperneat", seed=6, P=24)
+    outs = []
+    for prune in (0, 1):
+        plan = _plan(spec, 24)
+        plan.set_tuning(prune_dead=prune)
+        plan.transform(_dev(nodes), _dev(conns))
+        outs.append(plan.hyperneat(grid=9, thresh=0.2).view(torch.int32).clone())
+    assert torch.equal(outs[0], outs[1])
 
 
 def test_forward_saved_aggregates_match_oracle_values():
