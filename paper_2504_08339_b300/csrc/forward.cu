@@ -353,7 +353,7 @@ __device__ __forceinline__ void cwalk(const CNode *__restrict__ nodes, int nn,
 // L1/L2-resident while in use).
 //
 // With `coop`, the items of the queue's first counters[CTR_SP_NBIG] genomes
-// (the most expensive ones, sp_cost >= SP_COOP_COST) are taken by whole CTAs:
+// (the most expensive ones, sp_cost >= sp_coop_cost) are taken by whole CTAs:
 // the CTA's warps split each frontier's positions (no position of a frontier
 // reads another's value) with a barrier between frontiers, in the slot of the
 // CTA's first warp.  One warp walking such a genome alone would finish long

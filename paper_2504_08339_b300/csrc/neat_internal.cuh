@@ -308,11 +308,14 @@ constexpr int CTR_FWD_ITEM = 0, CTR_FWD_DONE = 1, CTR_HN_ITEM = 2, CTR_HN_DONE =
               CTR_LVL_ITEM = 4, CTR_LVL_DONE = 5, CTR_FWD_BIG = 6, CTR_SP_NBIG = 7,
               CTR_NBATCH = 8, CTR_ERR = 9, CTR_REC_ITEM = 10, CTR_REC_DONE = 11;
 // genomes of at least this cost (sp_cost) are evaluated by a whole CTA in the
-// sample-parallel forward (counters[CTR_SP_NBIG] of them, a queue prefix)
-#ifndef NEAT_SP_COOP_COST
-#define NEAT_SP_COOP_COST 512
-#endif
-constexpr int SP_COOP_COST = NEAT_SP_COOP_COST;
+// sample-parallel forward (counters[CTR_SP_NBIG] of them, a queue prefix);
+// measured best on the uneven workload: 2048 evaluating every node, 512 with
+// the nodes no output depends on skipped (the CTA-wide walk then covers the
+// long per-warp items that otherwise end the launch)
+constexpr int SP_COOP_COST = 2048, SP_COOP_COST_PRUNED = 512;
+__host__ __device__ inline int sp_coop_cost(bool prune) {
+  return prune ? SP_COOP_COST_PRUNED : SP_COOP_COST;
+}
 // cost of a genome in the sample-parallel forward: edges + 2 * nodes of the
 // part some output depends on, plus a quarter per skipped position
 __host__ __device__ inline int sp_cost(const GenomeHdr &h) {

@@ -626,7 +626,7 @@ __global__ void __launch_bounds__(1024) k_offsets(Ws w) {
     se += h.E;
     // the most expensive genomes (a prefix of the cost-sorted queue) go to
     // whole CTAs in the sample-parallel forward
-    sb += (h.status == 0u && sp_cost(h) >= SP_COOP_COST) ? 1 : 0;
+    sb += (h.status == 0u && sp_cost(h) >= sp_coop_cost(w.prune != 0)) ? 1 : 0;
   }
   if (sb) atomicAdd(&nbig, sb);
   int xv = sv, xe = se;

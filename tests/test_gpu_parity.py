@@ -167,16 +167,17 @@ def test_sample_parallel_shapes_agree_bitwise(name, P, S, prune):
     and 4 samples per lane."""
     nodes, conns, spec, x = _fwd_case(name, P, S)
     if name == "uneven":
-        # genomes of cost E + 2V >= 512 (the part the outputs depend on, with
-        # pruning) are evaluated by whole CTAs (layer by layer); the others by
-        # single warps: both run here
+        # genomes of cost E + 2V >= 2048 (>= 512 for the part the outputs
+        # depend on, with pruning) are evaluated by whole CTAs (layer by
+        # layer); the others by single warps: both run here
         if prune:
             cost = np.array([_live_cost(nodes[g], conns[g], spec.I, spec.O) for g in range(P)])
         else:
             en = (~np.isnan(conns[:, :, 0]) & ~np.isnan(conns[:, :, 1]) &
                   ~np.isnan(conns[:, :, 3]) & (conns[:, :, 3] != 0))
             cost = en.sum(1) + 2 * ((~np.isnan(nodes[:, :, 0])).sum(1) - spec.I)
-        assert (cost >= 512).sum() >= 10 and (cost < 512).sum() >= 10
+        big = 512 if prune else 2048
+        assert (cost >= big).sum() >= 10 and (cost < big).sum() >= 10
     plan = _plan(spec, P)
     plan.set_tuning(small_s_max=-1, prune_dead=prune)
     plan.transform(_dev(nodes), _dev(conns))
