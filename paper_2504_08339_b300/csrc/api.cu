@@ -289,7 +289,7 @@ neat_status neat_hyperneat_query(neat_plan *plan, int grid, float thresh, float 
   if (plan->P == 0) return NEAT_OK;
   if (weights == nullptr || !aligned(weights, 4)) return NEAT_ERR_ARG;
   const int spl = plan->tune.samples_per_lane > 0 ? plan->tune.samples_per_lane : 2;
-  const int warps = plan->tune.warps_per_cta > 0 ? plan->tune.warps_per_cta : 8;
+  const int warps = plan->tune.warps_per_cta > 0 ? plan->tune.warps_per_cta : 16;
   // shared memory per CTA: an SM's share for about 32 resident warps (the
   // staged program plus as many value arrays as fit), less the static part
   int per_sm = 0, reserved = 0;
@@ -301,16 +301,14 @@ neat_status neat_hyperneat_query(neat_plan *plan, int grid, float thresh, float 
   const int want = std::max(1, 32 / warps);
   const int prog = neat::hn_prog_bytes(plan->N, plan->C);
   int smem = std::min(plan->smem_optin, per_sm / want - reserved) - 1024;
-  // a CTA holds at least the program and the staging scratch of a full-size
+  // a CTA holds at least the program and one value array of a full-size
   // genome (fewer CTAs per SM for large N, C)
-  if (smem < prog + neat::hn_stage_bytes(plan->N, plan->C)) smem = plan->smem_optin - 1024;
+  const int64_t rows_max = int64_t(plan->N + 2) * 32 * spl * 4;
+  if (smem < prog + rows_max) smem = plan->smem_optin - 1024;
   if (smem < prog) return NEAT_ERR_UNSUPPORTED;
   const int occ = std::max(1, neat::hyperneat_occupancy(spl, warps, size_t(smem)));
   int64_t ctas = int64_t(plan->sm_count) * occ;
-  const int64_t stage_need = std::max<int64_t>(neat::hn_stage_bytes(plan->N, plan->C),
-                                               int64_t(plan->N + neat::HN_ROW_FIRST) * 32 * spl * 4);
-  const bool all_fit = stage_need + prog <= smem;
-  if (!all_fit) {  // some genomes may use workspace slots: one per warp
+  if (rows_max + prog > smem) {  // some genomes may use workspace slots: one per warp
     ctas = std::min<int64_t>(ctas, neat::sp_scratch_slots(plan->w, spl) / warps);
     if (ctas >= plan->sm_count) ctas -= ctas % plan->sm_count;
   }
@@ -371,7 +369,7 @@ neat_status neat_forward_recurrent(neat_plan *plan, const float *inputs, int64_t
   if (outputs == nullptr || !aligned(outputs, 4)) return NEAT_ERR_ARG;
   // 8 warps per CTA (the tuning's warps_per_cta if set); two value buffers
   // per warp bound the grid, kept to whole multiples of the SM count
-  const int warps = plan->tune.warps_per_cta > 0 ? plan->tune.warps_per_cta : 8;
+  const int warps = plan->tune.warps_per_cta > 0 ? plan->tune.warps_per_cta : 16;
   const int slots = neat::sp_scratch_slots(plan->w, 2);
   const int occ = std::max(1, neat::forward_rec_occupancy(warps));
   const int64_t items = int64_t(plan->P) * ((S + 31) / 32);

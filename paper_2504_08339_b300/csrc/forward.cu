@@ -658,269 +658,14 @@ __global__ void __launch_bounds__(32) k_forward_plain(Ws w, const float *__restr
 // Item = (genome in queue order, chunk of tiles), claimed by a whole CTA; tile =
 // 32 * SPL consecutive queries, lane l of its warp evaluating queries
 // tile * 32 * SPL + k * 32 + l, k < SPL (every program record loaded serves
-// SPL queries per lane).  The CTA first stages the genome's program in shared
-// memory in a form made for this walk (HnNode below): input positions dropped,
-// each node's incoming edges in pairs with value offsets precomputed, so the
-// walk issues one 16-byte broadcast load per two edges, one vector load of the
-// lane's SPL values per edge and one FMA per edge and query.  Node values live
-// in shared memory too, [row][32][SPL] per warp.  A genome whose values do not
-// fit falls back to the sample-parallel walk over the packed program with
-// values in the warp's workspace slot.
-
-// Staged node (16 B): non-input nodes in program order.
-//   pairs = byte offset of the node's first edge pair in the pair array
-//           [0, 17) | pair count << 17
-//   meta  = byte offset of the node's value row [0, 20) | activation << 20 |
-//           aggregation << 23 | (in-degree odd) << 25
-// A pair (uint4) is (offset0, w0, offset1, w1), the offsets being byte offsets
-// of the source rows in a warp's value array; each node's list is padded to an
-// even length with an edge that leaves the aggregate unchanged: weight 0 on the
-// zero row (rows V and V + 1 hold 0 and 1) for sum and mean, weight 1 on the
-// one row for product, a repeat of the last edge for max.
-struct __align__(16) HnNode {
-  float bias, resp;
-  uint32_t pairs;
-  uint32_t meta;
-};
-constexpr uint32_t HN_PAIR_BITS = 17, HN_ROW_BITS = 20;
-static_assert(((NEAT_MAX_CONNS + NEAT_MAX_NODES) / 2 + 1) * 16 <= (1 << HN_PAIR_BITS),
-              "pair offsets overflow their field");
-static_assert((NEAT_MAX_NODES + 7) * 32 * 4 * 4 <= (1 << HN_ROW_BITS), "row offsets overflow their field");
-
-// exclusive block-wide prefix sums of (a, b) and their totals; s: 64 ints
-__device__ __forceinline__ void block_scan2(int a, int b, int &ea, int &eb, int &ta, int &tb,
-                                            int *s) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  int ia = a, ib = b;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int x = __shfl_up_sync(0xffffffffu, ia, o), y = __shfl_up_sync(0xffffffffu, ib, o);
-    if (lane >= o) {
-      ia += x;
-      ib += y;
-    }
-  }
-  if (lane == 31) {
-    s[wid] = ia;
-    s[32 + wid] = ib;
-  }
-  __syncthreads();
-  int oa = 0, ob = 0;
-  ta = 0;
-  tb = 0;
-  for (int i = 0; i < nw; ++i) {
-    const int x = s[i], y = s[32 + i];
-    if (i < wid) {
-      oa += x;
-      ob += y;
-    }
-    ta += x;
-    tb += y;
-  }
-  ea = oa + ia - a;
-  eb = ob + ib - b;
-  __syncthreads();  // s is reused by the next call
-}
-
-// Walk of a staged program for this lane's SPL queries; vb = the warp's value
-// array + lane * SPL floats (bytes), row stride 32 * SPL floats.
-template <int SPL>
-__device__ __forceinline__ void hn_walk(const HnNode *__restrict__ nodes, int nn,
-                                        const uint4 *__restrict__ pairs, char *vb) {
-  const char *pbase = reinterpret_cast<const char *>(pairs);
-  for (int c = 0; c < nn; ++c) {
-    const HnNode n = nodes[c];
-    const int np = int(n.pairs >> HN_PAIR_BITS);
-    const uint4 *pp =
-        reinterpret_cast<const uint4 *>(pbase + (n.pairs & ((1u << HN_PAIR_BITS) - 1u)));
-    const int agg = int(n.meta >> (HN_ROW_BITS + 3)) & 3;
-    float a[SPL];
-    if (agg == NEAT_AGG_SUM || agg == NEAT_AGG_MEAN) {
-      // even edges into a0, odd edges into a1 (the rounding order of the
-      // sample-parallel walk)
-      float a0[SPL], a1[SPL];
-#pragma unroll
-      for (int j = 0; j < SPL; ++j) a0[j] = a1[j] = 0.0f;
-#pragma unroll 2
-      for (int k = 0; k < np; ++k) {
-        const uint4 e = pp[k];
-        float x0[SPL], x1[SPL];
-        HnVec<SPL>::ld(vb + e.x, x0);
-        HnVec<SPL>::ld(vb + e.z, x1);
-        hn_fma<SPL>(__uint_as_float(e.y), x0, a0);
-        hn_fma<SPL>(__uint_as_float(e.w), x1, a1);
-      }
-#pragma unroll
-      for (int j = 0; j < SPL; ++j) a[j] = a0[j] + a1[j];
-      if (agg == NEAT_AGG_MEAN && np > 0) {
-        const float cnt = float(2 * np - int((n.meta >> (HN_ROW_BITS + 5)) & 1u));
-#pragma unroll
-        for (int j = 0; j < SPL; ++j) a[j] = a[j] / cnt;
-      }
-    } else if (np == 0) {
-#pragma unroll
-      for (int j = 0; j < SPL; ++j) a[j] = 0.0f;
-    } else if (agg == NEAT_AGG_MAX) {
-      const uint4 e = pp[0];
-      float x0[SPL], x1[SPL];
-      HnVec<SPL>::ld(vb + e.x, x0);
-      HnVec<SPL>::ld(vb + e.z, x1);
-#pragma unroll
-      for (int j = 0; j < SPL; ++j)
-        a[j] = fmaxf(__uint_as_float(e.y) * x0[j], __uint_as_float(e.w) * x1[j]);
-      for (int k = 1; k < np; ++k) {
-        const uint4 f = pp[k];
-        HnVec<SPL>::ld(vb + f.x, x0);
-        HnVec<SPL>::ld(vb + f.z, x1);
-#pragma unroll
-        for (int j = 0; j < SPL; ++j) {
-          a[j] = fmaxf(a[j], __uint_as_float(f.y) * x0[j]);
-          a[j] = fmaxf(a[j], __uint_as_float(f.w) * x1[j]);
-        }
-      }
-    } else {  // product
-#pragma unroll
-      for (int j = 0; j < SPL; ++j) a[j] = 1.0f;
-      for (int k = 0; k < np; ++k) {
-        const uint4 f = pp[k];
-        float x0[SPL], x1[SPL];
-        HnVec<SPL>::ld(vb + f.x, x0);
-        HnVec<SPL>::ld(vb + f.z, x1);
-#pragma unroll
-        for (int j = 0; j < SPL; ++j) {
-          a[j] = a[j] * (__uint_as_float(f.y) * x0[j]);
-          a[j] = a[j] * (__uint_as_float(f.w) * x1[j]);
-        }
-      }
-    }
-#pragma unroll
-    for (int j = 0; j < SPL; ++j) a[j] = fmaf(n.resp, a[j], n.bias);
-    act_apply_n<SPL>(int(n.meta >> HN_ROW_BITS) & 7, a);
-    HnVec<SPL>::st(vb + (n.meta & ((1u << HN_ROW_BITS) - 1u)), a);
-  }
-}
-
-// Stage genome g's program for the query walk (every thread of the CTA calls
-// it; tmp = hn_stage_bytes(V, E) bytes of scratch, 16-byte aligned).
-//  1. copy its node and edge records into tmp;
-//  2. keep only the nodes the output depends on (one warp, reverse program
-//     order: a node is needed when a needed node reads it) - the others
-//     cannot change the output;
-//  3. give each kept node a value row by a linear scan in program order: a
-//     row is released at the last node that reads it (before that node's own
-//     row is taken; a node reads all its inputs before it writes), inputs keep
-//     rows 0-4, the output keeps its row to the end;
-//  4. write the node records and edge pairs (HnNode) with those rows.
-// info[0..2] = staged nodes, rows used, the output's row.
-template <int SPL>
-__device__ void hn_stage(const Ws &w, const GenomeHdr &h, const int32_t *io, HnNode *nodes,
-                         uint4 *pairs, int *s_scan, char *tmp, int *info) {
-  constexpr uint32_t ROWB = 32 * SPL * 4;  // bytes per value row
-  const int V = h.V, E = h.E;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  NodeRec *tn = reinterpret_cast<NodeRec *>(tmp);
-  int *need = reinterpret_cast<int *>(tmp + size_t(V) * 16);
-  int *last = need + V;
-  int *row = last + V;
-  int *fstack = row + V;
-  EdgeRec *te = reinterpret_cast<EdgeRec *>(fstack + V);
-  const NodeRec *nr = w.knode + h.node_off;
-  const EdgeRec *er = w.kedge + h.edge_off;
-  const int po = io[5];
-  for (int i = threadIdx.x; i < V; i += blockDim.x) {
-    tn[i] = ld_node(nr + i);
-    need[i] = w.prune ? i == po : 1;  // without pruning every node is evaluated
-    last[i] = -1;
-    row[i] = -1;
-  }
-  for (int i = threadIdx.x; i < E; i += blockDim.x) te[i] = ld_edge(er + i);
-  __syncthreads();
-  if (wid == 0) {
-    for (int p = V - 1; p >= 0; --p) {
-      const NodeRec n = tn[p];
-      if (need[p] && !(n.meta & META_INPUT))
-        for (int k = lane; k < meta_cnt(n.meta); k += 32) need[te[n.in_begin + k].src] = 1;
-      __syncwarp();
-    }
-    if (lane == 0) {
-      for (int i = 0; i < 5; ++i) row[io[i]] = i;
-      int c = 0;
-      for (int p = 0; p < V; ++p) {  // last reader of every value
-        const NodeRec n = tn[p];
-        if (!need[p] || (n.meta & META_INPUT)) continue;
-        for (int k = 0; k < meta_cnt(n.meta); ++k) last[te[n.in_begin + k].src] = c;
-        ++c;
-      }
-      int sp = 0, next = HN_ROW_FIRST;
-      c = 0;
-      for (int p = 0; p < V; ++p) {
-        const NodeRec n = tn[p];
-        if (!need[p] || (n.meta & META_INPUT)) continue;
-        for (int k = 0; k < meta_cnt(n.meta); ++k) {
-          const int src = te[n.in_begin + k].src;
-          if (last[src] == c && src != po && !(tn[src].meta & META_INPUT)) {
-            fstack[sp++] = row[src];
-            last[src] = -2;  // released once, whatever the duplicates
-          }
-        }
-        row[p] = sp > 0 ? fstack[--sp] : next++;
-        ++c;
-      }
-      info[0] = c;
-      info[1] = next;
-      info[2] = row[po];
-    }
-  }
-  __syncthreads();
-  int carry_n = 0, carry_p = 0;
-  for (int base = 0; base < V; base += blockDim.x) {
-    const int p = base + int(threadIdx.x);
-    NodeRec n{};
-    int keep = 0, np = 0;
-    if (p < V) {
-      n = tn[p];
-      keep = (need[p] && !(n.meta & META_INPUT)) ? 1 : 0;
-      np = keep ? (meta_cnt(n.meta) + 1) >> 1 : 0;
-    }
-    int en, ep, tk, tp;
-    block_scan2(keep, np, en, ep, tk, tp, s_scan);
-    if (keep) {
-      const int c = carry_n + en, pb = carry_p + ep;
-      const int cnt = meta_cnt(n.meta), agg = meta_agg(n.meta);
-      HnNode r;
-      r.bias = n.bias;
-      r.resp = n.resp;
-      r.pairs = uint32_t(pb) * 16u | (uint32_t(np) << HN_PAIR_BITS);
-      r.meta = uint32_t(row[p]) * ROWB | (uint32_t(meta_act(n.meta)) << HN_ROW_BITS) |
-               (uint32_t(agg) << (HN_ROW_BITS + 3)) | (uint32_t(cnt & 1) << (HN_ROW_BITS + 5));
-      nodes[c] = r;
-      const EdgeRec *e = te + n.in_begin;
-      for (int k = 0; k < np; ++k) {
-        const EdgeRec e0 = e[2 * k];
-        uint4 q;
-        q.x = uint32_t(row[e0.src]) * ROWB;
-        q.y = __float_as_uint(e0.w);
-        if (2 * k + 1 < cnt) {
-          const EdgeRec e1 = e[2 * k + 1];
-          q.z = uint32_t(row[e1.src]) * ROWB;
-          q.w = __float_as_uint(e1.w);
-        } else if (agg == NEAT_AGG_MAX) {
-          q.z = q.x;
-          q.w = q.y;
-        } else if (agg == NEAT_AGG_PRODUCT) {
-          q.z = HN_ROW_ONE * ROWB;
-          q.w = __float_as_uint(1.0f);
-        } else {
-          q.z = HN_ROW_ZERO * ROWB;
-          q.w = 0u;
-        }
-        pairs[pb + k] = q;
-      }
-    }
-    carry_n += tk;
-    carry_p += tp;
-  }
-}
+// SPL queries per lane).  The CTA copies the CPPN's compiled program (the
+// transform's: 16-byte node records, 16-byte edge pairs, value rows) into
+// shared memory, and as many of its warps as have room for a value array
+// ([row][32][SPL] floats) walk tiles with the values in shared memory too: one
+// broadcast pair load per two edges, one vector value load and one paired FMA
+// per edge and query lane.  A CPPN whose value array does not fit falls back
+// to the sample-parallel walk over the packed program with values in the
+// warp's workspace slot.
 
 // Query geometry and output of one item
 struct HnTile {
@@ -980,13 +725,12 @@ __global__ void __launch_bounds__(512) k_hyperneat(Ws w, int G, float thresh,
                                                    int smem_bytes) {
   constexpr int RS = 32 * SPL;
   extern __shared__ __align__(16) unsigned char hsm[];
-  __shared__ int s_item, s_info[3];
-  __shared__ int s_scan[64];
+  __shared__ int s_item;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int N = w.N;
+  const int N = w.N, I = w.I;
   const int prog_bytes = hn_prog_bytes(N, w.C);
-  HnNode *s_nodes = reinterpret_cast<HnNode *>(hsm);
-  uint4 *s_pairs = reinterpret_cast<uint4 *>(hsm + size_t(N) * sizeof(HnNode));
+  uint4 *s_nodes = reinterpret_cast<uint4 *>(hsm);  // CNode records
+  uint4 *s_pairs = reinterpret_cast<uint4 *>(hsm + size_t(N) * sizeof(CNode));
   float *s_vals = reinterpret_cast<float *>(hsm + prog_bytes);
   // workspace slots of every warp of this CTA (the fallback walk), or none
   const bool slots_ok = w.sp_scratch != nullptr &&
@@ -1010,15 +754,9 @@ __global__ void __launch_bounds__(512) k_hyperneat(Ws w, int G, float thresh,
     float *wg = weights + size_t(g) * G4;
     const int t0 = chunk * tiles_per_chunk, t1 = min(t0 + tiles_per_chunk, tiles);
     const int32_t *io = w.pio + size_t(g) * 6;
-    // stage when the scratch fits (CTA-uniform), then as many warps as have
-    // room for a value array take tiles
-    const bool can_stage =
-        h.status == 0u && hn_stage_bytes(h.V, h.E) <= smem_bytes - prog_bytes;
-    if (can_stage) hn_stage<SPL>(w, h, io, s_nodes, s_pairs, s_scan,
-                                   reinterpret_cast<char *>(hsm + prog_bytes), s_info);
-    __syncthreads();
-    const int rows = can_stage ? s_info[1] : 0;
-    const int vwarps = can_stage ? min(nw, (smem_bytes - prog_bytes) / (rows * RS * 4)) : 0;
+    // warps with room for a value array of the compiled rows (CTA-uniform)
+    const bool comp = w.cnode != nullptr && h.crows > 0;
+    const int vwarps = comp ? min(nw, (smem_bytes - prog_bytes) / (h.crows * RS * 4)) : 0;
     if (h.status != 0u || (vwarps < 1 && !slots_ok)) {  // CTA-uniform
       if (h.status == 0u && lane == 0) atomicOr(w.counters + CTR_ERR, ERR_SP_NO_SCRATCH);
       for (int qi = t0 * RS + int(threadIdx.x); qi < min(t1 * RS, G4); qi += blockDim.x)
@@ -1027,18 +765,25 @@ __global__ void __launch_bounds__(512) k_hyperneat(Ws w, int G, float thresh,
       continue;
     }
     if (vwarps >= 1) {
+      // the compiled program to shared memory
+      const uint4 *cn = reinterpret_cast<const uint4 *>(w.cnode + size_t(g) * N);
+      const uint4 *cp = w.cpair + size_t(g) * cpair_cap(N, w.C);
+      for (int i = threadIdx.x; i < h.nlive; i += blockDim.x) s_nodes[i] = __ldg(cn + i);
+      for (int i = threadIdx.x; i < h.cpairs; i += blockDim.x) s_pairs[i] = __ldg(cp + i);
+      __syncthreads();
       if (wid < vwarps) {
-        const HnTile t{G, G2, G4, step, inv_g, thresh, 0, 1, 2, 3, 4, s_info[2], wg};
-        float *v = s_vals + size_t(wid) * rows * RS;  // shared memory
-        const int nn = s_info[0];
+        // inputs in rows 0..4, constants 0 and 1 in rows I and I + 1
+        const HnTile t{G, G2, G4, step, inv_g, thresh, 0, 1, 2, 3, 4, w.cout[g], wg};
+        float *v = s_vals + size_t(wid) * h.crows * RS;  // shared memory
 #pragma unroll
         for (int k = 0; k < SPL; ++k) {
-          v[(HN_ROW_ZERO * 32 + lane) * SPL + k] = 0.0f;
-          v[(HN_ROW_ONE * 32 + lane) * SPL + k] = 1.0f;
+          v[(I * 32 + lane) * SPL + k] = 0.0f;
+          v[((I + 1) * 32 + lane) * SPL + k] = 1.0f;
         }
         char *vb = reinterpret_cast<char *>(v + lane * SPL);
+        const CNode *sn = reinterpret_cast<const CNode *>(s_nodes);
         hn_tiles<SPL, true>(t, v, t0 + wid, t1, vwarps,
-                            [&]() { hn_walk<SPL>(s_nodes, nn, s_pairs, vb); });
+                            [&]() { cwalk<SPL, false>(sn, h.nlive, s_pairs, vb); });
       }
     } else {
       const HnTile t{G, G2, G4, step, inv_g, thresh, io[0], io[1], io[2], io[3], io[4], io[5], wg};

@@ -54,7 +54,7 @@ struct __align__(16) GenomeHdr {
   int elive;     // enabled connections into those nodes
   int crows;     // value rows of the compiled program (0: none)
   int clayers;   // layers holding compiled nodes (their first nodes: Ws::clay)
-  int pad;
+  int cpairs;    // edge pairs of the compiled program
 };
 
 // -- compiled program (outputs-only walks) -----------------------------------------
@@ -430,19 +430,14 @@ cudaError_t launch_backward(const Ws &w, const float *inputs, int64_t stride, in
                             float *gr, float *gi, int warps, int smem_bytes, cudaStream_t st);
 size_t backward_smem(int N, int C, int warps);
 // HyperNEAT query: spl queries per lane (1, 2 or 4), `ctas` CTAs of `warps`
-// warps with smem_bytes of dynamic shared memory (>= hn_prog_bytes(N, C)).  A
-// genome whose staging scratch or value array does not fit next to its staged
-// program uses the warp's workspace slot instead (unless every genome fits,
-// ctas * warps <= sp_scratch_slots(w, spl)).
+// warps with smem_bytes of dynamic shared memory (>= hn_prog_bytes(N, C): a
+// compiled program's records and pairs).  A genome whose value array does not
+// fit next to its program uses the warp's workspace slot instead (unless every
+// genome fits, ctas * warps <= sp_scratch_slots(w, spl)).
 __host__ __device__ inline int hn_prog_bytes(int N, int C) {
-  return N * 16 + ((C + N) / 2 + 1) * 16;
+  return N * 16 + cpair_cap(N, C) * 16;
 }
-// Rows of a staged value array: the five CPPN inputs, then constants 0 and 1,
-// then the rows the node values take (at most V - 5 of them).
-constexpr int HN_ROW_ZERO = 5, HN_ROW_ONE = 6, HN_ROW_FIRST = 7;
-// shared-memory scratch the staging needs for a genome of V positions and E
-// enabled connections (copies of its records, four ints per position)
-__host__ __device__ inline int hn_stage_bytes(int V, int E) { return V * 32 + E * 8; }
+
 cudaError_t launch_hyperneat(const Ws &w, int grid, float thresh, float *weights, int spl,
                              int warps, int ctas, int smem_bytes, cudaStream_t st);
 // one-time kernel attributes and occupancy queries (host side)

@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(256) k_transform(Ws w, const float *__restrict
   // 7. padded program (valid genomes only)
   GenomeHdr h;
   h.V = 0; h.E = 0; h.L = 0; h.status = status; h.node_off = 0; h.edge_off = 0;
-  h.nlive = 0; h.nch = 0; h.elive = 0; h.crows = 0; h.clayers = 0; h.pad = 0;
+  h.nlive = 0; h.nch = 0; h.elive = 0; h.crows = 0; h.clayers = 0; h.cpairs = 0;
   if (status == 0u) {
     h.V = V; h.E = E; h.L = t;
     // nodes some output depends on (with pruning on, feed-forward only): the
@@ -457,7 +457,7 @@ __global__ void __launch_bounds__(256) k_transform(Ws w, const float *__restrict
       }
       __syncthreads();
       block_exclusive_scan(cidx, V, wbuf);
-      block_exclusive_scan(pbeg, V, wbuf);
+      h.cpairs = block_exclusive_scan(pbeg, V, wbuf);
       // the outputs keep their rows; every other value is released at its
       // last reader
       for (int i = tid; i < O; i += T) clast[s_of_row[I + i]] = 0x7fffffff;
