@@ -603,10 +603,11 @@ def bench_ours(args, rank, world, local, pg):
         fwd_launches = 1
         ro = None
         # HBM: the padded genomes in, the distance matrix out; on chip: both
-        # genomes' sorted gene lists (16 B a gene) streamed through for every pair
+        # genomes' sorted keys streamed through for every pair (4 B a node
+        # key, 8 B a connection key; the attributes of shared keys on top)
         alg_bytes = float(P * (spec.N * 5 + spec.C * 4) * 4 + 4.0 * P * P)
         M = (~np.isnan(conns[:, :, 0]) & ~np.isnan(conns[:, :, 1])).sum(1)  # connection genes
-        chip_bytes = float(P) * P * 16.0 * 2 * float((Vn + M).mean())
+        chip_bytes = float(P) * P * 2 * (4.0 * float(Vn.mean()) + 8.0 * float(M.mean()))
     elif name == "recurrent":
         S, T = cfg["S"], cfg["T"]
         x = np.random.default_rng(args.seed + rank).standard_normal((P, S, spec.I)).astype(

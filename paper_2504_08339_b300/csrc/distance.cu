@@ -13,8 +13,9 @@
 //  k_dist_prep  one CTA per genome: sorts its node genes by key and its
 //               connection genes by (in, out, row) in shared memory (bitonic),
 //               drops repeated connection keys, writes the sorted gene lists
+//               and their key arrays
 //  k_distance   one thread per pair (16 x 16 pairs per CTA): merges the two
-//               pairs of sorted lists (keys compared as order-preserving
+//               pairs of sorted key arrays (keys compared as order-preserving
 //               integers, so exactly like the float values)
 #include <cuda_runtime.h>
 
@@ -95,6 +96,8 @@ __global__ void __launch_bounds__(256) k_dist_prep(const float *__restrict__ nod
                                                    const uint32_t *__restrict__ gstatus, int N,
                                                    int C, int I, NodeGene *__restrict__ ng,
                                                    ConnGene *__restrict__ cg,
+                                                   uint32_t *__restrict__ nkey,
+                                                   uint64_t *__restrict__ ckey,
                                                    int4 *__restrict__ counts) {
   extern __shared__ __align__(16) unsigned char sm[];
   const int g = blockIdx.x, tid = threadIdx.x, T = blockDim.x;
@@ -165,6 +168,7 @@ __global__ void __launch_bounds__(256) k_dist_prep(const float *__restrict__ nod
     const uint32_t agg = r >= I ? uint32_t(int(row[4]) & 0xff) : 0xffu;
     q.meta = act | (agg << 8) | (uint32_t(r < I) << 16);
     ng[size_t(g) * N + i] = q;
+    nkey[size_t(g) * N + i] = q.key;
   }
   // first row of every (in, out) key
   for (int i = tid; i < C; i += T)
@@ -183,6 +187,7 @@ __global__ void __launch_bounds__(256) k_dist_prep(const float *__restrict__ nod
     q.w = row[2];
     q.en = (!isnan(row[3]) && row[3] != 0.0f) ? 1u : 0u;
     cg[size_t(g) * C + flag[i]] = q;
+    ckey[size_t(g) * C + flag[i]] = uint64_t(q.kin) << 32 | q.kout;
   }
   if (tid == 0) {
     const bool bad = gstatus != nullptr && (gstatus[g] & ~uint32_t(NEAT_G_CYCLE)) != 0u;
@@ -203,8 +208,15 @@ __device__ __forceinline__ ConnGene ld_cg(const ConnGene *p) {
   return q;
 }
 
+// One thread per pair, 16 x 16 pairs per CTA.  The merges step through the
+// genomes' sorted key arrays (node keys 4 B, connection keys 8 B, L1-cached),
+// loading only the key of the side that advances; a shared key loads both
+// genes' attributes for the homologous term.  The sums run in key order, as
+// in the record merge: the same bits, d(a, b) = d(b, a).
 __global__ void __launch_bounds__(256) k_distance(const NodeGene *__restrict__ ng,
                                                   const ConnGene *__restrict__ cg,
+                                                  const uint32_t *__restrict__ nkey,
+                                                  const uint64_t *__restrict__ ckey,
                                                   const int4 *__restrict__ counts, int P, int N,
                                                   int C, float cd, float ch,
                                                   float *__restrict__ dist) {
@@ -213,43 +225,58 @@ __global__ void __launch_bounds__(256) k_distance(const NodeGene *__restrict__ n
   const int4 ca = __ldg(counts + a), cb = __ldg(counts + b);
   float d = qnan();
   if (!ca.z && !cb.z) {
-    // nodes: one step per key of either list (merge)
-    const NodeGene *A = ng + size_t(a) * N, *B = ng + size_t(b) * N;
+    // nodes
+    const uint32_t *A = nkey + size_t(a) * N, *B = nkey + size_t(b) * N;
+    const NodeGene *GA = ng + size_t(a) * N, *GB = ng + size_t(b) * N;
     int i = 0, j = 0, D = 0;
     float H = 0.0f;
-    while (i < ca.x || j < cb.x) {
-      const NodeGene x = ld_ng(A + min(i, ca.x - 1 < 0 ? 0 : ca.x - 1));
-      const NodeGene y = ld_ng(B + min(j, cb.x - 1 < 0 ? 0 : cb.x - 1));
-      const uint32_t kx = i < ca.x ? x.key : KEY_END, ky = j < cb.x ? y.key : KEY_END;
+    uint32_t kx = ca.x > 0 ? __ldg(A) : KEY_END, ky = cb.x > 0 ? __ldg(B) : KEY_END;
+    while (kx != KEY_END || ky != KEY_END) {
       if (kx == ky) {
+        const NodeGene x = ld_ng(GA + i), y = ld_ng(GB + j);
         if (!((x.meta | y.meta) & 0x10000u))
           H += fabsf(x.bias - y.bias) + fabsf(x.resp - y.resp) +
                float((x.meta & 0xffu) != (y.meta & 0xffu)) +
                float(((x.meta >> 8) & 0xffu) != ((y.meta >> 8) & 0xffu));
         ++i;
         ++j;
+        kx = i < ca.x ? __ldg(A + i) : KEY_END;
+        ky = j < cb.x ? __ldg(B + j) : KEY_END;
       } else {
         ++D;
-        if (kx < ky) ++i; else ++j;
+        if (kx < ky) {
+          ++i;
+          kx = i < ca.x ? __ldg(A + i) : KEY_END;
+        } else {
+          ++j;
+          ky = j < cb.x ? __ldg(B + j) : KEY_END;
+        }
       }
     }
     const int nmax = max(ca.x, cb.x);
     d = nmax > 0 ? (cd * float(D) + ch * H) / float(nmax) : 0.0f;
     // connections
-    const ConnGene *X = cg + size_t(a) * C, *Y = cg + size_t(b) * C;
+    const uint64_t *X = ckey + size_t(a) * C, *Y = ckey + size_t(b) * C;
+    const ConnGene *CX = cg + size_t(a) * C, *CY = cg + size_t(b) * C;
     i = 0; j = 0; D = 0; H = 0.0f;
-    while (i < ca.y || j < cb.y) {
-      const ConnGene x = ld_cg(X + min(i, ca.y - 1 < 0 ? 0 : ca.y - 1));
-      const ConnGene y = ld_cg(Y + min(j, cb.y - 1 < 0 ? 0 : cb.y - 1));
-      const uint64_t kx = i < ca.y ? (uint64_t(x.kin) << 32 | x.kout) : ~0ull;
-      const uint64_t ky = j < cb.y ? (uint64_t(y.kin) << 32 | y.kout) : ~0ull;
-      if (kx == ky) {
+    uint64_t qx = ca.y > 0 ? __ldg(X) : ~0ull, qy = cb.y > 0 ? __ldg(Y) : ~0ull;
+    while (qx != ~0ull || qy != ~0ull) {
+      if (qx == qy) {
+        const ConnGene x = ld_cg(CX + i), y = ld_cg(CY + j);
         H += fabsf(x.w - y.w) + float(x.en != y.en);
         ++i;
         ++j;
+        qx = i < ca.y ? __ldg(X + i) : ~0ull;
+        qy = j < cb.y ? __ldg(Y + j) : ~0ull;
       } else {
         ++D;
-        if (kx < ky) ++i; else ++j;
+        if (qx < qy) {
+          ++i;
+          qx = i < ca.y ? __ldg(X + i) : ~0ull;
+        } else {
+          ++j;
+          qy = j < cb.y ? __ldg(Y + j) : ~0ull;
+        }
       }
     }
     const int mmax = max(ca.y, cb.y);
@@ -266,7 +293,7 @@ size_t prep_smem(int N, int C) {
 }
 
 struct DistLayout {
-  size_t ng, cg, counts, total;
+  size_t ng, cg, nkey, ckey, counts, total;
 };
 DistLayout dist_layout(int P, int N, int C) {
   DistLayout L{};
@@ -274,6 +301,8 @@ DistLayout dist_layout(int P, int N, int C) {
   auto take = [&](size_t bytes) { size_t o = off; off = (off + bytes + 255) / 256 * 256; return o; };
   L.ng = take(sizeof(NodeGene) * size_t(P) * N);
   L.cg = take(sizeof(ConnGene) * size_t(P) * C);
+  L.nkey = take(sizeof(uint32_t) * size_t(P) * N);
+  L.ckey = take(sizeof(uint64_t) * size_t(P) * C);
   L.counts = take(sizeof(int4) * size_t(P));
   L.total = off;
   return L;
@@ -307,15 +336,18 @@ extern "C" neat_status neat_distance(const float *nodes, const float *conns,
   char *base = static_cast<char *>(scratch);
   auto *ng = reinterpret_cast<neat::NodeGene *>(base + L.ng);
   auto *cg = reinterpret_cast<neat::ConnGene *>(base + L.cg);
+  auto *nkey = reinterpret_cast<uint32_t *>(base + L.nkey);
+  auto *ckey = reinterpret_cast<uint64_t *>(base + L.ckey);
   auto *counts = reinterpret_cast<int4 *>(base + L.counts);
   const size_t smem = neat::prep_smem(N, C);
   if (cudaFuncSetAttribute(neat::k_dist_prep, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            int(smem)) != cudaSuccess)
     return NEAT_ERR_UNSUPPORTED;
-  neat::k_dist_prep<<<P, 256, smem, stream>>>(nodes, conns, gstatus, N, C, I, ng, cg, counts);
+  neat::k_dist_prep<<<P, 256, smem, stream>>>(nodes, conns, gstatus, N, C, I, ng, cg, nkey, ckey,
+                                               counts);
   if (cudaGetLastError() != cudaSuccess) return NEAT_ERR_CUDA;
   const dim3 grid(unsigned((P + 15) / 16), unsigned((P + 15) / 16)), block(16, 16);
-  neat::k_distance<<<grid, block, 0, stream>>>(ng, cg, counts, P, N, C, c_disjoint, c_homologous,
-                                               dist);
+  neat::k_distance<<<grid, block, 0, stream>>>(ng, cg, nkey, ckey, counts, P, N, C, c_disjoint,
+                                               c_homologous, dist);
   return cudaGetLastError() == cudaSuccess ? NEAT_OK : NEAT_ERR_CUDA;
 }
