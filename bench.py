@@ -779,7 +779,10 @@ def bench_ours(args, rank, world, local, pg):
         d2h = h_out.numel() * 4
         e2e = {"value": allreduce_sum(pg, units_per_step, dev) / (allreduce_max(pg, ems, dev) / 1e3),
                "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
-               "ms_per_step": round(ems, 3), "steps": K}
+               "ms_per_step": round(ems, 3), "steps": K,
+               "form": f"Rollout.run_host: chunks of {ro.chunk} steps, each a graph; input "
+                       "and output copies on two streams overlap the kernels (open loop: "
+                       "every step's inputs are given)"}
 
     if not args.no_e2e and name == "differentiation":
         # through the public differentiable API (torch.autograd.Function):

@@ -614,6 +614,41 @@ def test_cuda_graph_replay_matches_direct_calls():
         assert torch.equal(outs, direct)
 
 
+@pytest.mark.parametrize("name,T,S,ring,chunk", [("locomotion", 23, 1, 23, 5),
+                                                  ("uneven", 9, 33, 4, 2),
+                                                  ("locomotion", 4, 1, 4, 8)])
+def test_rollout_from_host_buffers_matches_device_rollout(name, T, S, ring, chunk):
+    """The pipelined host-buffer rollout (chunks of steps, copies on their own
+    streams) gives the device-resident rollout's outputs bit for bit; chunks
+    that do not divide T, a ring shorter than T and a chunk longer than T;
+    repeated calls reuse the buffers."""
+    from paper_2504_08339_b300.rollout import Rollout
+    P = 300
+    nodes, conns, spec = population_for(name, seed=4, P=P)
+    plan = _plan(spec, P)
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((ring, P, S, spec.I)).astype(np.float32)
+    ro = Rollout(plan, T, S=S, ring=ring, chunk=chunk)
+    ro.load(torch.from_numpy(nodes), torch.from_numpy(conns), torch.from_numpy(x),
+            non_blocking=False)
+    dev_out = ro.run().clone()
+    torch.cuda.synchronize()
+    ro2 = Rollout(plan, T, S=S, ring=ring, chunk=chunk)
+    h_nodes = torch.from_numpy(nodes).pin_memory()
+    h_conns = torch.from_numpy(conns).pin_memory()
+    h_in = torch.from_numpy(x).pin_memory()
+    h_out = torch.full((T, P, S, spec.O), 7.0).pin_memory()
+    for _ in range(2):
+        h_out.fill_(7.0)
+        ro2.run_host(h_nodes, h_conns, h_in, h_out)
+        torch.cuda.synchronize()
+        assert torch.equal(h_out.view(torch.int32), dev_out.cpu().view(torch.int32))
+    # the outputs are the plan's own forward of each step's inputs
+    plan.transform(_dev(nodes), _dev(conns))
+    for t in (0, T - 1):
+        assert torch.equal(h_out[t], plan.forward(_dev(x[t % ring])).cpu())
+
+
 def test_tuning_knobs_and_autotuner(tmp_path, monkeypatch):
     from paper_2504_08339_b300 import NeatError
     from paper_2504_08339_b300.autotune import autotune
