@@ -369,7 +369,7 @@ neat_status neat_forward_recurrent(neat_plan *plan, const float *inputs, int64_t
   if (outputs == nullptr || !aligned(outputs, 4)) return NEAT_ERR_ARG;
   // 8 warps per CTA (the tuning's warps_per_cta if set); two value buffers
   // per warp bound the grid, kept to whole multiples of the SM count
-  const int warps = plan->tune.warps_per_cta > 0 ? plan->tune.warps_per_cta : 16;
+  const int warps = plan->tune.warps_per_cta > 0 ? plan->tune.warps_per_cta : 8;
   const int slots = neat::sp_scratch_slots(plan->w, 2);
   const int occ = std::max(1, neat::forward_rec_occupancy(warps));
   const int64_t items = int64_t(plan->P) * ((S + 31) / 32);
