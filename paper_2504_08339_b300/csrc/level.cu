@@ -484,9 +484,23 @@ __global__ void __launch_bounds__(256) k_forward_lvl(Ws w, const float *__restri
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb1) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  // the step's inputs towards L2, one 128-byte line per thread of the grid
+  // (every address inside the inputs): the batches' input loads then hit L2
+  if (stride >= 0) {
+    const size_t total = size_t(w.P - 1) * size_t(stride) + size_t(S) * I;
+    const size_t lines = (total + 31) / 32;
+    for (size_t l = size_t(blockIdx.x) * blockDim.x + tid; l < lines;
+         l += size_t(gridDim.x) * blockDim.x)
+      asm volatile("prefetch.L2 [%0];" ::"l"(inputs + l * 32));
+  }
   uint32_t parity = 0;
+  // the first batch of each CTA is its own index, later ones are claimed in
+  // order of finishing: no contended atomic at the start of the launch
+  bool first = true;
   for (;;) {
-    if (tid == 0) s_b = int(atomicAdd(w.counters + CTR_LVL_ITEM, 1u));
+    if (tid == 0)
+      s_b = first ? int(blockIdx.x) : int(gridDim.x + atomicAdd(w.counters + CTR_LVL_ITEM, 1u));
+    first = false;
     __syncthreads();
     const int b = s_b;
     if (b >= nbatch) break;
