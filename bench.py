@@ -16,13 +16,15 @@ for the population's programs, which a rollout re-reads by design.
 Legs of the JSON line:
   value        device-resident throughput over K timed steps (CUDA events)
   e2e          same metric through the public Rollout API from pinned host
-               buffers (H2D population + inputs, D2H outputs inside the timing)
+               buffers (H2D population + inputs, D2H outputs inside the timing,
+               pipelined by chunks of steps so the copies overlap the kernels)
   roofline     forward kernel: algorithmic bytes / average launch duration
   plain        the padded one-launch-per-step form on the same workload
   cpu_baseline the FP64 oracle on the host cores, on a bounded sample
 
---impl reference times the FP64 oracle (the reference of this build) on the
-same workload, one bounded sample per step.
+--impl reference times the FP64 oracle (the method's reference is the paper's
+text, so the plain definition written out is the comparison arm) on the same
+workload, one bounded sample per step.
 """
 from __future__ import annotations
 
