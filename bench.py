@@ -345,11 +345,50 @@ def describe(name, cfg, spec):
 
 
 # ---------------------------------------------------------------------------
-def cpu_baseline(name, cfg, spec, nodes, conns, seed, budget_steps=None):
-    """The FP64 oracle as it stands (single thread) on a bounded sample."""
+def accuracy(g, r, bound=None):
+    """Error of the GPU results g against the FP64 oracle's r: max absolute
+    error, max relative error (over |r| >= 1e-3), the elements beyond the
+    stated tolerance (1e-5 relative + 1e-6 absolute) and, with the oracle's
+    fp32 error bound, those beyond max(tolerance, 2 x bound) -- the parity
+    tests' criterion (0 expected)."""
+    g = np.asarray(g, np.float64)
+    r = np.asarray(r, np.float64)
+    fin = np.isfinite(r)
+    same_nf = (np.isnan(g) & np.isnan(r)) | (g == r)
+    err = np.abs(g - r)
+    ar = np.abs(r)
+    tol = 1e-6 + 1e-5 * ar
+    big = fin & (ar >= 1e-3)
+    res = {"n": int(fin.sum()),
+           "max_abs_err": float(err[fin].max()) if fin.any() else 0.0,
+           "max_rel_err": float((err[big] / ar[big]).max()) if big.any() else 0.0,
+           "beyond_tolerance": int((fin & (err > tol)).sum()),
+           "nonfinite_mismatch": int((~fin & ~same_nf).sum())}
+    if bound is not None:
+        lim = np.maximum(tol, 2.0 * np.asarray(bound, np.float64))
+        res["beyond_bound"] = int((fin & (err > lim)).sum())
+    return res
+
+
+def grad_accuracy(g, r):
+    """Gradients: max error relative to each genome's largest |gradient|."""
+    g = np.asarray(g, np.float64).reshape(r.shape[0], -1)
+    r = np.asarray(r, np.float64).reshape(r.shape[0], -1)
+    scale = np.maximum(np.abs(r).max(axis=1, keepdims=True), 1e-30)
+    rel = np.abs(g - r) / scale
+    return {"n": int(r.size), "max_err_rel_to_genome_max": float(rel.max()),
+            "beyond_1e-4": int((rel > 1e-4).sum())}
+
+
+def cpu_baseline(name, cfg, spec, nodes, conns, seed, budget_steps=None, gpu=None):
+    """The FP64 oracle as it stands (single thread) on a bounded sample; with
+    `gpu` (callables returning the GPU's results for the same sample) also
+    the GPU's error against it, outside the timing."""
     import oracle
     from workloads import locomotion_inputs, regression_batch, uneven_inputs
     E, _ = enabled_counts(nodes, conns)
+    gpu = gpu or {}
+    acc = None
     t0 = time.perf_counter()
     if name == "locomotion":
         R = budget_steps or 200
@@ -358,6 +397,10 @@ def cpu_baseline(name, cfg, spec, nodes, conns, seed, budget_steps=None):
         oracle.forward(nodes, conns, x, spec.I, spec.O)
         units = float(E.sum()) * R
         sample = f"all {cfg['P']} genomes x {R} of the {cfg['steps']} rollout steps"
+        if "out" in gpu:
+            dt = time.perf_counter() - t0
+            ref, bnd = oracle.forward(nodes, conns, x, spec.I, spec.O, with_bound=True)
+            acc = {"outputs": accuracy(gpu["out"](R), ref, bnd)}
     elif name == "uneven":
         k = budget_steps or 1500
         sel = np.arange(k)
@@ -366,15 +409,29 @@ def cpu_baseline(name, cfg, spec, nodes, conns, seed, budget_steps=None):
         oracle.forward(nodes[sel], conns[sel], x, spec.I, spec.O)
         units = float(E[sel].sum()) * cfg["S"]
         sample = f"{k} of {cfg['P']} genomes x 1 step (S={cfg['S']})"
+        if "out" in gpu:
+            dt = time.perf_counter() - t0
+            ref, bnd = oracle.forward(nodes[sel], conns[sel], x, spec.I, spec.O, with_bound=True)
+            acc = {"outputs": accuracy(gpu["out"](k), ref, bnd)}
     elif name == "differentiation":
         k = budget_steps or (64 if cfg["S"] <= 4096 else 4)
         x, y = regression_batch(seed, cfg["S"])
         t0 = time.perf_counter()
         out = oracle.forward(nodes[:k], conns[:k], x, spec.I, spec.O)
         go = (2.0 / cfg["S"]) * (out[..., 0] - y[None].astype(np.float64))
-        oracle.backward(nodes[:k], conns[:k], x, spec.I, spec.O, go[..., None], want_inputs=True)
+        grads = oracle.backward(nodes[:k], conns[:k], x, spec.I, spec.O, go[..., None],
+                                want_inputs=True)
         units = float(E[:k].sum()) * cfg["S"]
         sample = f"{k} of {cfg['P']} genomes, forward + backward at S={cfg['S']}"
+        if "out" in gpu:
+            dt = time.perf_counter() - t0
+            _, bnd = oracle.forward(nodes[:k], conns[:k], x, spec.I, spec.O, with_bound=True)
+            acc = {"outputs": accuracy(gpu["out"](k), out, bnd)}
+            gg = gpu["grads"](k)
+            for nm, a_, b_ in zip(("grad_weight", "grad_bias", "grad_response", "grad_inputs"),
+                                  gg, grads):
+                if a_ is not None and b_ is not None and np.size(a_) == np.size(b_):
+                    acc[nm] = grad_accuracy(a_, b_)
     elif name == "substrate":
         k = budget_steps or 1
         G, S = 32, 64
@@ -393,18 +450,27 @@ def cpu_baseline(name, cfg, spec, nodes, conns, seed, budget_steps=None):
         n2, c2, _ = oracle.apply_ops(nodes[:k], conns[:k], ops)
         oracle.transform(n2, c2, spec.I, spec.O)
         dt = time.perf_counter() - t0
-        return {"value": k / dt, "unit": "genomes/s", "cores": 1, "kind": "oracle",
-                "sample": f"{k} of {cfg['P']} genomes: 16 operations + transform",
-                "seconds": round(dt, 3)}
+        res = {"value": k / dt, "unit": "genomes/s", "cores": 1, "kind": "oracle",
+               "sample": f"{k} of {cfg['P']} genomes: 16 operations + transform",
+               "seconds": round(dt, 3)}
+        if "pop" in gpu:
+            gn, gc = gpu["pop"](k)
+            same = lambda a, b: ((a == b) | (np.isnan(a) & np.isnan(b))).reshape(k, -1).all(1)  # noqa: E731
+            res["gpu_vs_oracle"] = {"genomes": k, "nodes_bit_exact": int(same(gn, n2).sum()),
+                                    "conns_bit_exact": int(same(gc, c2).sum())}
+        return res
     elif name == "distance":
         k = budget_steps or 300
         t0 = time.perf_counter()
-        oracle.distance(nodes[:k], conns[:k], spec.I, spec.O)
+        ref = oracle.distance(nodes[:k], conns[:k], spec.I, spec.O)
         units = float(k) * k
         sample = f"all pairs of {k} of {cfg['P']} genomes"
         dt = time.perf_counter() - t0
-        return {"value": units / dt, "unit": "genome-pairs/s", "cores": 1, "kind": "oracle",
-                "sample": sample, "seconds": round(dt, 3)}
+        res = {"value": units / dt, "unit": "genome-pairs/s", "cores": 1, "kind": "oracle",
+               "sample": sample, "seconds": round(dt, 3)}
+        if "dist" in gpu:
+            res["gpu_vs_oracle"] = {"distances": accuracy(gpu["dist"](k), ref)}
+        return res
     elif name == "recurrent":
         k = budget_steps or 300
         x = np.random.default_rng(seed).standard_normal((k, cfg["S"], spec.I)).astype(np.float32)
@@ -412,6 +478,11 @@ def cpu_baseline(name, cfg, spec, nodes, conns, seed, budget_steps=None):
         oracle.forward_recurrent(nodes[:k], conns[:k], x, spec.I, spec.O, cfg["T"])
         units = float(E[:k].sum()) * cfg["S"] * cfg["T"]
         sample = f"{k} of {cfg['P']} genomes x S={cfg['S']} x T={cfg['T']}"
+        if "out" in gpu:
+            dt = time.perf_counter() - t0
+            ref, bnd = oracle.forward_recurrent(nodes[:k], conns[:k], x, spec.I, spec.O,
+                                                cfg["T"], with_bound=True)
+            acc = {"outputs": accuracy(gpu["out"](k), ref, bnd)}
     elif name == "hyperneat":
         k = budget_steps or 2
         q = np.arange(32 ** 4 // 4)
@@ -419,6 +490,19 @@ def cpu_baseline(name, cfg, spec, nodes, conns, seed, budget_steps=None):
         oracle.hyperneat(nodes[:k], conns[:k], grid=32, qidx=q)
         units = float(E[:k].sum()) * q.size
         sample = f"{k} of {cfg['P']} CPPNs x a quarter of the 2^20 queries"
+        if "weights" in gpu:
+            dt = time.perf_counter() - t0
+            ref, raw, bnd = oracle.hyperneat(nodes[:k], conns[:k], grid=32,
+                                             thresh=cfg["thresh"], qidx=q, with_raw=True,
+                                             with_bound=True)
+            g = gpu["weights"](k, q)
+            # queries whose raw value lies within the error band of the
+            # threshold may be kept or zeroed either way: left out
+            near = np.abs(np.abs(raw) - cfg["thresh"]) <= np.maximum(1e-6 + 1e-5 * np.abs(raw),
+                                                                      2 * bnd)
+            acc = {"weights": accuracy(np.where(near, 0.0, g), np.where(near, 0.0, ref),
+                                       np.where(near, 0.0, bnd)),
+                   "threshold_ties_left_out": int(near.sum())}
     else:
         from workloads import xor_inputs
         t0 = time.perf_counter()
@@ -426,9 +510,17 @@ def cpu_baseline(name, cfg, spec, nodes, conns, seed, budget_steps=None):
             oracle.forward(nodes, conns, xor_inputs(), spec.I, spec.O)
         units = float(E.sum()) * 4 * 200
         sample = "200 repetitions of the whole population"
-    dt = time.perf_counter() - t0
-    return {"value": units / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
-            "seconds": round(dt, 3)}
+        if "out" in gpu:
+            dt = time.perf_counter() - t0
+            ref, bnd = oracle.forward(nodes, conns, xor_inputs(), spec.I, spec.O, with_bound=True)
+            acc = {"outputs": accuracy(gpu["out"](None), ref, bnd)}
+    if acc is None:
+        dt = time.perf_counter() - t0
+    res = {"value": units / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+           "seconds": round(dt, 3)}
+    if acc is not None:
+        res["gpu_vs_oracle"] = acc
+    return res
 
 
 # ---------------------------------------------------------------------------
@@ -836,7 +928,27 @@ def bench_ours(args, rank, world, local, pg):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        cpu = cpu_baseline(name, cfg, spec, nodes, conns, args.seed)
+        # the GPU's results for the oracle's sample, read after the timing
+        gpu = {}
+        np_ = lambda t: t.float().cpu().numpy()  # noqa: E731
+        if name == "locomotion":
+            gpu["out"] = lambda R: np_(ro.outputs[:R, :, 0, :].permute(1, 0, 2))
+        elif name == "uneven":
+            gpu["out"] = lambda k: np_(ro.outputs[0][:k])
+        elif name == "tiny":
+            gpu["out"] = lambda _: np_(ro.outputs[0])
+        elif name == "differentiation":
+            gpu["out"] = lambda k: np_(out[:k])
+            gpu["grads"] = lambda k: [None if t is None else np_(t[:k]) for t in run()]
+        elif name == "recurrent":
+            gpu["out"] = lambda k: np_(out[:k])
+        elif name == "hyperneat":
+            gpu["weights"] = lambda k, q: np_(w[:k].reshape(k, -1)[:, torch.from_numpy(q).to(dev)])
+        elif name == "distance":
+            gpu["dist"] = lambda k: np_(dist[:k, :k])
+        elif name == "mutate":
+            gpu["pop"] = lambda k: (np_(d_nodes[:k]), np_(d_conns[:k]))
+        cpu = cpu_baseline(name, cfg, spec, nodes, conns, args.seed, gpu=gpu)
 
     gpu_launches = launches_per_step * args.steps
     line = {
