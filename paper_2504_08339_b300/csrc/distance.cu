@@ -14,9 +14,14 @@
 //               connection genes by (in, out, row) in shared memory (bitonic),
 //               drops repeated connection keys, writes the sorted gene lists
 //               and their key arrays
-//  k_distance   one thread per pair (16 x 16 pairs per CTA): merges the two
-//               pairs of sorted key arrays (keys compared as order-preserving
-//               integers, so exactly like the float values)
+//  k_dist_hist, k_dist_scan, k_dist_scatter
+//               a counting sort of the genomes by connection-gene count, so
+//               that the pairs of a warp have genomes of like sizes and their
+//               merge loops run about equally long
+//  k_distance   one thread per pair (16 x 16 pairs per CTA, genomes taken in
+//               that size order): merges the two pairs of sorted key arrays
+//               (keys compared as order-preserving integers, so exactly like
+//               the float values)
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -213,15 +218,41 @@ __device__ __forceinline__ ConnGene ld_cg(const ConnGene *p) {
 // loading only the key of the side that advances; a shared key loads both
 // genes' attributes for the homologous term.  The sums run in key order, as
 // in the record merge: the same bits, d(a, b) = d(b, a).
+// size bucket of a genome: its connection-gene count (0 for a malformed one)
+__device__ __forceinline__ int dist_bucket(const int4 c, int C) { return c.z ? 0 : min(c.y, C); }
+
+__global__ void __launch_bounds__(256) k_dist_hist(const int4 *__restrict__ counts, int P, int C,
+                                                   int *__restrict__ hist) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < P) atomicAdd(hist + dist_bucket(counts[g], C), 1);
+}
+
+// exclusive scan of the C + 1 bucket counts in place (one CTA)
+__global__ void __launch_bounds__(1024) k_dist_scan(int *hist, int n) {
+  __shared__ int wsum[32];
+  cta_scan(hist, n, wsum);
+}
+
+// perm[k] = the genome at size rank k (the order inside a bucket is that of
+// the atomics; the distances do not depend on it)
+__global__ void __launch_bounds__(256) k_dist_scatter(const int4 *__restrict__ counts, int P,
+                                                      int C, int *__restrict__ hist,
+                                                      int *__restrict__ perm) {
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g < P) perm[atomicAdd(hist + dist_bucket(counts[g], C), 1)] = g;
+}
+
 __global__ void __launch_bounds__(256) k_distance(const NodeGene *__restrict__ ng,
                                                   const ConnGene *__restrict__ cg,
                                                   const uint32_t *__restrict__ nkey,
                                                   const uint64_t *__restrict__ ckey,
-                                                  const int4 *__restrict__ counts, int P, int N,
+                                                  const int4 *__restrict__ counts,
+                                                  const int *__restrict__ perm, int P, int N,
                                                   int C, float cd, float ch,
                                                   float *__restrict__ dist) {
-  const int b = blockIdx.x * 16 + threadIdx.x, a = blockIdx.y * 16 + threadIdx.y;
-  if (a >= P || b >= P) return;
+  const int rb = blockIdx.x * 16 + threadIdx.x, ra = blockIdx.y * 16 + threadIdx.y;
+  if (ra >= P || rb >= P) return;
+  const int a = __ldg(perm + ra), b = __ldg(perm + rb);
   const int4 ca = __ldg(counts + a), cb = __ldg(counts + b);
   float d = qnan();
   if (!ca.z && !cb.z) {
@@ -293,7 +324,7 @@ size_t prep_smem(int N, int C) {
 }
 
 struct DistLayout {
-  size_t ng, cg, nkey, ckey, counts, total;
+  size_t ng, cg, nkey, ckey, counts, hist, perm, total;
 };
 DistLayout dist_layout(int P, int N, int C) {
   DistLayout L{};
@@ -304,6 +335,8 @@ DistLayout dist_layout(int P, int N, int C) {
   L.nkey = take(sizeof(uint32_t) * size_t(P) * N);
   L.ckey = take(sizeof(uint64_t) * size_t(P) * C);
   L.counts = take(sizeof(int4) * size_t(P));
+  L.hist = take(sizeof(int) * size_t(C + 1));
+  L.perm = take(sizeof(int) * size_t(P));
   L.total = off;
   return L;
 }
@@ -339,6 +372,8 @@ extern "C" neat_status neat_distance(const float *nodes, const float *conns,
   auto *nkey = reinterpret_cast<uint32_t *>(base + L.nkey);
   auto *ckey = reinterpret_cast<uint64_t *>(base + L.ckey);
   auto *counts = reinterpret_cast<int4 *>(base + L.counts);
+  auto *hist = reinterpret_cast<int *>(base + L.hist);
+  auto *perm = reinterpret_cast<int *>(base + L.perm);
   const size_t smem = neat::prep_smem(N, C);
   if (cudaFuncSetAttribute(neat::k_dist_prep, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            int(smem)) != cudaSuccess)
@@ -346,8 +381,15 @@ extern "C" neat_status neat_distance(const float *nodes, const float *conns,
   neat::k_dist_prep<<<P, 256, smem, stream>>>(nodes, conns, gstatus, N, C, I, ng, cg, nkey, ckey,
                                                counts);
   if (cudaGetLastError() != cudaSuccess) return NEAT_ERR_CUDA;
+  if (cudaMemsetAsync(hist, 0, sizeof(int) * size_t(C + 1), stream) != cudaSuccess)
+    return NEAT_ERR_CUDA;
+  const unsigned gb = unsigned((P + 255) / 256);
+  neat::k_dist_hist<<<gb, 256, 0, stream>>>(counts, P, C, hist);
+  neat::k_dist_scan<<<1, 1024, 0, stream>>>(hist, C + 1);
+  neat::k_dist_scatter<<<gb, 256, 0, stream>>>(counts, P, C, hist, perm);
+  if (cudaGetLastError() != cudaSuccess) return NEAT_ERR_CUDA;
   const dim3 grid(unsigned((P + 15) / 16), unsigned((P + 15) / 16)), block(16, 16);
-  neat::k_distance<<<grid, block, 0, stream>>>(ng, cg, nkey, ckey, counts, P, N, C, c_disjoint,
-                                               c_homologous, dist);
+  neat::k_distance<<<grid, block, 0, stream>>>(ng, cg, nkey, ckey, counts, perm, P, N, C,
+                                               c_disjoint, c_homologous, dist);
   return cudaGetLastError() == cudaSuccess ? NEAT_OK : NEAT_ERR_CUDA;
 }
