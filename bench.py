@@ -697,11 +697,13 @@ def bench_ours(args, rank, world, local, pg):
         fwd_launches = 1
         ro = None
         # HBM: the padded genomes in, the distance matrix out; on chip: both
-        # genomes' sorted keys streamed through for every pair (4 B a node
-        # key, 8 B a connection key; the attributes of shared keys on top)
+        # genomes' sorted keys streamed through once per unordered pair (the
+        # distance is symmetric: P (P + 1) / 2 merges for the P^2 entries; 4 B
+        # a node key, 8 B a connection key; the attributes of shared keys on
+        # top)
         alg_bytes = float(P * (spec.N * 5 + spec.C * 4) * 4 + 4.0 * P * P)
         M = (~np.isnan(conns[:, :, 0]) & ~np.isnan(conns[:, :, 1])).sum(1)  # connection genes
-        chip_bytes = float(P) * P * 2 * (4.0 * float(Vn.mean()) + 8.0 * float(M.mean()))
+        chip_bytes = (float(P) * (P + 1) / 2) * 2 * (4.0 * float(Vn.mean()) + 8.0 * float(M.mean()))
     elif name == "recurrent":
         S, T = cfg["S"], cfg["T"]
         x = np.random.default_rng(args.seed + rank).standard_normal((P, S, spec.I)).astype(

@@ -18,10 +18,11 @@
 //               a counting sort of the genomes by connection-gene count, so
 //               that the pairs of a warp have genomes of like sizes and their
 //               merge loops run about equally long
-//  k_distance   one thread per pair (16 x 16 pairs per CTA, genomes taken in
-//               that size order): merges the two pairs of sorted key arrays
-//               (keys compared as order-preserving integers, so exactly like
-//               the float values)
+//  k_distance   one thread per unordered pair (16 x 16 pairs per CTA, tiles
+//               on or above the diagonal, genomes taken in that size order):
+//               merges the two pairs of sorted key arrays (keys compared as
+//               order-preserving integers, so exactly like the float values)
+//               and writes both entries of the symmetric matrix
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -250,8 +251,12 @@ __global__ void __launch_bounds__(256) k_distance(const NodeGene *__restrict__ n
                                                   const int *__restrict__ perm, int P, int N,
                                                   int C, float cd, float ch,
                                                   float *__restrict__ dist) {
+  // the merge is symmetric in its two genomes (the same keys in the same
+  // order, |x - y| = |y - x|): only tiles on or above the diagonal run, and
+  // each pair writes both of its entries
+  if (blockIdx.y > blockIdx.x) return;
   const int rb = blockIdx.x * 16 + threadIdx.x, ra = blockIdx.y * 16 + threadIdx.y;
-  if (ra >= P || rb >= P) return;
+  if (ra >= P || rb >= P || rb < ra) return;
   const int a = __ldg(perm + ra), b = __ldg(perm + rb);
   const int4 ca = __ldg(counts + a), cb = __ldg(counts + b);
   float d = qnan();
@@ -314,6 +319,7 @@ __global__ void __launch_bounds__(256) k_distance(const NodeGene *__restrict__ n
     if (mmax > 0) d += (cd * float(D) + ch * H) / float(mmax);
   }
   dist[size_t(a) * P + b] = d;
+  dist[size_t(b) * P + a] = d;
 }
 
 size_t prep_smem(int N, int C) {
