@@ -53,10 +53,10 @@ PEAKS_FALLBACK = {"hbm_gbs": 6400.0, "source": "fallback"}
 # while those sources are unchanged.
 _INTERNAL = ("paper_2504_08339_b300/csrc/neat_internal.cuh", "b0c429a08cd68ae5")
 TRAFFIC = {
-    ("locomotion", "k_forward_lvl"): (6492416, 2000, dict([
-        ("paper_2504_08339_b300/csrc/level.cu", "7b97e9f49079d9b1"), _INTERNAL])),
-    ("uneven", "k_forward_sp"): (107732992, 2048, dict([
-        ("paper_2504_08339_b300/csrc/forward.cu", "9dbf046bcf7a9410"), _INTERNAL])),
+    ("locomotion", "k_forward_lvl"): (6490880, 2000, dict([
+        ("paper_2504_08339_b300/csrc/level.cu", "613a45af98c30e3a"), _INTERNAL])),
+    ("uneven", "k_forward_sp"): (107699456, 2048, dict([
+        ("paper_2504_08339_b300/csrc/forward.cu", "dbf8a64f8cc70842"), _INTERNAL])),
     ("differentiation", "k_backward"): (359940608, 512, dict([
         ("paper_2504_08339_b300/csrc/backward.cu", "4363b84f35c1616c"), _INTERNAL])),
 }

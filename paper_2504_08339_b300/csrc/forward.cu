@@ -20,6 +20,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <type_traits>
 
 #include "neat_internal.cuh"
 
@@ -241,29 +242,71 @@ __device__ __forceinline__ void hn_fma(float w, const float (&x)[SPL], float (&a
   }
 }
 
-// Walk of a compiled program (CNode records and edge pairs; see
-// neat_internal.cuh) for this lane's SPL samples.  vb = the warp's value array
-// + lane * SPL floats (bytes); value row r of it at vb + r * 128 * SPL
-// ([row][32 lanes][SPL]: one vector access per row and lane).  GLOBAL: the
-// records come from global memory (read-only path), else from shared memory.
-// Per node: a 16-byte record; per two edges: one 16-byte pair; per edge and
-// sample: one value and one FMA.  Sum and mean keep even edges in a0 and odd
-// edges in a1, the rounding order of the position walk.
+// Addresses of a walk's records and values: generic 64-bit pointers when they
+// live in global memory (GLOBAL: records through the read-only path, values
+// in the workspace slots), 32-bit shared-window addresses when both are
+// staged in shared memory (explicit shared-space instructions: fewer address
+// instructions than generic accesses; volatile with a memory clobber, so
+// they keep their order with the walk's other shared accesses).
+template <bool GLOBAL>
+using waddr_t = std::conditional_t<GLOBAL, const char *, uint32_t>;
+template <bool GLOBAL>
+__device__ __forceinline__ waddr_t<GLOBAL> waddr(const void *p) {
+  if constexpr (GLOBAL) return static_cast<const char *>(p);
+  else return uint32_t(__cvta_generic_to_shared(p));
+}
+template <bool GLOBAL>
+__device__ __forceinline__ uint4 w_ld16(waddr_t<GLOBAL> a) {
+  if constexpr (GLOBAL) {
+    return __ldg(reinterpret_cast<const uint4 *>(a));
+  } else {
+    uint4 r;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                 : "r"(a)
+                 : "memory");
+    return r;
+  }
+}
 template <int SPL, bool GLOBAL>
-__device__ __forceinline__ uint4 ld_rec(const uint4 *p) {
-  if constexpr (GLOBAL) return __ldg(p);
-  return *p;
+__device__ __forceinline__ void w_ldv(waddr_t<GLOBAL> a, float (&x)[SPL]) {
+  if constexpr (GLOBAL) {
+    HnVec<SPL>::ld(a, x);
+  } else if constexpr (SPL == 1) {
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(x[0]) : "r"(a) : "memory");
+  } else if constexpr (SPL == 2) {
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(x[0]), "=f"(x[1]) : "r"(a) : "memory");
+  } else {
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(x[0]), "=f"(x[1]), "=f"(x[2]), "=f"(x[3])
+                 : "r"(a)
+                 : "memory");
+  }
+}
+template <int SPL, bool GLOBAL>
+__device__ __forceinline__ void w_stv(waddr_t<GLOBAL> a, const float (&x)[SPL]) {
+  if constexpr (GLOBAL) {
+    HnVec<SPL>::st(const_cast<char *>(a), x);
+  } else if constexpr (SPL == 1) {
+    asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(x[0]) : "memory");
+  } else if constexpr (SPL == 2) {
+    asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(a), "f"(x[0]), "f"(x[1]) : "memory");
+  } else {
+    asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(x[0]), "f"(x[1]),
+                 "f"(x[2]), "f"(x[3])
+                 : "memory");
+  }
 }
 
 // One compiled node (its 16-byte record nraw) for this lane's SPL samples.
 template <int SPL, bool GLOBAL>
-__device__ __forceinline__ void cnode_eval(const uint4 nraw, const uint4 *__restrict__ pairs,
-                                           char *vb) {
+__device__ __forceinline__ void cnode_eval(const uint4 nraw, const waddr_t<GLOBAL> pairs,
+                                           const waddr_t<GLOBAL> vb) {
   constexpr int SH = 7 + (SPL == 4 ? 2 : (SPL == 2 ? 1 : 0));
   const float bias = __uint_as_float(nraw.x), resp = __uint_as_float(nraw.y);
   const uint32_t meta = nraw.w;
   const int np = int(nraw.z >> CN_PAIR_BITS);
-  const uint4 *pp = pairs + (nraw.z & ((1u << CN_PAIR_BITS) - 1u));
+  const waddr_t<GLOBAL> pp = pairs + 16u * (nraw.z & ((1u << CN_PAIR_BITS) - 1u));
   const int agg = int(meta >> (CN_ROW_BITS + 3)) & 3;
   float a[SPL];
   if (agg == NEAT_AGG_SUM || agg == NEAT_AGG_MEAN) {
@@ -272,10 +315,10 @@ __device__ __forceinline__ void cnode_eval(const uint4 nraw, const uint4 *__rest
     for (int j = 0; j < SPL; ++j) a0[j] = a1[j] = 0.0f;
 #pragma unroll 2
     for (int k = 0; k < np; ++k) {
-      const uint4 e = ld_rec<SPL, GLOBAL>(pp + k);
+      const uint4 e = w_ld16<GLOBAL>(pp + 16u * uint32_t(k));
       float x0[SPL], x1[SPL];
-      HnVec<SPL>::ld(vb + (e.x << SH), x0);
-      HnVec<SPL>::ld(vb + (e.z << SH), x1);
+      w_ldv<SPL, GLOBAL>(vb + (e.x << SH), x0);
+      w_ldv<SPL, GLOBAL>(vb + (e.z << SH), x1);
       hn_fma<SPL>(__uint_as_float(e.y), x0, a0);
       hn_fma<SPL>(__uint_as_float(e.w), x1, a1);
     }
@@ -290,17 +333,17 @@ __device__ __forceinline__ void cnode_eval(const uint4 nraw, const uint4 *__rest
 #pragma unroll
     for (int j = 0; j < SPL; ++j) a[j] = 0.0f;
   } else if (agg == NEAT_AGG_MAX) {
-    const uint4 e = ld_rec<SPL, GLOBAL>(pp);
+    const uint4 e = w_ld16<GLOBAL>(pp);
     float x0[SPL], x1[SPL];
-    HnVec<SPL>::ld(vb + (e.x << SH), x0);
-    HnVec<SPL>::ld(vb + (e.z << SH), x1);
+    w_ldv<SPL, GLOBAL>(vb + (e.x << SH), x0);
+    w_ldv<SPL, GLOBAL>(vb + (e.z << SH), x1);
 #pragma unroll
     for (int j = 0; j < SPL; ++j)
       a[j] = fmaxf(__uint_as_float(e.y) * x0[j], __uint_as_float(e.w) * x1[j]);
     for (int k = 1; k < np; ++k) {
-      const uint4 f = ld_rec<SPL, GLOBAL>(pp + k);
-      HnVec<SPL>::ld(vb + (f.x << SH), x0);
-      HnVec<SPL>::ld(vb + (f.z << SH), x1);
+      const uint4 f = w_ld16<GLOBAL>(pp + 16u * uint32_t(k));
+      w_ldv<SPL, GLOBAL>(vb + (f.x << SH), x0);
+      w_ldv<SPL, GLOBAL>(vb + (f.z << SH), x1);
 #pragma unroll
       for (int j = 0; j < SPL; ++j) {
         a[j] = fmaxf(a[j], __uint_as_float(f.y) * x0[j]);
@@ -311,10 +354,10 @@ __device__ __forceinline__ void cnode_eval(const uint4 nraw, const uint4 *__rest
 #pragma unroll
     for (int j = 0; j < SPL; ++j) a[j] = 1.0f;
     for (int k = 0; k < np; ++k) {
-      const uint4 f = ld_rec<SPL, GLOBAL>(pp + k);
+      const uint4 f = w_ld16<GLOBAL>(pp + 16u * uint32_t(k));
       float x0[SPL], x1[SPL];
-      HnVec<SPL>::ld(vb + (f.x << SH), x0);
-      HnVec<SPL>::ld(vb + (f.z << SH), x1);
+      w_ldv<SPL, GLOBAL>(vb + (f.x << SH), x0);
+      w_ldv<SPL, GLOBAL>(vb + (f.z << SH), x1);
 #pragma unroll
       for (int j = 0; j < SPL; ++j) {
         a[j] = a[j] * (__uint_as_float(f.y) * x0[j]);
@@ -325,23 +368,24 @@ __device__ __forceinline__ void cnode_eval(const uint4 nraw, const uint4 *__rest
 #pragma unroll
   for (int j = 0; j < SPL; ++j) a[j] = fmaf(resp, a[j], bias);
   act_apply_n<SPL>(int(meta >> CN_ROW_BITS) & 7, a);
-  HnVec<SPL>::st(vb + ((meta & ((1u << CN_ROW_BITS) - 1u)) << SH), a);
+  w_stv<SPL, GLOBAL>(vb + ((meta & ((1u << CN_ROW_BITS) - 1u)) << SH), a);
 }
 
 // Walk of a compiled program (CNode records and edge pairs; see
 // neat_internal.cuh) for this lane's SPL samples.  vb = the warp's value array
 // + lane * SPL floats (bytes); value row r of it at vb + r * 128 * SPL
-// ([row][32 lanes][SPL]: one vector access per row and lane).  GLOBAL: the
-// records come from global memory (read-only path), else from shared memory.
-// Per node: a 16-byte record; per two edges: one 16-byte pair; per edge and
-// sample: one value and one FMA.  Sum and mean keep even edges in a0 and odd
-// edges in a1, the rounding order of the position walk.
+// ([row][32 lanes][SPL]: one vector access per row and lane).  GLOBAL: records
+// and values in global memory, else both in shared memory.  Per node: a
+// 16-byte record; per two edges: one 16-byte pair; per edge and sample: one
+// value and one FMA.  Sum and mean keep even edges in a0 and odd edges in a1,
+// the rounding order of the position walk.
 template <int SPL, bool GLOBAL>
 __device__ __forceinline__ void cwalk(const CNode *__restrict__ nodes, int nn,
                                       const uint4 *__restrict__ pairs, char *vb) {
+  const waddr_t<GLOBAL> na = waddr<GLOBAL>(nodes), pa = waddr<GLOBAL>(pairs),
+                        va = waddr<GLOBAL>(vb);
   for (int c = 0; c < nn; ++c)
-    cnode_eval<SPL, GLOBAL>(ld_rec<SPL, GLOBAL>(reinterpret_cast<const uint4 *>(nodes + c)), pairs,
-                            vb);
+    cnode_eval<SPL, GLOBAL>(w_ld16<GLOBAL>(na + 16u * uint32_t(c)), pa, va);
 }
 
 // Item = (genome in queue order, tile of 32 * SPL samples); lane l evaluates
@@ -424,7 +468,8 @@ __global__ void __launch_bounds__(512, 3)
         for (int k = 0; k < h.clayers; ++k) {
           const int c1 = cl[k + 1];
           for (int c = cl[k] + wid; c < c1; c += nw)
-            cnode_eval<SPL, true>(__ldg(reinterpret_cast<const uint4 *>(cn + c)), cp, vb);
+            cnode_eval<SPL, true>(__ldg(reinterpret_cast<const uint4 *>(cn + c)),
+                                  waddr<true>(cp), waddr<true>(vb));
           __syncthreads();
         }
         const int32_t *orow = w.cout + size_t(g) * O;

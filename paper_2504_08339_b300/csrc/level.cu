@@ -375,6 +375,53 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, int byte
   }
 }
 
+// Shared-memory accesses of the rounds as explicit shared-space instructions
+// (the batch arrays are addressed through offsets read at run time; generic
+// accesses to them measured ~4 % slower per launch on the partial loads
+// alone).  Volatile: never moved across the round's barriers.
+__device__ __forceinline__ unsigned sh_addr(const void *p) {
+  return unsigned(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ float lds_f32(const float *p) {
+  float r;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(r) : "r"(sh_addr(p)) : "memory");
+  return r;
+}
+__device__ __forceinline__ float4 lds_f32x4(const float4 *p) {
+  float4 r;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
+               : "r"(sh_addr(p))
+               : "memory");
+  return r;
+}
+__device__ __forceinline__ uint2 lds_u32x2(const uint2 *p) {
+  uint2 r;
+  asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(r.x), "=r"(r.y) : "r"(sh_addr(p)) : "memory");
+  return r;
+}
+__device__ __forceinline__ TaskRec lds_task(const TaskRec *p) {
+  uint32_t b, r, c, m;
+  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(b), "=r"(r), "=r"(c), "=r"(m)
+               : "r"(sh_addr(p))
+               : "memory");
+  TaskRec t;
+  t.bias = __uint_as_float(b);
+  t.resp = __uint_as_float(r);
+  t.chunk = c;
+  t.meta = m;
+  return t;
+}
+__device__ __forceinline__ void sts_f32(float *p, float x) {
+  asm volatile("st.shared.f32 [%0], %1;" ::"r"(sh_addr(p)), "f"(x) : "memory");
+}
+__device__ __forceinline__ void sts_f32x4(float4 *p, float4 x) {
+  asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(sh_addr(p)), "f"(x.x), "f"(x.y),
+               "f"(x.z), "f"(x.w)
+               : "memory");
+}
+
 // One round, two fully packed phases.
 //  A: one thread per (4-edge chunk, sample): sum, product and max of the
 //     chunk's w * v terms (padding slots skipped) into part[].
@@ -392,7 +439,7 @@ __device__ __forceinline__ void node_group(const TaskRec *__restrict__ tasks, co
   for (int it = lane; it < gn; it += 32) {
     const int t = g0 + (ST == 1 ? it : it / ST);
     const int s = ST == 1 ? 0 : it % ST;
-    const TaskRec tk = tasks[t];
+    const TaskRec tk = lds_task(tasks + t);
     const int cnt = task_cnt(tk.meta), agg = task_agg(tk.meta);
     const int c0 = int(tk.chunk) - lo.chunk, nc = (cnt + 3) >> 2;
     float sum = 0.0f, prod = 1.0f, mx = qnan();
@@ -401,7 +448,8 @@ __device__ __forceinline__ void node_group(const TaskRec *__restrict__ tasks, co
       float4 p[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u)
-        p[u] = k + u < nc ? part[(c0 + k + u) * ST + s] : make_float4(0.0f, 1.0f, qnan(), 0.0f);
+        p[u] = k + u < nc ? lds_f32x4(part + (c0 + k + u) * ST + s)
+                          : make_float4(0.0f, 1.0f, qnan(), 0.0f);
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         sum += p[u].x;
@@ -413,7 +461,7 @@ __device__ __forceinline__ void node_group(const TaskRec *__restrict__ tasks, co
     const float a = nc == 0 ? 0.0f
                   : agg == NEAT_AGG_PRODUCT ? prod
                   : agg == NEAT_AGG_MAX ? mx : sum;
-    v[task_slot(tk.meta) * ST + s] = act_apply(ACT, fmaf(tk.resp, a, tk.bias));
+    sts_f32(v + task_slot(tk.meta) * ST + s, act_apply(ACT, fmaf(tk.resp, a, tk.bias)));
   }
 }
 
@@ -426,22 +474,22 @@ __device__ __forceinline__ void run_round(const TaskRec *__restrict__ tasks,
   for (int it = threadIdx.x; it < na; it += blockDim.x) {
     const int c = lo.chunk + (ST == 1 ? it : it / ST);
     const int s = ST == 1 ? 0 : it % ST;
-    const uint2 sl = eslot[c];
-    const float4 w4 = ew[c];
+    const uint2 sl = lds_u32x2(eslot + c);
+    const float4 w4 = lds_f32x4(ew + c);
     const uint32_t q[4] = {sl.x & 0xffffu, sl.x >> 16, sl.y & 0xffffu, sl.y >> 16};
     const float wq[4] = {w4.x, w4.y, w4.z, w4.w};
     float sum = 0.0f, prod = 1.0f, mx = qnan();
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       if (q[k] != 0xffffu) {
-        const float x = v[q[k] * ST + s];
+        const float x = lds_f32(v + q[k] * ST + s);
         sum = fmaf(wq[k], x, sum);
         const float tv = wq[k] * x;
         prod *= tv;
         mx = fmaxf(mx, tv);
       }
     }
-    part[it] = make_float4(sum, prod, mx, 0.0f);
+    sts_f32x4(part + it, make_float4(sum, prod, mx, 0.0f));
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
