@@ -355,7 +355,8 @@ def accuracy(g, r, bound=None):
     r = np.asarray(r, np.float64)
     fin = np.isfinite(r)
     same_nf = (np.isnan(g) & np.isnan(r)) | (g == r)
-    err = np.abs(g - r)
+    with np.errstate(invalid="ignore"):  # inf - inf on the non-finite class
+        err = np.abs(g - r)
     ar = np.abs(r)
     tol = 1e-6 + 1e-5 * ar
     big = fin & (ar >= 1e-3)
