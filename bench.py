@@ -57,8 +57,8 @@ TRAFFIC = {
         ("paper_2504_08339_b300/csrc/level.cu", "613a45af98c30e3a"), _INTERNAL])),
     ("uneven", "k_forward_sp"): (107699456, 2048, dict([
         ("paper_2504_08339_b300/csrc/forward.cu", "dbf8a64f8cc70842"), _INTERNAL])),
-    ("differentiation", "k_backward"): (359940608, 512, dict([
-        ("paper_2504_08339_b300/csrc/backward.cu", "4363b84f35c1616c"), _INTERNAL])),
+    ("differentiation", "k_backward"): (360216576, 512, dict([
+        ("paper_2504_08339_b300/csrc/backward.cu", "221df7ba2447ddd9"), _INTERNAL])),
 }
 
 

@@ -96,6 +96,24 @@ __host__ __device__ inline int pow2_at_least(int x) {
   return p;
 }
 
+// Explicit shared-space loads with 32-bit addresses for the reverse walk's
+// pulls and the cross-sample sums (the per-warp arrays are addressed through
+// sizes read at run time); volatile with a memory clobber, so they keep
+// their order with the walk's other accesses to the same arrays.
+__device__ __forceinline__ unsigned sh_addr(const void *p) {
+  return unsigned(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ float lds_f32(unsigned a) {
+  float r;
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(r) : "r"(a) : "memory");
+  return r;
+}
+__device__ __forceinline__ uint2 lds_u32x2(unsigned a) {
+  uint2 r;
+  asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(r.x), "=r"(r.y) : "r"(a) : "memory");
+  return r;
+}
+
 // One pulled edge: consumer position and c_e * w_e.
 struct __align__(8) PullRec {
   int dst;
@@ -254,10 +272,11 @@ __global__ void k_backward(Ws w, const float *__restrict__ inputs, int64_t strid
         } else if (agg == NEAT_AGG_SUM || agg == NEAT_AGG_MEAN) {
           float a0 = 0.0f, a1 = 0.0f;
           int k = 0;
+          const unsigned ea = sh_addr(e), va = sh_addr(v);
           for (; k + 1 < cnt; k += 2) {
-            const EdgeRec e0 = e[k], e1 = e[k + 1];
-            a0 = fmaf(e0.w, v[e0.src * RS], a0);
-            a1 = fmaf(e1.w, v[e1.src * RS], a1);
+            const uint2 e0 = lds_u32x2(ea + 8u * unsigned(k)), e1 = lds_u32x2(ea + 8u * unsigned(k + 1));
+            a0 = fmaf(__uint_as_float(e0.y), lds_f32(va + 4u * RS * e0.x), a0);
+            a1 = fmaf(__uint_as_float(e1.y), lds_f32(va + 4u * RS * e1.x), a1);
           }
           if (k < cnt) a0 = fmaf(e[k].w, v[e[k].src * RS], a0);
           a = a0 + a1;
@@ -285,16 +304,21 @@ __global__ void k_backward(Ws w, const float *__restrict__ inputs, int64_t strid
       const int b = pbeg[p], en = pend[p];
       float d0 = dv[p * RS], d1 = 0.0f;
       int i = b;
+      const unsigned pla = sh_addr(pull), dva = sh_addr(dv);
       for (; i + 3 < en; i += 4) {
-        const PullRec r0 = pull[i], r1 = pull[i + 1], r2 = pull[i + 2], r3 = pull[i + 3];
-        const float u0 = dv[r0.dst * RS], u1 = dv[r1.dst * RS], u2 = dv[r2.dst * RS],
-                    u3 = dv[r3.dst * RS];
-        d0 = fmaf(r0.cw, u0, d0);
-        d1 = fmaf(r1.cw, u1, d1);
-        d0 = fmaf(r2.cw, u2, d0);
-        d1 = fmaf(r3.cw, u3, d1);
+        const uint2 r0 = lds_u32x2(pla + 8u * unsigned(i)), r1 = lds_u32x2(pla + 8u * unsigned(i + 1)),
+                    r2 = lds_u32x2(pla + 8u * unsigned(i + 2)), r3 = lds_u32x2(pla + 8u * unsigned(i + 3));
+        const float u0 = lds_f32(dva + 4u * RS * r0.x), u1 = lds_f32(dva + 4u * RS * r1.x),
+                    u2 = lds_f32(dva + 4u * RS * r2.x), u3 = lds_f32(dva + 4u * RS * r3.x);
+        d0 = fmaf(__uint_as_float(r0.y), u0, d0);
+        d1 = fmaf(__uint_as_float(r1.y), u1, d1);
+        d0 = fmaf(__uint_as_float(r2.y), u2, d0);
+        d1 = fmaf(__uint_as_float(r3.y), u3, d1);
       }
-      for (; i < en; ++i) d0 = fmaf(pull[i].cw, dv[pull[i].dst * RS], d0);
+      for (; i < en; ++i) {
+        const uint2 r0 = lds_u32x2(pla + 8u * unsigned(i));
+        d0 = fmaf(__uint_as_float(r0.y), lds_f32(dva + 4u * RS * r0.x), d0);
+      }
       const float d = d0 + d1;
       if (n.meta & META_INPUT) {
         dv[p * RS] = d;  // dL/dx
@@ -365,14 +389,16 @@ __global__ void k_backward(Ws w, const float *__restrict__ inputs, int64_t strid
     const float *vw = v - lane, *aww = av - lane, *dw = dv - lane;  // warp arrays
     for (int p = lane; p < V; p += 32) {
       if (nr[p].meta & (META_INPUT | META_DEAD)) continue;
-      const float *up = dw + p * RS, *ap = aww + p * RS;
+      const unsigned up = sh_addr(dw + p * RS), ap = sh_addr(aww + p * RS);
       float sb0 = 0.0f, sb1 = 0.0f, sr0 = 0.0f, sr1 = 0.0f;
 #pragma unroll 8
       for (int q = 0; q < 32; q += 2) {
-        sb0 += up[q];
-        sb1 += up[q + 1];
-        sr0 = fmaf(up[q], ap[q], sr0);
-        sr1 = fmaf(up[q + 1], ap[q + 1], sr1);
+        const float u0 = lds_f32(up + 4u * q), u1 = lds_f32(up + 4u * (q + 1));
+        const float x0 = lds_f32(ap + 4u * q), x1 = lds_f32(ap + 4u * (q + 1));
+        sb0 += u0;
+        sb1 += u1;
+        sr0 = fmaf(u0, x0, sr0);
+        sr1 = fmaf(u1, x1, sr1);
       }
       accb[p] += sb0 + sb1;
       accr[p] += sr0 + sr1;
@@ -380,14 +406,14 @@ __global__ void k_backward(Ws w, const float *__restrict__ inputs, int64_t strid
     for (int k = lane; k < E; k += 32) {
       const int dd = edst[k];
       if (dd < 0) continue;
-      const float *up = dw + dd * RS, *vp = vw + er[k].src * RS;
+      const unsigned up = sh_addr(dw + dd * RS), vp = sh_addr(vw + er[k].src * RS);
       float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
 #pragma unroll 8
       for (int q = 0; q < 32; q += 4) {
-        s0 = fmaf(up[q], vp[q], s0);
-        s1 = fmaf(up[q + 1], vp[q + 1], s1);
-        s2 = fmaf(up[q + 2], vp[q + 2], s2);
-        s3 = fmaf(up[q + 3], vp[q + 3], s3);
+        s0 = fmaf(lds_f32(up + 4u * q), lds_f32(vp + 4u * q), s0);
+        s1 = fmaf(lds_f32(up + 4u * (q + 1)), lds_f32(vp + 4u * (q + 1)), s1);
+        s2 = fmaf(lds_f32(up + 4u * (q + 2)), lds_f32(vp + 4u * (q + 2)), s2);
+        s3 = fmaf(lds_f32(up + 4u * (q + 3)), lds_f32(vp + 4u * (q + 3)), s3);
       }
       accw[k] = fmaf(ecoef[k], (s0 + s1) + (s2 + s3), accw[k]);
     }
