@@ -55,8 +55,8 @@ _INTERNAL = ("paper_2504_08339_b300/csrc/neat_internal.cuh", "b0c429a08cd68ae5")
 TRAFFIC = {
     ("locomotion", "k_forward_lvl"): (6490880, 2000, dict([
         ("paper_2504_08339_b300/csrc/level.cu", "613a45af98c30e3a"), _INTERNAL])),
-    ("uneven", "k_forward_sp"): (107699456, 2048, dict([
-        ("paper_2504_08339_b300/csrc/forward.cu", "dbf8a64f8cc70842"), _INTERNAL])),
+    ("uneven", "k_forward_sp"): (106829056, 2048, dict([
+        ("paper_2504_08339_b300/csrc/forward.cu", "206a6d7795853bb2"), _INTERNAL])),
     ("differentiation", "k_backward"): (360216576, 512, dict([
         ("paper_2504_08339_b300/csrc/backward.cu", "221df7ba2447ddd9"), _INTERNAL])),
 }

@@ -764,7 +764,7 @@ __device__ __forceinline__ void hn_tiles(const HnTile &t, float *v, int tile0, i
 }
 
 template <int SPL>
-__global__ void __launch_bounds__(512) k_hyperneat(Ws w, int G, float thresh,
+__global__ void __launch_bounds__(512, 2) k_hyperneat(Ws w, int G, float thresh,
                                                    float *__restrict__ weights,
                                                    int chunks_per_genome, int tiles_per_chunk,
                                                    int smem_bytes) {
