@@ -56,8 +56,18 @@ typedef enum {
   NEAT_ERR_CUDA = -2,         /* a CUDA launch or runtime call failed           */
   NEAT_ERR_WORKSPACE = -3,    /* workspace smaller than neat_workspace_bytes() */
   NEAT_ERR_UNSUPPORTED = -4,  /* sizes beyond the library limits below          */
-  NEAT_ERR_STATE = -5         /* e.g. forward before any transform              */
+  NEAT_ERR_STATE = -5,        /* e.g. forward before any transform              */
+  NEAT_ERR_TIMEOUT = -6       /* a kernel's bounded wait gave up (neat_plan_check) */
 } neat_status;
+
+/* Device-side failure bits of a plan (neat_plan_device_errors): set by a
+ * kernel that could not finish some genomes; those genomes' outputs are NaN.
+ *   NEAT_DEV_TIMEOUT    a bounded wait for a bulk copy of a batch program gave
+ *                       up (after neat_tuning.wait_polls polls)
+ *   NEAT_DEV_NO_SCRATCH a genome found no workspace value slot (not reachable
+ *                       with the launch shapes the library picks) */
+#define NEAT_DEV_TIMEOUT 1u
+#define NEAT_DEV_NO_SCRATCH 2u
 
 /* Limits of this build. */
 #define NEAT_MAX_NODES 1024
@@ -121,19 +131,29 @@ neat_status neat_plan_destroy(neat_plan *plan);
  *   samples_per_lane samples one lane evaluates in the sample-parallel forward,
  *                    queries one lane evaluates in the HyperNEAT query (1, 2, 4)
  *   lvl_threads      threads of a level-synchronous (small-sample) CTA: 32..256,
- *                    a multiple of 32
+ *                    a multiple of 32; each warp of it evaluates its own batches
+ *                    (default: the CTA size that keeps the most warps resident)
  *   small_s_max      largest S that uses the level-synchronous forward (1..64,
  *                    -1 = never; default 8); larger S, calls that ask for the
  *                    saved aggregates, and batches that do not fit in shared
  *                    memory use the sample-parallel forward
- *   lvl_budget_kb    program bytes (KiB, 8..160) per level-synchronous batch;
- *                    applied by the next neat_transform
+ *   lvl_budget_kb    program bytes (KiB, 8..160) of a level-synchronous batch,
+ *                    the shared-memory buffer of one warp (raised to what the
+ *                    largest possible genome of the plan needs); applied by the
+ *                    next neat_transform
  *   prune_dead       0 (default): every valid node is evaluated, as the
  *                    paper's calculation does; 1: forwards that return only the
  *                    outputs, the HyperNEAT query and the backward skip the
  *                    nodes no output depends on (the same outputs; their
  *                    parameters' gradients are 0); applied by the next
- *                    neat_transform */
+ *                    neat_transform
+ *   wait_polls       polls of a level-synchronous warp's wait for its staged
+ *                    batch program before it gives up on the batch (0: the
+ *                    default 2^22; -1: no poll, every batch gives up at once,
+ *                    which exercises the failure path).  A batch given up on
+ *                    gets NaN outputs and sets NEAT_DEV_TIMEOUT; the warp
+ *                    still waits (bounded) for its copies before it reuses
+ *                    its buffer. */
 typedef struct {
   int warps_per_cta;
   int samples_per_lane;
@@ -141,9 +161,22 @@ typedef struct {
   int small_s_max;
   int lvl_budget_kb;
   int prune_dead;
+  int wait_polls;
 } neat_tuning;
 neat_status neat_plan_set_tuning(neat_plan *plan, const neat_tuning *t);
 neat_status neat_plan_get_tuning(const neat_plan *plan, neat_tuning *t);
+
+/* The plan's device failure word (NEAT_DEV_* bits, OR-ed by the kernels since
+ * it was last cleared; neat_transform clears it): copied to *errors (device
+ * u32, caller-owned) on `stream` and, if `clear` != 0, reset to 0 after the
+ * copy.  Asynchronous and stream-ordered (capturable in a CUDA graph). */
+neat_status neat_plan_device_errors(neat_plan *plan, uint32_t *errors, int clear,
+                                    cudaStream_t stream);
+
+/* Synchronising check: waits for `stream`, reads and clears the failure word;
+ * NEAT_ERR_TIMEOUT if NEAT_DEV_TIMEOUT was set, NEAT_ERR_WORKSPACE if
+ * NEAT_DEV_NO_SCRATCH was, NEAT_OK otherwise.  Not during a stream capture. */
+neat_status neat_plan_check(neat_plan *plan, cudaStream_t stream);
 
 /* Transformation stage (Sec. 3.3) for all P genomes.
  *   nodes   [P, N, 5] f32, conns [P, C, 4] f32 (read only)
@@ -237,11 +270,15 @@ neat_status neat_hyperneat_query(neat_plan *plan, int grid, float thresh, float 
  *   neat_forward; outputs [P, S, O] f32 out; gstatus [P] u32 out.
  * The plan workspace and the transform's order/layer tensors live in one
  * static device array of NEAT_NOALLOC_SCRATCH_BYTES compiled into the library
- * (held by every GPU that loads it until the process exits).  A population
- * whose workspace does not fit returns NEAT_ERR_WORKSPACE before any launch
- * (about P * (56 N + 28 C + 4 (I + O)) bytes plus the small-sample schedule;
- * e.g. 600 genomes of N = 128, C = 512 fit).  Uses the sample-parallel
- * forward for every S.
+ * (held by every GPU that loads it until the process exits).  The call uses
+ * 16 regions of it, each rounded up to 256 bytes: at most
+ * P (48 N + 24 C + 4 (I + O) + 60) + 4352 bytes.  A population whose regions
+ * do not fit returns NEAT_ERR_WORKSPACE before any launch (the limit is
+ * exactly 1,800 genomes of N = 128, C = 512, I = 27, O = 8 and 227 of N = 1024,
+ * C = 4096, I = 17, O = 6).  Every shape check (sizes, alignment, shared
+ * memory, the 2^31 work-item limit of P * ceil(S / 32)) also comes before the
+ * first launch.  Uses the sample-parallel forward with each genome's values in
+ * shared memory, for every S.
  * The first call on a device (that device current) looks up the array's
  * address with cudaGetSymbolAddress and sets kernel attributes: make it before
  * any stream capture.  All calls share the array and each call overwrites it:

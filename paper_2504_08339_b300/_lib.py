@@ -14,15 +14,17 @@ import threading
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libneat.so")
 
-NEAT_OK, NEAT_ERR_ARG, NEAT_ERR_CUDA, NEAT_ERR_WORKSPACE, NEAT_ERR_UNSUPPORTED, NEAT_ERR_STATE = (
-    0, -1, -2, -3, -4, -5)
+(NEAT_OK, NEAT_ERR_ARG, NEAT_ERR_CUDA, NEAT_ERR_WORKSPACE, NEAT_ERR_UNSUPPORTED, NEAT_ERR_STATE,
+ NEAT_ERR_TIMEOUT) = (0, -1, -2, -3, -4, -5, -6)
+DEV_TIMEOUT, DEV_NO_SCRATCH = 1, 2
 G_CYCLE, G_DANGLING_KEY, G_DUP_KEY, G_DUP_EDGE, G_EDGE_INTO_INPUT, G_BAD_ATTR, G_IO_ROW_INVALID = (
     1, 2, 4, 8, 16, 32, 64)
 
 # every symbol include/neat.h declares
 SYMBOLS = ("neat_version", "neat_status_string", "neat_last_cuda_error",
            "neat_workspace_bytes", "neat_plan_create",
-           "neat_plan_destroy", "neat_plan_set_tuning", "neat_plan_get_tuning", "neat_transform",
+           "neat_plan_destroy", "neat_plan_set_tuning", "neat_plan_get_tuning",
+           "neat_plan_device_errors", "neat_plan_check", "neat_transform",
            "neat_forward", "neat_forward_plain", "neat_backward", "neat_hyperneat_query",
            "neat_forward_noalloc", "neat_probe_smem_read", "neat_transform_recurrent",
            "neat_forward_recurrent", "neat_distance_scratch_bytes", "neat_distance",
@@ -38,7 +40,7 @@ class neat_tuning(ctypes.Structure):
     _fields_ = [("warps_per_cta", ctypes.c_int), ("samples_per_lane", ctypes.c_int),
                 ("lvl_threads", ctypes.c_int), ("small_s_max", ctypes.c_int),
                 ("lvl_budget_kb", ctypes.c_int),
-                ("prune_dead", ctypes.c_int)]
+                ("prune_dead", ctypes.c_int), ("wait_polls", ctypes.c_int)]
 
 
 _lock = threading.Lock()
@@ -66,6 +68,8 @@ def load(path: str = LIB_PATH):
             "neat_plan_destroy": (i32, [vp]),
             "neat_plan_set_tuning": (i32, [vp, ctypes.POINTER(neat_tuning)]),
             "neat_plan_get_tuning": (i32, [vp, ctypes.POINTER(neat_tuning)]),
+            "neat_plan_device_errors": (i32, [vp, vp, i32, vp]),
+            "neat_plan_check": (i32, [vp, vp]),
             "neat_transform": (i32, [vp, vp, vp, vp, vp, vp, vp, vp]),
             "neat_forward": (i32, [vp, vp, i64, i32, vp, vp, vp]),
             "neat_forward_plain": (i32, [vp, vp, i64, i32, vp, vp]),

@@ -55,6 +55,7 @@ class Plan:
         base = self.workspace.data_ptr()
         self._ws_ptr = (base + 255) // 256 * 256
         self._h = ctypes.c_void_p()
+        self.generation = 0  # bumped by every transform (the programs it built)
         with torch.cuda.device(self.device):
             _lib.check(lib.neat_plan_create(ctypes.byref(self._h), self.P, self.N, self.C, self.I,
                                             self.O, ctypes.c_void_p(self._ws_ptr), nbytes),
@@ -85,6 +86,20 @@ class Plan:
             setattr(t, k, int(v))
         _lib.check(self._lib.neat_plan_set_tuning(self._h, ctypes.byref(t)), "set_tuning")
 
+    # -- device failures -----------------------------------------------------------
+    def device_errors(self, clear=True, stream=None) -> int:
+        """The plan's device failure bits (_lib.DEV_*) OR-ed by its kernels since
+        the last clear (synchronises with the stream)."""
+        word = torch.zeros((1,), dtype=torch.int32, device=self.device)
+        _lib.check(self._lib.neat_plan_device_errors(self._h, _ptr(word), int(bool(clear)),
+                                                     _stream(stream)), "neat_plan_device_errors")
+        return int(word.item()) & 0xffffffff
+
+    def check(self, stream=None) -> None:
+        """Raise NeatError if a kernel of this plan gave up on some genomes
+        (their outputs are NaN) since the last check or transform."""
+        _lib.check(self._lib.neat_plan_check(self._h, _stream(stream)), "neat_plan_check")
+
     # -- transformation stage -----------------------------------------------------
     def transform(self, nodes, conns, out: Transformed | None = None, stream=None) -> Transformed:
         P, N, C = self.P, self.N, self.C
@@ -100,6 +115,7 @@ class Plan:
                                             _ptr(out.layer), _ptr(out.n_layers),
                                             _ptr(out.status), _stream(stream)),
                    "neat_transform")
+        self.generation += 1
         return out
 
     def hyperneat_substrate(self, inputs, grid=32, thresh=0.2, act=2, weights=None, out=None,
@@ -146,6 +162,7 @@ class Plan:
             self._h, _ptr(nodes), _ptr(conns), _ptr(ops), ops.shape[1], _ptr(op_status),
             _ptr(out.order), _ptr(out.layer), _ptr(out.n_layers), _ptr(out.status),
             _stream(stream)), "neat_mutate_transform")
+        self.generation += 1
         return out, op_status
 
     def transform_recurrent(self, nodes, conns, status=None, stream=None):
@@ -159,6 +176,7 @@ class Plan:
         _lib.check(self._lib.neat_transform_recurrent(self._h, _ptr(nodes), _ptr(conns),
                                                       _ptr(status), _stream(stream)),
                    "neat_transform_recurrent")
+        self.generation += 1
         return status
 
     def forward_recurrent(self, inputs, T, out=None, stream=None):
@@ -303,6 +321,7 @@ class NeatFunction(torch.autograd.Function):
             saved = torch.empty((plan.P, plan.N, S), dtype=torch.float32, device=inputs.device)
         out = plan.forward(inputs, saved=saved)
         ctx.plan = plan
+        ctx.generation = plan.generation
         ctx.saved_agg = saved
         ctx.save_for_backward(nodes, conns, inputs)
         return out
@@ -311,6 +330,11 @@ class NeatFunction(torch.autograd.Function):
     def backward(ctx, grad_out):
         nodes, conns, inputs = ctx.saved_tensors
         plan = ctx.plan
+        if plan.generation != ctx.generation:
+            # the plan was transformed again since this forward (e.g. another
+            # evaluate on the same plan): rebuild this population's programs,
+            # which the saved aggregates were taken on
+            plan.transform(nodes, conns)
         gw, gb, gr, gi = plan.backward(inputs, grad_out.contiguous(), saved=ctx.saved_agg,
                                        want_inputs=ctx.needs_input_grad[3])
         g_nodes = g_conns = g_inputs = None

@@ -1,8 +1,9 @@
 """Autotuner for the launch shapes of a plan.
 
 Times `neat_forward` on the caller's own population and inputs under a small
-set of candidate tunings (threads of a level-synchronous CTA, its batch byte
-budget, warps of a sample-parallel CTA, the small-S switch point), applies the
+set of candidate tunings (the per-warp batch byte budget and CTA size of the
+level-synchronous form, warps of a sample-parallel CTA, samples per lane, the
+small-S switch point), applies the
 fastest, and caches the choice per workload signature in a JSON file
 (`$NEAT_TUNE_CACHE`, default `~/.cache/neat_b300/tune.json`).  Changing the
 batch budget rebuilds the level batches, so the population is re-transformed.
@@ -32,9 +33,9 @@ def candidates(plan: Plan, S: int):
     """Candidate tunings for S samples per genome."""
     out = []
     if S <= 8:
-        for thr in (128, 256):
-            for kb in (24, 32, 48):
-                out.append(dict(lvl_threads=thr, lvl_budget_kb=kb))
+        for kb in (8, 10, 12, 16, 24):
+            out.append(dict(lvl_budget_kb=kb))
+        out.append(dict(lvl_budget_kb=12, lvl_threads=64))
     for spl in (1, 2, 4):
         if spl > 1 and S < 32 * spl:
             continue

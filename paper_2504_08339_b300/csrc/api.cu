@@ -36,11 +36,7 @@ bool sizes_ok(int P, int N, int C, int I, int O) {
 
 thread_local int g_last_cuda_error = 0;
 
-neat_status cuda_status(cudaError_t e) {
-  if (e == cudaSuccess) return NEAT_OK;
-  g_last_cuda_error = int(e);
-  return NEAT_ERR_CUDA;
-}
+neat_status cuda_status(cudaError_t e) { return neat::cuda_error_status(e); }
 
 // Launch shape of the sample-parallel forward for S samples per genome.
 // Every genome's values live in its warp's workspace slot (measured faster
@@ -67,14 +63,42 @@ neat::SpShape sp_shape(const neat_plan *p, int S) {
   return sh;
 }
 
-int lvl_threads(const neat_plan *p) { return p->tune.lvl_threads > 0 ? p->tune.lvl_threads : 256; }
-
 int small_s_max(const neat_plan *p) {
   return p->tune.small_s_max != 0 ? p->tune.small_s_max : 8;  // -1: never
 }
 
+// Per-warp shared memory of the level-synchronous forward above which the
+// sample-parallel forward takes small S too (fewer than three warps per SM).
+constexpr size_t kLvlWarpMaxBytes = 72 * 1024;
+
 bool lvl_fits(const neat_plan *p, int S) {
-  return neat::forward_lvl_smem(p->w, neat::lvl_tile(S)) <= size_t(p->smem_optin);
+  const size_t wb = neat::lvl_warp_bytes(p->w, neat::lvl_tile(S));
+  return wb <= kLvlWarpMaxBytes && wb <= size_t(p->smem_optin);
+}
+
+// Warps per CTA of the level-synchronous forward: the tuning's lvl_threads,
+// else the CTA size (8, 4, 2 or 1 warps) that keeps the most warps resident
+// per SM (each warp owns a batch buffer, so the per-SM shared memory is what
+// limits them).
+int lvl_warps(const neat_plan *p, int st, int *occ_out) {
+  const size_t wb = neat::lvl_warp_bytes(p->w, st);
+  int best = 0, best_w = 1, best_occ = 1;
+  for (int wp : {8, 4, 2, 1}) {
+    if (p->tune.lvl_threads > 0 && wp != p->tune.lvl_threads / 32) continue;
+    const int occ = neat::forward_lvl_occupancy(wp, wb * size_t(wp), st);
+    if (occ * wp > best) { best = occ * wp; best_w = wp; best_occ = occ; }
+  }
+  if (best == 0) {  // the tuning's CTA size does not fit: fall back to one warp
+    best_w = 1;
+    best_occ = std::max(1, neat::forward_lvl_occupancy(1, wb, st));
+  }
+  if (occ_out) *occ_out = best_occ;
+  return best_w;
+}
+
+// Polls of a staging wait before the level kernel gives up on a batch.
+int wait_polls(const neat_plan *p) {
+  return p->tune.wait_polls == 0 ? (1 << 22) : (p->tune.wait_polls < 0 ? 0 : p->tune.wait_polls);
 }
 
 // Backward CTA: 16 warps over all the shared memory a CTA may have; each
@@ -87,10 +111,27 @@ neat_status check_inputs(const neat_plan *p, const float *inputs, int64_t stride
   if (S == 0 || p->P == 0) return NEAT_OK;
   if (inputs == nullptr || !aligned(inputs, 4)) return NEAT_ERR_ARG;
   if (stride != 0 && stride < int64_t(S) * p->I) return NEAT_ERR_ARG;
+  // the persistent kernels count (genome, 32-sample tile) work items in 32 bits
+  if (int64_t(p->P) * ((int64_t(S) + 31) / 32) > int64_t(INT32_MAX)) return NEAT_ERR_UNSUPPORTED;
   return NEAT_OK;
 }
 
+// copy (and optionally clear) the plan's device failure word
+__global__ void k_read_errors(uint32_t *word, uint32_t *dst, int clear) {
+  const uint32_t v = *word;
+  *dst = v;
+  if (clear) *word = 0u;
+}
+
 }  // namespace
+
+namespace neat {
+neat_status cuda_error_status(cudaError_t e) {
+  if (e == cudaSuccess) return NEAT_OK;
+  g_last_cuda_error = int(e);
+  return NEAT_ERR_CUDA;
+}
+}  // namespace neat
 
 extern "C" {
 
@@ -106,6 +147,7 @@ const char *neat_status_string(neat_status s) {
     case NEAT_ERR_WORKSPACE: return "workspace too small";
     case NEAT_ERR_UNSUPPORTED: return "unsupported size";
     case NEAT_ERR_STATE: return "plan not transformed (for this network type)";
+    case NEAT_ERR_TIMEOUT: return "a bounded device wait gave up (outputs of its genomes are NaN)";
   }
   return "unknown status";
 }
@@ -175,6 +217,7 @@ neat_status neat_plan_set_tuning(neat_plan *plan, const neat_tuning *t) {
                                 t->lvl_budget_kb * 1024 > neat::LVL_MAX_BUDGET))
     return NEAT_ERR_ARG;
   if (t->prune_dead != 0 && t->prune_dead != 1) return NEAT_ERR_ARG;
+  if (t->wait_polls < -1) return NEAT_ERR_ARG;
   plan->tune = *t;
   return NEAT_OK;
 }
@@ -185,9 +228,33 @@ neat_status neat_plan_get_tuning(const neat_plan *plan, neat_tuning *t) {
   const neat::SpShape sh = sp_shape(plan, 32);
   if (t->warps_per_cta == 0) t->warps_per_cta = sh.warps;
   if (t->samples_per_lane == 0) t->samples_per_lane = sh.spl;
-  if (t->lvl_threads == 0) t->lvl_threads = lvl_threads(plan);
+  if (t->lvl_threads == 0) t->lvl_threads = 32 * lvl_warps(plan, 1, nullptr);
   if (t->small_s_max == 0) t->small_s_max = small_s_max(plan);
-  if (t->lvl_budget_kb == 0) t->lvl_budget_kb = plan->w.lvl_budget / 1024;
+  if (t->lvl_budget_kb == 0)
+    t->lvl_budget_kb = (neat::lvl_budget(plan->N, plan->C, plan->I, plan->O) + 1023) / 1024;
+  if (t->wait_polls == 0) t->wait_polls = wait_polls(plan);
+  return NEAT_OK;
+}
+
+neat_status neat_plan_device_errors(neat_plan *plan, uint32_t *errors, int clear,
+                                    cudaStream_t stream) {
+  if (plan == nullptr || errors == nullptr || !aligned(errors, 4)) return NEAT_ERR_ARG;
+  k_read_errors<<<1, 1, 0, stream>>>(plan->w.counters + neat::CTR_ERR, errors, clear ? 1 : 0);
+  return cuda_status(cudaGetLastError());
+}
+
+neat_status neat_plan_check(neat_plan *plan, cudaStream_t stream) {
+  if (plan == nullptr) return NEAT_ERR_ARG;
+  uint32_t word = 0;
+  cudaError_t e = cudaMemcpyAsync(&word, plan->w.counters + neat::CTR_ERR, sizeof(word),
+                                  cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e == cudaSuccess && word != 0u)
+    e = cudaMemsetAsync(plan->w.counters + neat::CTR_ERR, 0, sizeof(uint32_t), stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (word & NEAT_DEV_TIMEOUT) return NEAT_ERR_TIMEOUT;
+  if (word & NEAT_DEV_NO_SCRATCH) return NEAT_ERR_WORKSPACE;
   return NEAT_OK;
 }
 
@@ -205,10 +272,11 @@ neat_status neat_transform(neat_plan *plan, const float *nodes, const float *con
   }
   // the batch budget is fixed by the transform that builds the batches
   plan->w.prune = plan->tune.prune_dead == 1 ? 1 : 0;
-  plan->w.lvl_budget = plan->tune.lvl_budget_kb > 0
-                           ? plan->tune.lvl_budget_kb * 1024
-                           : neat::lvl_budget(plan->N, plan->C, plan->I, plan->O);
-  cudaError_t e = neat::launch_transform(plan->w, nodes, conns, order, layer, n_layers, gstatus,
+  plan->w.lvl_budget =
+      neat::lvl_budget(plan->N, plan->C, plan->I, plan->O, plan->tune.lvl_budget_kb * 1024);
+  // a new population: the device error word starts clean
+  cudaError_t e = cudaMemsetAsync(plan->w.counters + neat::CTR_ERR, 0, sizeof(uint32_t), stream);
+  if (e == cudaSuccess) e = neat::launch_transform(plan->w, nodes, conns, order, layer, n_layers, gstatus,
                                          stream);
   if (e == cudaSuccess) e = neat::launch_queue_build(plan->w, 0, stream);
   if (e == cudaSuccess) e = neat::launch_lvl_build(plan->w, stream);
@@ -227,14 +295,14 @@ neat_status neat_forward(neat_plan *plan, const float *inputs, int64_t in_pop_st
   if (outputs == nullptr || !aligned(outputs, 4) || (saved && !aligned(saved, 4)))
     return NEAT_ERR_ARG;
   if (saved == nullptr && S <= small_s_max(plan) && lvl_fits(plan, S)) {
-    // few samples per genome: level-synchronous batches of genomes
-    const int threads = lvl_threads(plan);
+    // few samples per genome: level-synchronous batches of genomes, one per warp
     const int st = neat::lvl_tile(S);
-    const size_t smem = neat::forward_lvl_smem(plan->w, st);
-    const int occ = std::max(1, neat::forward_lvl_occupancy(threads, smem, st));
-    const int grid = std::max(1, std::min(plan->sm_count * occ, plan->w.lvl_max_batches));
-    return cuda_status(neat::launch_forward_lvl(plan->w, inputs, in_pop_stride, S, outputs,
-                                                threads, grid, stream));
+    int occ = 1;
+    const int warps = lvl_warps(plan, st, &occ);
+    const int64_t want = (int64_t(plan->P) + warps - 1) / warps;  // batches <= P
+    const int grid = int(std::max<int64_t>(1, std::min<int64_t>(int64_t(plan->sm_count) * occ, want)));
+    return cuda_status(neat::launch_forward_lvl(plan->w, inputs, in_pop_stride, S, outputs, warps,
+                                                grid, wait_polls(plan), stream));
   }
   const neat::SpShape sh = sp_shape(plan, S);
   if (int64_t(sh.grid) * sh.warps > neat::sp_scratch_slots(plan->w, sh.spl))

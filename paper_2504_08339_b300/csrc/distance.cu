@@ -386,16 +386,17 @@ extern "C" neat_status neat_distance(const float *nodes, const float *conns,
     return NEAT_ERR_UNSUPPORTED;
   neat::k_dist_prep<<<P, 256, smem, stream>>>(nodes, conns, gstatus, N, C, I, ng, cg, nkey, ckey,
                                                counts);
-  if (cudaGetLastError() != cudaSuccess) return NEAT_ERR_CUDA;
-  if (cudaMemsetAsync(hist, 0, sizeof(int) * size_t(C + 1), stream) != cudaSuccess)
-    return NEAT_ERR_CUDA;
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemsetAsync(hist, 0, sizeof(int) * size_t(C + 1), stream);
+  if (e != cudaSuccess) return neat::cuda_error_status(e);
   const unsigned gb = unsigned((P + 255) / 256);
   neat::k_dist_hist<<<gb, 256, 0, stream>>>(counts, P, C, hist);
   neat::k_dist_scan<<<1, 1024, 0, stream>>>(hist, C + 1);
   neat::k_dist_scatter<<<gb, 256, 0, stream>>>(counts, P, C, hist, perm);
-  if (cudaGetLastError() != cudaSuccess) return NEAT_ERR_CUDA;
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return neat::cuda_error_status(e);
   const dim3 grid(unsigned((P + 15) / 16), unsigned((P + 15) / 16)), block(16, 16);
   neat::k_distance<<<grid, block, 0, stream>>>(ng, cg, nkey, ckey, counts, perm, P, N, C,
                                                c_disjoint, c_homologous, dist);
-  return cudaGetLastError() == cudaSuccess ? NEAT_OK : NEAT_ERR_CUDA;
+  return neat::cuda_error_status(cudaGetLastError());
 }

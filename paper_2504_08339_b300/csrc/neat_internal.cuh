@@ -85,32 +85,28 @@ constexpr uint32_t CN_PAIR_BITS = 17, CN_ROW_BITS = 20;
 __host__ __device__ inline int cpair_cap(int N, int C) { return (C + N) / 2 + 1; }
 
 // -- level-synchronous batches (small-S form) --------------------------------------
-// Consecutive genomes of a layer-sorted queue are packed into batches.  A batch
-// program lives in the level arena as one contiguous, 16-byte aligned block:
+// Consecutive genomes of a layer-sorted queue are packed into small batches,
+// one per warp: a warp stages its batch program into its own shared-memory
+// buffer (lvl_budget bytes, fixed per plan) and evaluates the batch round by
+// round, synchronising with __syncwarp only.  A batch program lives in the
+// level arena as one contiguous, 16-byte aligned block:
 //   BatchHead (48 B)
 //   gio       int32[n_genomes*(1+I+O)] genome id, input slots, output slots
-//   rounds    RoundRec[n_rounds + 1]   first task, first chunk and activation
-//                                      groups of each round
+//   rounds    uint32[n_rounds + 1]     first task | first chunk << 16
 //   --- off_task: the head part above is staged first, the rest after it
 //   tasks     TaskRec[n_tasks]         non-input nodes, by (layer, act, -cnt)
-//   eslot     uint16[4 * n_chunks]     source value slot of each edge (0xffff: pad)
+//   eslot     uint16[4 * n_chunks]     source value slot of each edge (0xffff: pad);
+//                                      the first entry of a chunk (never padding)
+//                                      carries the task's aggregation in bits 12-13
 //   ew        float[4 * n_chunks]      weight of each edge
 // Every task's incoming edges are padded to whole 4-edge chunks.  A round
-// holds tasks of one layer only and at most LVL_PCAP chunks (a layer may span
+// holds tasks of one layer only and at most lvl_pcap chunks (a layer may span
 // several rounds).  Value slot of position p of the k-th genome of the batch
 // = slot_base(k) + p.
 struct __align__(16) BatchHead {
   int n_genomes, n_slots, n_rounds, n_tasks;
   int n_chunks, off_round, off_task, off_eslot;
   int off_gio, prog_bytes, off_ew, pad;
-};
-constexpr int LVL_PCAP = 256;  // chunks per round (>= the chunks of any one node)
-// Round record (24 B): tasks [task, next.task), chunks [chunk, next.chunk);
-// tasks task + act[a] .. task + act[a+1] - 1 have activation a (act[7] = count).
-struct __align__(8) RoundRec {
-  int task;
-  int chunk;
-  uint16_t act[8];
 };
 // where a batch program sits in the arena
 struct __align__(16) BatchLoc {
@@ -131,10 +127,6 @@ struct __align__(16) TaskRec {
 constexpr int LVL_SLOT_BITS = 12;
 constexpr int LVL_MAX_SLOTS = 1 << LVL_SLOT_BITS;  // 4096 value slots per batch
 constexpr int LVL_MAX_GENOMES = 64;                // genomes per batch (hard cap)
-constexpr int LVL_GENOME_BUDGET = 48;
-// value slots a batch may fill before its last genome (a batch then holds
-// fewer than slot_budget + N slots)
-__host__ __device__ inline int lvl_slot_budget(int N) { return N <= 256 ? 1024 : 3072; }
 __host__ __device__ inline uint32_t task_meta(int cnt, int act, int agg, int slot) {
   return uint32_t(cnt) | (uint32_t(act) << 14) | (uint32_t(agg) << 17) | (uint32_t(slot) << 19);
 }
@@ -143,47 +135,47 @@ __host__ __device__ inline int task_act(uint32_t m) { return int((m >> 14) & 7u)
 __host__ __device__ inline int task_agg(uint32_t m) { return int((m >> 17) & 3u); }
 __host__ __device__ inline int task_slot(uint32_t m) { return int(m >> 19); }
 
-// Bytes a genome contributes to a batch program (upper bound incl. alignment):
-// task records, padded edges (24 B per chunk), I/O slots, and round-table
-// entries (one per layer plus one per task, bounding the chunk-cap splits).
-__host__ __device__ inline int lvl_genome_bytes(int V, int nch, int L, int I, int O, bool ok) {
-  const int tasks = ok ? (V - I) : 0;
-  const int b = 24 * tasks + 24 * (ok ? nch : 0) + 4 * (1 + I + O) + 24 * ((ok ? L : 0) + 2) + 160;
+// Bytes a genome contributes to a batch program (upper bound): 16 B per task,
+// 24 B per 4-edge chunk, 4 B per genome id and I/O slot, and round-table
+// entries (4 B each: one per layer, plus one per task for the rounds split at
+// the chunk cap).  A batch program takes at most LVL_BATCH_FIXED (header and
+// alignment of its five arrays) plus the sum of its genomes' bytes.
+constexpr int LVL_BATCH_FIXED = 112;
+__host__ __device__ inline int lvl_genome_bytes(int tasks, int nch, int L, int I, int O, bool ok) {
+  const int b = 4 * (1 + I + O) + (ok ? 20 * tasks + 24 * nch + 4 * L + 4 : 4);
   return (b + 15) & ~15;
 }
-// largest chunk count of a genome with N node rows and C connection rows
-inline int lvl_max_chunks(int N, int C) { return C / 4 + N; }
-// Batch-assignment weight: program bytes, or the genome's share of the slot /
-// genome-count budgets, whichever is larger (all scaled to bytes).
-__host__ __device__ inline int lvl_genome_weight(int pb, int V, int budget, int slot_budget) {
-  const int ws = int((long long)V * budget / slot_budget);
-  const int wg = budget / LVL_GENOME_BUDGET;
-  const int m = ws > wg ? ws : wg;
-  return pb > m ? pb : m;
-}
-// Byte budget of a batch (a batch holds the genomes whose weight prefix falls
-// in [b * budget, (b+1) * budget), so its program is < budget + max weight).
+// largest genome bytes for N node rows and C connection rows: at most N - I
+// tasks, sum over tasks of ceil(indeg / 4) <= (C + 3 (N - I)) / 4 chunks, N layers
 inline int lvl_pb_max(int N, int C, int I, int O) {
-  return lvl_genome_bytes(N, lvl_max_chunks(N, C), N, I, O, true);
+  return lvl_genome_bytes(N - I, (C + 3 * (N - I)) / 4, N, I, O, true);
 }
-constexpr int LVL_MIN_BUDGET = 8 * 1024;
-constexpr int LVL_MAX_BUDGET = 160 * 1024;
-inline int lvl_budget(int N, int C, int I, int O) {
-  // 48 KiB measured best on the locomotion rollout (sweep of 24..64 KiB);
-  // larger genomes get a budget of at least twice their largest program
-  const int pbmax = lvl_pb_max(N, C, I, O);
-  int b = 48 * 1024;
-  while (b < 2 * pbmax && b < 96 * 1024) b *= 2;
-  return b;
+// per-warp program buffer: any single genome fits (the budget knob may ask
+// for more, never for less)
+inline int lvl_min_budget(int N, int C, int I, int O) {
+  return (LVL_BATCH_FIXED + lvl_pb_max(N, C, I, O) + 127) & ~127;
 }
-inline int lvl_max_weight(int N, int C, int I, int O, int budget) {
-  return lvl_genome_weight(lvl_pb_max(N, C, I, O), N, budget, lvl_slot_budget(N));
+constexpr int LVL_MIN_BUDGET = 8 * 1024;    // smallest budget knob (KiB granularity)
+constexpr int LVL_MAX_BUDGET = 160 * 1024;  // largest budget knob
+inline int lvl_budget(int N, int C, int I, int O, int knob_bytes = 0) {
+  // 12 KiB: about three locomotion-sized genomes per warp batch
+  const int want = knob_bytes > 0 ? knob_bytes : 12 * 1024;
+  const int m = lvl_min_budget(N, C, I, O);
+  return want > m ? ((want + 127) & ~127) : m;
+}
+// value slots of a batch (>= N: any single genome fits)
+inline int lvl_slots(int N) { return N > 512 ? N : 512; }
+// chunks of a round (>= the chunks of any one task: in-degree <= min(N - 1, C))
+inline int lvl_pcap(int N, int C) {
+  const int t = ((N - 1 < C ? N - 1 : C) + 3) / 4;
+  return t > 128 ? t : 128;
 }
 
 // -- workspace layout ------------------------------------------------------------
 struct Layout {
-  size_t hdr, pnode, pedge, perow, prow, player, pio, qorder, knode, kedge, kerow, counters;
-  size_t qlvl, lvl_goff, lvl_first, lvl_loc, lvl_arena;  // small-S schedule
+  size_t hdr, pnode, pedge, perow, prow, player, pio, qorder, qlvl, knode, kedge, kerow, counters;
+  size_t base;                                 // bytes of the regions above
+  size_t lvl_goff, lvl_first, lvl_loc, lvl_arena;  // small-S schedule
   size_t lvl_arena_bytes;
   int lvl_max_batches;
   size_t core;                       // bytes of everything above
@@ -214,20 +206,19 @@ inline Layout make_layout(int P, int N, int C, int I, int O) {
   L.player = take(sizeof(int32_t) * p * N);
   L.pio = take(sizeof(int32_t) * p * (I + O));
   L.qorder = take(sizeof(int32_t) * (p + 1));
+  L.qlvl = take(sizeof(int32_t) * (p + 1));
   L.knode = take(sizeof(NodeRec) * p * N);
   L.kedge = take(sizeof(EdgeRec) * p * C);
   L.kerow = take(sizeof(int32_t) * p * C);
   L.counters = take(sizeof(uint32_t) * 64);
-  // small-S schedule
-  // batches for any budget >= LVL_MIN_BUDGET: sum of weights / budget + 1,
-  // with weight <= pb + V * budget / slot_budget + budget / 48
-  L.lvl_max_batches = int(p * size_t(lvl_pb_max(N, C, I, O)) / LVL_MIN_BUDGET +
-                          p * size_t(N) / size_t(lvl_slot_budget(N)) + p / LVL_GENOME_BUDGET) + 3;
-  L.qlvl = take(sizeof(int32_t) * (p + 1));
+  L.base = off;
+  // small-S schedule: at most one batch per genome; a batch program is at
+  // most LVL_BATCH_FIXED + the bytes of its genomes
+  L.lvl_max_batches = int(p) + 1;
   L.lvl_goff = take(sizeof(int32_t) * (p + 1));
   L.lvl_first = take(sizeof(int32_t) * (size_t(L.lvl_max_batches) + 2));
   L.lvl_loc = take(sizeof(BatchLoc) * (size_t(L.lvl_max_batches) + 1));
-  L.lvl_arena_bytes = p * size_t(lvl_pb_max(N, C, I, O)) + 256;
+  L.lvl_arena_bytes = p * size_t(lvl_pb_max(N, C, I, O) + LVL_BATCH_FIXED) + 256;
   L.lvl_arena = take(L.lvl_arena_bytes);
   L.core = off;
   L.cnode = take(sizeof(CNode) * p * N);
@@ -265,7 +256,10 @@ struct Ws {
   int32_t *clay;
   float *sp_scratch;  // per-warp node value slots (nullptr: none)
   size_t sp_scratch_floats;
-  int lvl_budget, lvl_max_batches;
+  int lvl_budget;  // bytes of a batch program buffer (per warp), set at transform time
+  int lvl_slots;   // value slots of a batch
+  int lvl_pcap;    // chunks of a round
+  int lvl_max_batches;
   int prune;  // skip the nodes no output depends on (set at transform time)
   int P, N, C, I, O;
 };
@@ -297,6 +291,8 @@ inline Ws make_ws(void *base, const Layout &L, int P, int N, int C, int I, int O
   w.sp_scratch = L.sp_scratch_bytes ? reinterpret_cast<float *>(b + L.sp_scratch) : nullptr;
   w.sp_scratch_floats = L.sp_scratch_bytes / sizeof(float);
   w.lvl_budget = lvl_budget(N, C, I, O);
+  w.lvl_slots = lvl_slots(N);
+  w.lvl_pcap = lvl_pcap(N, C);
   w.prune = 0;
   w.lvl_max_batches = L.lvl_max_batches;
   w.P = P; w.N = N; w.C = C; w.I = I; w.O = O;
@@ -321,8 +317,8 @@ __host__ __device__ inline int sp_coop_cost(bool prune) {
 __host__ __device__ inline int sp_cost(const GenomeHdr &h) {
   return h.elive + 2 * h.nlive + (h.V - h.nlive) / 4;
 }
-// error bits in counters[CTR_ERR]
-constexpr uint32_t ERR_TMA_TIMEOUT = 1u, ERR_SP_NO_SCRATCH = 2u;
+// error bits in counters[CTR_ERR] (the NEAT_DEV_* bits of neat.h)
+constexpr uint32_t ERR_TMA_TIMEOUT = NEAT_DEV_TIMEOUT, ERR_SP_NO_SCRATCH = NEAT_DEV_NO_SCRATCH;
 
 // -- activations (textbook forms; accurate libm-style device functions) -----------
 __device__ __forceinline__ float act_apply(int a, float z) {
@@ -388,6 +384,10 @@ __device__ __forceinline__ float act_deriv(int a, float z, float v) {
 
 __device__ __forceinline__ float qnan() { return __int_as_float(0x7fc00000); }
 
+// NEAT_OK for cudaSuccess; otherwise records e for neat_last_cuda_error() (per
+// host thread) and returns NEAT_ERR_CUDA
+neat_status cuda_error_status(cudaError_t e);
+
 // -- launch wrappers (defined in the .cu files) ------------------------------------
 // recurrent != 0: no topological order (cycles legal); every valid node in
 // ascending key forms one frontier; order / layer / n_layers may be null
@@ -449,11 +449,16 @@ int forward_sp_occupancy(int warps, size_t smem, int spl);
 int hyperneat_occupancy(int spl, int warps, size_t smem);
 // level-synchronous small-S form
 cudaError_t launch_lvl_build(const Ws &w, cudaStream_t st);
-size_t forward_lvl_smem(const Ws &w, int st_samples);
+// shared memory of one warp of the level-synchronous forward: its batch
+// program buffer, value slots and chunk partials for st_samples per tile
+size_t lvl_warp_bytes(const Ws &w, int st_samples);
+size_t lvl_vals_bytes(const Ws &w, int st_samples);
+// `warps` per CTA, each owning lvl_warp_bytes; a staging wait gives up after
+// `polls` polls (0: at once)
 cudaError_t launch_forward_lvl(const Ws &w, const float *inputs, int64_t stride, int S,
-                               float *outputs, int threads, int grid, cudaStream_t st);
+                               float *outputs, int warps, int grid, int polls, cudaStream_t st);
 cudaError_t lvl_set_smem_limit(int bytes);
-int forward_lvl_occupancy(int threads, size_t smem, int st_samples);
+int forward_lvl_occupancy(int warps, size_t smem, int st_samples);
 int lvl_tile(int S);
 
 }  // namespace neat

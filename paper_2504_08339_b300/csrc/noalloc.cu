@@ -57,15 +57,25 @@ cudaError_t setup_device(int dev) {
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
-// bytes of the array a population of these sizes uses (0 for invalid sizes)
+// bytes of the array a population of these sizes uses (0 for invalid sizes):
+// the plan regions this call touches (headers, padded and packed programs,
+// both queue orders, counters; not the small-S batches, the compiled
+// programs or the workspace value slots) and the transform's order, layer and
+// layer-count arrays, each region rounded up to 256 bytes
 size_t scratch_needed(int P, int N, int C, int I, int O) {
   if (P < 0 || I < 1 || O < 1 || N < I + O || N > NEAT_MAX_NODES || C < 1 || C > NEAT_MAX_CONNS)
     return 0;
-  // the plan layout without its value array for large genomes (this call keeps
-  // every genome's values in shared memory)
   const neat::Layout L = neat::make_layout(P, N, C, I, O);
-  const size_t tr = sizeof(int32_t) * (2 * size_t(P) * N + size_t(P));
-  return align256(L.core) + align256(tr);
+  const size_t pn = sizeof(int32_t) * size_t(P) * N;
+  return L.base + 2 * align256(pn) + align256(sizeof(int32_t) * size_t(P));
+}
+
+// warps per CTA and shared memory of the sample-parallel forward with every
+// genome's values in shared memory
+void sp_launch_shape(int N, int &warps, size_t &smem) {
+  warps = 8;
+  while (warps > 1 && neat::forward_sp_smem(N, warps, 1) > size_t(96 * 1024)) --warps;
+  smem = neat::forward_sp_smem(N, warps, 1);
 }
 
 }  // namespace
@@ -88,34 +98,48 @@ extern "C" neat_status neat_forward_noalloc(const float *nodes, const float *con
                 (reinterpret_cast<uintptr_t>(outputs) % 4) != 0))
     return NEAT_ERR_ARG;
   if (in_pop_stride != 0 && in_pop_stride < int64_t(S) * I) return NEAT_ERR_ARG;
+  // (genome, 32-sample tile) work items are counted in 32 bits
+  if (int64_t(P) * ((int64_t(S) + 31) / 32) > int64_t(INT32_MAX)) return NEAT_ERR_UNSUPPORTED;
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return NEAT_ERR_CUDA;
-  if (setup_device(dev) != cudaSuccess) return NEAT_ERR_CUDA;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return neat::cuda_error_status(e);
+  if (dev < 0 || dev >= kMaxDevices) return NEAT_ERR_UNSUPPORTED;
+  e = setup_device(dev);
+  if (e != cudaSuccess) return neat::cuda_error_status(e);
+  // every shape check before the first launch
   if (neat::transform_smem(N, C) > size_t(g_smem_optin[dev])) return NEAT_ERR_UNSUPPORTED;
+  int warps = 1;
+  size_t smem = 0;
+  sp_launch_shape(N, warps, smem);
+  if (S > 0 && smem > size_t(g_smem_optin[dev])) return NEAT_ERR_UNSUPPORTED;
 
   unsigned char *base = g_scratch_ptr[dev];
   const neat::Layout L = neat::make_layout(P, N, C, I, O);
   neat::Ws w = neat::make_ws(base, L, P, N, C, I, O);
-  w.cnode = nullptr;  // only the core part of the layout lives in the array
+  // only the base regions of the layout live in the array
+  w.lvl_goff = nullptr;
+  w.lvl_first = nullptr;
+  w.lvl_loc = nullptr;
+  w.lvl_arena = nullptr;
+  w.cnode = nullptr;
   w.cpair = nullptr;
   w.cout = nullptr;
   w.clay = nullptr;
   w.sp_scratch = nullptr;
   w.sp_scratch_floats = 0;
-  int32_t *order = reinterpret_cast<int32_t *>(base + align256(L.core));
-  int32_t *layer = order + size_t(P) * N;
-  int32_t *n_layers = layer + size_t(P) * N;
+  int32_t *order = reinterpret_cast<int32_t *>(base + L.base);
+  int32_t *layer = reinterpret_cast<int32_t *>(base + L.base +
+                                               align256(sizeof(int32_t) * size_t(P) * N));
+  int32_t *n_layers = reinterpret_cast<int32_t *>(base + L.base +
+                                                  2 * align256(sizeof(int32_t) * size_t(P) * N));
 
-  // the queue counters must start at zero (the array keeps the last call's state)
-  cudaError_t e = cudaMemsetAsync(base + L.counters, 0, sizeof(uint32_t) * 64, stream);
+  // the queue counters and the failure word must start at zero (the array
+  // keeps the last call's state)
+  e = cudaMemsetAsync(base + L.counters, 0, sizeof(uint32_t) * 64, stream);
   if (e == cudaSuccess)
     e = neat::launch_transform(w, nodes, conns, order, layer, n_layers, gstatus, stream);
   if (e == cudaSuccess) e = neat::launch_queue_build(w, 0, stream);
   if (e == cudaSuccess && S > 0) {
-    int warps = 8;
-    while (warps > 1 && neat::forward_sp_smem(N, warps, 1) > size_t(96 * 1024)) --warps;
-    const size_t smem = neat::forward_sp_smem(N, warps, 1);
-    if (smem > size_t(g_smem_optin[dev])) return NEAT_ERR_UNSUPPORTED;
     const int occ = std::max(1, neat::forward_sp_occupancy(warps, smem, 1));
     const int64_t items = int64_t(P) * ((S + 31) / 32);
     const int grid = int(std::max<int64_t>(
@@ -123,5 +147,5 @@ extern "C" neat_status neat_forward_noalloc(const float *nodes, const float *con
     const neat::SpShape sh{warps, 1, N, grid, 0};
     e = neat::launch_forward_sp(w, inputs, in_pop_stride, S, outputs, nullptr, sh, stream);
   }
-  return e == cudaSuccess ? NEAT_OK : NEAT_ERR_CUDA;
+  return neat::cuda_error_status(e);
 }

@@ -107,7 +107,6 @@ extern "C" neat_status neat_apply_ops(float *nodes, float *conns, int P, int N, 
       (reinterpret_cast<uintptr_t>(ops) % 4) != 0 ||
       (op_status != nullptr && (reinterpret_cast<uintptr_t>(op_status) % 4) != 0))
     return NEAT_ERR_ARG;
-  return neat::launch_apply_ops(nodes, conns, P, N, C, ops, K, op_status, stream) == cudaSuccess
-             ? NEAT_OK
-             : NEAT_ERR_CUDA;
+  return neat::cuda_error_status(
+      neat::launch_apply_ops(nodes, conns, P, N, C, ops, K, op_status, stream));
 }

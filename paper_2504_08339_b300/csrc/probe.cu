@@ -5,7 +5,7 @@
 
 #include <cstdint>
 
-#include "neat.h"
+#include "neat_internal.cuh"
 
 namespace {
 
@@ -47,9 +47,9 @@ extern "C" neat_status neat_probe_smem_read(int blocks, int iters, uint32_t *sin
   if (blocks < 1 || iters < 0 || sink == nullptr || (reinterpret_cast<uintptr_t>(sink) % 4) != 0)
     return NEAT_ERR_ARG;
   const int bytes = kWords * int(sizeof(uint4));
-  if (cudaFuncSetAttribute(k_smem_probe, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) !=
-      cudaSuccess)
-    return NEAT_ERR_CUDA;
+  const cudaError_t e =
+      cudaFuncSetAttribute(k_smem_probe, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return neat::cuda_error_status(e);
   k_smem_probe<<<blocks, kThreads, bytes, stream>>>(iters, sink);
-  return cudaGetLastError() == cudaSuccess ? NEAT_OK : NEAT_ERR_CUDA;
+  return neat::cuda_error_status(cudaGetLastError());
 }

@@ -112,8 +112,6 @@ extern "C" neat_status neat_substrate_forward(const float *weights, int P, int K
     return NEAT_ERR_ARG;
   if (in_pop_stride != 0 && in_pop_stride < int64_t(S) * K) return NEAT_ERR_ARG;
   if ((int64_t(S) + 63) / 64 > 65535) return NEAT_ERR_UNSUPPORTED;
-  return neat::launch_substrate(weights, P, K, inputs, in_pop_stride, S, act, outputs, stream) ==
-                 cudaSuccess
-             ? NEAT_OK
-             : NEAT_ERR_CUDA;
+  return neat::cuda_error_status(
+      neat::launch_substrate(weights, P, K, inputs, in_pop_stride, S, act, outputs, stream));
 }

@@ -5,7 +5,11 @@ per environment step).  The transformation stage runs once; the T forward
 launches, each reading its step's inputs and writing its step's outputs, are
 captured together with it into a single CUDA graph, so a whole rollout costs
 one graph launch.  With `events=k` an event pair brackets every k-th forward
-launch inside the graph, which gives per-launch device durations.
+launch inside the graph (an interval then also holds the event records and
+the launch gap).  `capture_split` captures the transform and the T forward
+steps as two graphs instead, replayed back to back by `run_split`: an event
+recorded between them times the forward launches alone, with no event node
+among them.
 
 From host buffers (`run_host`) the rollout is a pipeline of chunks of
 consecutive steps, one graph each: the input copies of later chunks (a copy
@@ -47,6 +51,7 @@ class Rollout:
             mk = lambda: torch.cuda.Event(enable_timing=True, external=True)  # noqa: E731
             self.ev = {t: (mk(), mk()) for t in range(0, self.T, self.every)}
         self.graph = None
+        self.split = None       # (transform graph, graph of the T forward steps)
         self.parts = None       # [transform graph, graph of each chunk]
         self.copy_streams = None
 
@@ -80,6 +85,32 @@ class Rollout:
         with torch.cuda.graph(self.graph):
             self._body()
         return self
+
+    def capture_split(self):
+        """Capture the transform and the T forward steps as two graphs."""
+        self._warm()
+        g_tr, g_fwd = torch.cuda.CUDAGraph(), torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g_tr):
+            self.plan.transform(self.nodes, self.conns, out=self.tr)
+        with torch.cuda.graph(g_fwd):
+            self._steps(0, self.T, events=False)
+        self.split = (g_tr, g_fwd)
+        return self
+
+    def run_split(self, ev_mid=None, ev_end=None):
+        """One rollout as two graph launches (transform, then the T steps);
+        ev_mid / ev_end (optional CUDA events) are recorded after each, so
+        ev_mid.elapsed_time(ev_end) is the device time of the T forward
+        launches."""
+        if self.split is None:
+            self.capture_split()
+        self.split[0].replay()
+        if ev_mid is not None:
+            ev_mid.record()
+        self.split[1].replay()
+        if ev_end is not None:
+            ev_end.record()
+        return self.outputs
 
     def load(self, nodes, conns, inputs=None, non_blocking=True):
         """Copy a population (and optionally the input ring) into the graph's
