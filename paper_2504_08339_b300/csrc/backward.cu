@@ -55,22 +55,7 @@ __device__ __forceinline__ void cp_async_wait() {
 
 // z[j] = act(z[j]) for four values of one activation: the four evaluations
 // are independent and overlap
-template <int A>
-__device__ __forceinline__ void act_same4(float (&z)[4]) {
-#pragma unroll
-  for (int j = 0; j < 4; ++j) z[j] = act_apply(A, z[j]);
-}
-__device__ __forceinline__ void act4(int act, float (&z)[4]) {
-  switch (act) {
-    case NEAT_ACT_IDENTITY: break;
-    case NEAT_ACT_SIGMOID: act_same4<NEAT_ACT_SIGMOID>(z); break;
-    case NEAT_ACT_TANH: act_same4<NEAT_ACT_TANH>(z); break;
-    case NEAT_ACT_RELU: act_same4<NEAT_ACT_RELU>(z); break;
-    case NEAT_ACT_SIN: act_same4<NEAT_ACT_SIN>(z); break;
-    case NEAT_ACT_GAUSSIAN: act_same4<NEAT_ACT_GAUSSIAN>(z); break;
-    default: act_same4<NEAT_ACT_ABS>(z); break;
-  }
-}
+__device__ __forceinline__ void act4(int act, float (&z)[4]) { act_apply_n<4>(act, z); }
 
 // Ascending bitonic sort of a[0..n2) by the whole CTA, n2 a power of two.
 __device__ void bitonic_sort_u32(uint32_t *a, int n2) {

@@ -5,23 +5,25 @@
 // layer at a time, so genomes are evaluated in small BATCHES: all their
 // layer-r nodes are independent of each other (Sec. 3.3's order only requires
 // each node to follow its inputs), so a round evaluates the layer-r nodes of
-// every genome in the batch.  Each batch belongs to one warp, which stages the
-// batch program into its own shared-memory buffer and runs the rounds with
-// __syncwarp only: a shallow batch never waits for a deep one, and no
-// CTA-wide barrier sits in a round.  A round has two passes: one lane per
+// every genome in the batch.  Each batch belongs to one warp, which runs the
+// rounds with __syncwarp only: a shallow batch never waits for a deep one, and
+// no CTA-wide barrier sits in a round.  A round has two passes: one lane per
 // 4-edge chunk of incoming connections (the partial of the task's
 // aggregation), then one lane per node (combine the partials, bias, response,
-// activation).  The node pass evaluates each activation function present in
-// the round once for the whole warp (a warp-uniform branch per function), so
-// the mixed activations of a round cost one evaluation of each kind.
+// activation), the nodes of mixed activations evaluated side by side without
+// divergent branches.
 //
 // Transform time (k_lvl_plan, k_lvl_build): genomes in layer-sorted queue
-// order are cut into batches whose programs fit the per-warp buffer, and each
-// batch program is written contiguously (see BatchHead in neat_internal.cuh).
-// Run time (k_forward_lvl): a warp claims a batch and stages its program with
-// two bulk copies (cp.async.bulk with mbarrier completion and bounded waits):
-// the head part (genome ids, I/O slots, round table) first, so the step's
-// input loads are issued while the tasks and edges are still in flight.
+// order are cut into batches under a byte budget, and each batch program is
+// written contiguously (see BatchHead in neat_internal.cuh).
+// Run time (k_forward_lvl): a warp takes its first batch by its index and
+// claims the next ones from a counter.  It stages the batch's head part
+// (header and I/O slots) into its shared memory with a bulk copy
+// (cp.async.bulk, mbarrier completion, bounded wait) and reads the round
+// table, task records and edge chunks straight from global memory (L2), each
+// round's records one round ahead: the shared memory a warp holds is only its
+// head part, its value slots and its chunk partials, so that many warps fit
+// on an SM whatever the batch size.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -41,7 +43,9 @@ __device__ __forceinline__ int pow2_ceil_d(int x) {
 // Batch assignment (one CTA).  Every thread takes a contiguous run of the
 // layer-sorted queue (at least 128 genomes) and cuts it greedily: a genome
 // joins the current batch unless the batch's byte bound would exceed the
-// per-warp buffer, its value slots the slot cap, or it holds LVL_MAX_GENOMES.
+// budget, its value slots the slot cap (less the two constant slots), or it
+// already holds as many genomes as the head cap allows (at most
+// LVL_MAX_GENOMES).
 // Runs never share a batch, so the cut is exact and parallel; a run ends with
 // one partly filled batch.  Batch b's program sits at arena offset
 // goff[first genome of b] + LVL_BATCH_FIXED * b, goff being the prefix of the
@@ -52,8 +56,12 @@ __global__ void __launch_bounds__(PLAN_THREADS) k_lvl_plan(Ws w) {
   __shared__ long long sb[32];
   __shared__ int sn[32];
   const int P = w.P, T = blockDim.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int I = w.I, O = w.O, cap = w.lvl_budget, scap = w.lvl_slots;
+  const int I = w.I, O = w.O, cap = w.lvl_budget, scap = w.lvl_slots - LVL_CONST_SLOTS;
   const int per = max(128, (P + T - 1) / T);
+  // genomes per batch: the staged head (header, 4 B per genome id and I/O
+  // slot, alignment) fits the warp's head buffer
+  const int gmax = min(LVL_MAX_GENOMES,
+                       (lvl_head_cap(I, O) - int(sizeof(BatchHead)) - 15) / (4 * (1 + I + O)));
   const int q0 = min(tid * per, P), q1 = min(q0 + per, P);
   auto genome = [&](int q, int &pb, int &V) {
     const GenomeHdr h = w.hdr[w.qlvl[q]];
@@ -69,7 +77,7 @@ __global__ void __launch_bounds__(PLAN_THREADS) k_lvl_plan(Ws w) {
     for (int q = q0; q < q1; ++q) {
       int pb, V;
       genome(q, pb, V);
-      if (cg == 0 || cg == LVL_MAX_GENOMES || cb + pb > cap || cs + V > scap) {
+      if (cg == 0 || cg == gmax || cb + pb > cap || cs + V > scap) {
         ++nb;
         cb = LVL_BATCH_FIXED;
         cs = 0;
@@ -112,7 +120,7 @@ __global__ void __launch_bounds__(PLAN_THREADS) k_lvl_plan(Ws w) {
     for (int q = q0; q < q1; ++q) {
       int pb, V;
       genome(q, pb, V);
-      if (cg == 0 || cg == LVL_MAX_GENOMES || cb + pb > cap || cs + V > scap) {
+      if (cg == 0 || cg == gmax || cb + pb > cap || cs + V > scap) {
         ++b;
         w.lvl_first[b] = q;
         cb = LVL_BATCH_FIXED;
@@ -130,6 +138,8 @@ __global__ void __launch_bounds__(PLAN_THREADS) k_lvl_plan(Ws w) {
     const int total = sn[(T >> 5) - 1];
     w.lvl_first[total] = P;
     w.counters[CTR_NBATCH] = uint32_t(total);
+    // the forward's 64-bit claim counter (counters[CTR_LVL_ITEM..+1])
+    *reinterpret_cast<unsigned long long *>(w.counters + CTR_LVL_ITEM) = 0ull;
   }
 }
 
@@ -138,10 +148,11 @@ __global__ void __launch_bounds__(PLAN_THREADS) k_lvl_plan(Ws w) {
 constexpr int BLD_THREADS = 256;
 
 __global__ void __launch_bounds__(BLD_THREADS) k_lvl_build(Ws w) {
-  __shared__ int g_id[LVL_MAX_GENOMES + 1], g_V[LVL_MAX_GENOMES + 1], g_L[LVL_MAX_GENOMES + 1];
+  __shared__ int g_id[LVL_MAX_GENOMES + 1], g_V[LVL_MAX_GENOMES + 1];
   __shared__ int g_noff[LVL_MAX_GENOMES + 1], g_eoff[LVL_MAX_GENOMES + 1];
   __shared__ int g_slot[LVL_MAX_GENOMES + 1], g_NL[LVL_MAX_GENOMES + 1];
   __shared__ int s_nslots, s_ntasks, s_nrounds, s_bad;
+  __shared__ unsigned s_acts;
   __shared__ int wbuf[33];
   extern __shared__ __align__(16) unsigned char dsm[];
   uint64_t *keys = reinterpret_cast<uint64_t *>(dsm);               // [LVL_MAX_SLOTS]
@@ -162,14 +173,13 @@ __global__ void __launch_bounds__(BLD_THREADS) k_lvl_build(Ws w) {
     const bool ok = h.status == 0u;
     g_id[k] = g;
     g_V[k] = ok ? h.V : 0;
-    g_L[k] = ok ? h.L : 0;
     g_NL[k] = ok ? h.nlive : 0;
     g_noff[k] = h.node_off;
     g_eoff[k] = h.edge_off;
   }
   __syncthreads();
   if (tid == 0) {
-    int s = 0, nt = 0;
+    int s = LVL_CONST_SLOTS, nt = 0;  // slots 0 and 1 hold the constants 0 and 1
     for (int k = 0; k < ng; ++k) {
       g_slot[k] = s;
       s += g_V[k];
@@ -178,19 +188,22 @@ __global__ void __launch_bounds__(BLD_THREADS) k_lvl_build(Ws w) {
     g_slot[ng] = s;
     s_nslots = s;
     s_ntasks = nt;
+    s_acts = 0u;
   }
   __syncthreads();
   const int nslots = s_nslots, ntasks = s_ntasks;
   if (nslots > w.lvl_slots) return;  // cannot happen by construction of the cut
-  const int n2 = pow2_ceil_d(max(nslots, 1));
+  // sort keys over the genome slots (slot i + LVL_CONST_SLOTS)
+  const int ngs = nslots - LVL_CONST_SLOTS;
+  const int n2 = pow2_ceil_d(max(ngs, 1));
   // task keys: (layer, act, -cnt, genome, position); inputs and the nodes no
   // output depends on sort last (they are not tasks)
   for (int i = tid; i < n2; i += T) {
     uint64_t key = ~0ull;
-    if (i < nslots) {
+    if (i < ngs) {
       int k = 0;
-      while (g_slot[k + 1] <= i) ++k;
-      const int p = i - g_slot[k];
+      while (g_slot[k + 1] <= i + LVL_CONST_SLOTS) ++k;
+      const int p = i + LVL_CONST_SLOTS - g_slot[k];
       const NodeRec n = w.knode[g_noff[k] + p];
       if (!(n.meta & (META_INPUT | META_DEAD))) {
         const uint64_t lay = uint64_t(w.player[size_t(g_id[k]) * w.N + p]);
@@ -273,7 +286,7 @@ __global__ void __launch_bounds__(BLD_THREADS) k_lvl_build(Ws w) {
   }
   __syncthreads();
   const int nrounds = s_nrounds;
-  // program layout: head part (header, gio, round table), then tasks and edges
+  // program layout: head part (header, gio), then round table, tasks and edges
   const int G = 1 + I + O;
   const int off_gio = int(sizeof(BatchHead));
   const int off_round = (off_gio + 4 * ng * G + 15) & ~15;
@@ -293,12 +306,12 @@ __global__ void __launch_bounds__(BLD_THREADS) k_lvl_build(Ws w) {
     hd.n_genomes = ng; hd.n_slots = nslots; hd.n_rounds = nrounds; hd.n_tasks = ntasks;
     hd.n_chunks = nchunks; hd.off_round = off_round; hd.off_task = off_task;
     hd.off_eslot = off_eslot; hd.off_gio = off_gio; hd.prog_bytes = bytes; hd.off_ew = off_ew;
-    hd.pad = 0;
+    hd.act_mask = 0u;  // set once the task records are written
     *reinterpret_cast<BatchHead *>(base) = hd;
     BatchLoc loc;
     loc.off = arena_off;
     loc.bytes = bytes;
-    loc.head = off_task;
+    loc.head = off_round;
     loc.pad = 0;
     w.lvl_loc[b] = loc;
     // round table (same walk as above)
@@ -329,20 +342,34 @@ __global__ void __launch_bounds__(BLD_THREADS) k_lvl_build(Ws w) {
     t.chunk = uint32_t(cnt[j]);
     t.meta = task_meta(c, meta_act(n.meta), agg, g_slot[k] + p);
     tasks[j] = t;
+    atomicOr(&s_acts, 1u << meta_act(n.meta));
     const EdgeRec *src = w.kedge + g_eoff[k] + n.in_begin;
     const int e0 = 4 * cnt[j], e1 = 4 * cnt[j + 1];
     for (int e = 0; e < e1 - e0; ++e) {
+      const uint32_t tag = (e & 3) == 0 ? uint32_t(agg) << LVL_SLOT_BITS : 0u;
+      uint32_t slot;
+      float wt;
       if (e < c) {
         const EdgeRec er = src[e];
-        const uint32_t tag = (e & 3) == 0 ? uint32_t(agg) << LVL_SLOT_BITS : 0u;
-        eslot[e0 + e] = uint16_t(uint32_t(g_slot[k] + int(er.src)) | tag);
-        ew[e0 + e] = er.w;
-      } else {
-        eslot[e0 + e] = 0xffffu;
-        ew[e0 + e] = 0.0f;
+        slot = uint32_t(g_slot[k] + int(er.src));
+        wt = er.w;
+      } else if (agg == NEAT_AGG_PRODUCT) {  // w 1 on the constant 1: a factor 1
+        slot = 1u;
+        wt = 1.0f;
+      } else if (agg == NEAT_AGG_MAX) {      // the chunk's first edge again
+        const EdgeRec er = src[e & ~3];
+        slot = uint32_t(g_slot[k] + int(er.src));
+        wt = er.w;
+      } else {                               // w 0 on the constant 0: a term 0
+        slot = 0u;
+        wt = 0.0f;
       }
+      eslot[e0 + e] = uint16_t(slot | tag);
+      ew[e0 + e] = wt;
     }
   }
+  __syncthreads();
+  if (tid == 0) reinterpret_cast<BatchHead *>(base)->act_mask = s_acts;
   // genome ids and input / output slots (-1 for a rejected genome)
   for (int i = tid; i < ng * G; i += T) {
     const int k = i / G, f = i - k * G;
@@ -385,150 +412,276 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, int byte
 }
 
 // Shared-memory accesses of the rounds as explicit shared-space instructions
-// (the batch arrays are addressed through offsets read at run time; generic
-// accesses to them measured slower).  Volatile: never moved across the
-// round's __syncwarp.
+// on 32-bit shared addresses (no generic pointer arithmetic or address
+// conversion per access).  Volatile: never moved across the round's
+// __syncwarp.
 __device__ __forceinline__ unsigned sh_addr(const void *p) {
   return unsigned(__cvta_generic_to_shared(p));
 }
-__device__ __forceinline__ float lds_f32(const float *p) {
+__device__ __forceinline__ float lds_f32_a(uint32_t a) {
   float r;
-  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(r) : "r"(sh_addr(p)) : "memory");
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(r) : "r"(a) : "memory");
   return r;
 }
-__device__ __forceinline__ float4 lds_f32x4(const float4 *p) {
-  float4 r;
-  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-               : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w)
-               : "r"(sh_addr(p))
-               : "memory");
-  return r;
-}
-__device__ __forceinline__ uint2 lds_u32x2(const uint2 *p) {
-  uint2 r;
-  asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(r.x), "=r"(r.y) : "r"(sh_addr(p)) : "memory");
-  return r;
-}
-__device__ __forceinline__ uint32_t lds_u32(const uint32_t *p) {
-  uint32_t r;
-  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(r) : "r"(sh_addr(p)) : "memory");
-  return r;
-}
-__device__ __forceinline__ TaskRec lds_task(const TaskRec *p) {
-  uint32_t b, r, c, m;
-  asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
-               : "=r"(b), "=r"(r), "=r"(c), "=r"(m)
-               : "r"(sh_addr(p))
-               : "memory");
-  TaskRec t;
-  t.bias = __uint_as_float(b);
-  t.resp = __uint_as_float(r);
-  t.chunk = c;
-  t.meta = m;
-  return t;
-}
-__device__ __forceinline__ void sts_f32(float *p, float x) {
-  asm volatile("st.shared.f32 [%0], %1;" ::"r"(sh_addr(p)), "f"(x) : "memory");
+__device__ __forceinline__ void sts_f32_a(uint32_t a, float x) {
+  asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(x) : "memory");
 }
 
-// Activation of one value per lane, each function present among the warp's
-// lanes evaluated once (warp-uniform branches; lanes of other activations
-// keep their own result).  Called by all 32 lanes.  The same functions as
-// act_apply: sigmoid 1 / (1 + e^-z) and gaussian e^(-z^2) share one expf.
-__device__ __forceinline__ float act_warp(int a, float z) {
-  constexpr unsigned full = 0xffffffffu;
-  float y = z;  // identity
-  if (a == NEAT_ACT_RELU) y = fmaxf(z, 0.0f);
-  if (a == NEAT_ACT_ABS) y = fabsf(z);
-  if (__any_sync(full, a == NEAT_ACT_SIGMOID || a == NEAT_ACT_GAUSSIAN)) {
-    const float e = expf(a == NEAT_ACT_SIGMOID ? -z : -(z * z));
-    if (a == NEAT_ACT_SIGMOID) y = 1.0f / (1.0f + e);
-    if (a == NEAT_ACT_GAUSSIAN) y = e;
+// Activation of one value per lane, the lanes holding nodes of mixed
+// activations.  `mask` (bit a: some task of the batch has activation a; the
+// same on every lane) names the evaluations needed: one exponential per lane
+// serves sigmoid, tanh and gaussian (act_exp_arg), one reciprocal sigmoid and
+// tanh, one sine the sin nodes; each is evaluated on every lane and the
+// lane's result selected, so no branch diverges (but for sine arguments
+// beyond 6.5e6, which take sinf).  The same arithmetic as act_apply, value
+// for value.
+__device__ __forceinline__ float act_lanes(int a, float z, uint32_t mask) {
+  float y = sel_eq<NEAT_ACT_RELU>(a, fmaxf(z, 0.0f), z);
+  y = sel_eq<NEAT_ACT_ABS>(a, fabsf(z), y);
+  if (mask & ACT_BIT_EXP) {
+    const float e = am::exp_cw(act_exp_arg(a, z));
+    const float q = am::rcp_nr(1.0f + e);
+    y = sel_eq<NEAT_ACT_SIGMOID>(a, q, y);
+    y = sel_eq<NEAT_ACT_GAUSSIAN>(a, e, y);
+    if (mask & (1u << NEAT_ACT_TANH)) y = sel_eq<NEAT_ACT_TANH>(a, tanh_of(z, q), y);
   }
-  if (__any_sync(full, a == NEAT_ACT_TANH)) {
-    const float t = tanhf(z);
-    if (a == NEAT_ACT_TANH) y = t;
-  }
-  if (__any_sync(full, a == NEAT_ACT_SIN)) {
-    const float s = sinf(z);
-    if (a == NEAT_ACT_SIN) y = s;
+  if (mask & ACT_BIT_SIN) {
+    const float zs = sel_eq<NEAT_ACT_SIN>(a, z, 0.0f);
+    float sn = am::sin_cw(zs);
+    if (fabsf(zs) > am::SIN_ARG_MAX) sn = sinf(zs);  // rare
+    y = sel_eq<NEAT_ACT_SIN>(a, sn, y);
   }
   return y;
 }
 
-// One round of a warp's batch: tasks [t0, t1), chunks [c0, c1).
-//  chunk pass: one lane per (4-edge chunk, sample): the partial of the
-//    chunk's aggregation (sum: fma chain; product; max, NaN-ignoring) over
-//    its real edges into part[];
+// the same for two values per lane, evaluated side by side
+__device__ __forceinline__ void act_lanes2(int a0, float z0, int a1, float z1, uint32_t mask,
+                                           float &y0, float &y1) {
+  y0 = sel_eq<NEAT_ACT_RELU>(a0, fmaxf(z0, 0.0f), z0);
+  y0 = sel_eq<NEAT_ACT_ABS>(a0, fabsf(z0), y0);
+  y1 = sel_eq<NEAT_ACT_RELU>(a1, fmaxf(z1, 0.0f), z1);
+  y1 = sel_eq<NEAT_ACT_ABS>(a1, fabsf(z1), y1);
+  if (mask & ACT_BIT_EXP) {
+    const float e0 = am::exp_cw(act_exp_arg(a0, z0)), e1 = am::exp_cw(act_exp_arg(a1, z1));
+    const float q0 = am::rcp_nr(1.0f + e0), q1 = am::rcp_nr(1.0f + e1);
+    y0 = sel_eq<NEAT_ACT_SIGMOID>(a0, q0, y0);
+    y0 = sel_eq<NEAT_ACT_GAUSSIAN>(a0, e0, y0);
+    y1 = sel_eq<NEAT_ACT_SIGMOID>(a1, q1, y1);
+    y1 = sel_eq<NEAT_ACT_GAUSSIAN>(a1, e1, y1);
+    if (mask & (1u << NEAT_ACT_TANH)) {
+      y0 = sel_eq<NEAT_ACT_TANH>(a0, tanh_of(z0, q0), y0);
+      y1 = sel_eq<NEAT_ACT_TANH>(a1, tanh_of(z1, q1), y1);
+    }
+  }
+  if (mask & ACT_BIT_SIN) {
+    const float zs0 = sel_eq<NEAT_ACT_SIN>(a0, z0, 0.0f), zs1 = sel_eq<NEAT_ACT_SIN>(a1, z1, 0.0f);
+    float s0 = am::sin_cw(zs0), s1 = am::sin_cw(zs1);
+    if (fabsf(zs0) > am::SIN_ARG_MAX) s0 = sinf(zs0);  // rare
+    if (fabsf(zs1) > am::SIN_ARG_MAX) s1 = sinf(zs1);
+    y0 = sel_eq<NEAT_ACT_SIN>(a0, s0, y0);
+    y1 = sel_eq<NEAT_ACT_SIN>(a1, s1, y1);
+  }
+}
+
+// A batch program's arrays: the round table, task records and edge chunks in
+// global memory (read-only for the kernel, L2-resident within a rollout), the
+// value slots and chunk partials as shared addresses.
+struct BatchArrays {
+  const uint32_t *rt;
+  const uint4 *tasks;
+  const uint2 *eslot;
+  const uint4 *ew;
+  uint32_t part, v;  // shared addresses
+};
+struct ChunkRec {
+  uint2 sl;
+  uint4 w;  // the four weights (bits)
+};
+__device__ __forceinline__ ChunkRec ld_chunk(const BatchArrays &ba, int c) {
+  ChunkRec r;
+  r.sl = __ldg(ba.eslot + c);
+  r.w = __ldg(ba.ew + c);
+  return r;
+}
+__device__ __forceinline__ TaskRec ld_task(const BatchArrays &ba, int t) {
+  const uint4 q = __ldg(ba.tasks + t);
+  TaskRec r;
+  r.bias = __uint_as_float(q.x);
+  r.resp = __uint_as_float(q.y);
+  r.chunk = q.z;
+  r.meta = q.w;
+  return r;
+}
+
+// partial of one chunk for sample s of ST: the edges' terms folded with the
+// task's aggregation (sum: fma chain; product; max, NaN-ignoring; padding
+// edges are neutral for it, so every lane runs the same instructions)
+template <int ST>
+__device__ __forceinline__ float chunk_partial(const ChunkRec &r, uint32_t v, int s) {
+  const int agg = int((r.sl.x >> LVL_SLOT_BITS) & 3u);
+  const uint32_t vs = v + 4u * uint32_t(s);
+  const float x0 = lds_f32_a(vs + 4u * ST * (r.sl.x & (LVL_MAX_SLOTS - 1u)));
+  const float x1 = lds_f32_a(vs + 4u * ST * (r.sl.x >> 16));
+  const float x2 = lds_f32_a(vs + 4u * ST * (r.sl.y & 0xffffu));
+  const float x3 = lds_f32_a(vs + 4u * ST * (r.sl.y >> 16));
+  const float w0 = __uint_as_float(r.w.x), w1 = __uint_as_float(r.w.y),
+              w2 = __uint_as_float(r.w.z), w3 = __uint_as_float(r.w.w);
+  const float sum = fmaf(w3, x3, fmaf(w2, x2, fmaf(w1, x1, w0 * x0)));
+  const float p0 = w0 * x0, p1 = w1 * x1, p2 = w2 * x2, p3 = w3 * x3;
+  const float prod = ((p0 * p1) * p2) * p3;
+  const float mx = fmaxf(fmaxf(fmaxf(p0, p1), p2), p3);
+  return sel_eq<NEAT_AGG_PRODUCT>(agg, prod, sel_eq<NEAT_AGG_MAX>(agg, mx, sum));
+}
+
+// aggregate of one task from its chunk partials (sample s of ST): the first
+// two partials (nc <= 2 for three tasks in four) with the second masked out
+// when absent, the rest (in-degrees above 8) in a loop.  Index pc + 1 stays
+// inside the partial buffer (it holds the round's chunks plus 4, per sample).
+template <int ST>
+__device__ __forceinline__ float task_aggregate(const TaskRec &tk, uint32_t part, int c0, int s) {
+  const int cnt = task_cnt(tk.meta), agg = task_agg(tk.meta);
+  const int nc = (cnt + 3) >> 2;
+  const uint32_t pa = part + 4u * uint32_t((int(tk.chunk) - c0) * ST + s);
+  const float p0 = lds_f32_a(pa), p1 = lds_f32_a(pa + 4u * ST);
+  const bool two = nc >= 2;
+  float sum = p0 + sel_if(two, p1, 0.0f);
+  float prod = p0 * sel_if(two, p1, 1.0f);
+  float mx = fmaxf(p0, sel_if(two, p1, qnan()));
+  for (int k = 2; k < nc; ++k) {
+    const float p = lds_f32_a(pa + 4u * uint32_t(k * ST));
+    sum += p;
+    prod *= p;
+    mx = fmaxf(mx, p);
+  }
+  // empty aggregation: 0 for every aggregation
+  return sel_if(nc == 0, 0.0f,
+                sel_eq<NEAT_AGG_PRODUCT>(agg, prod, sel_eq<NEAT_AGG_MAX>(agg, mx, sum)));
+}
+
+// One round of a warp's batch, ST samples per lane item: tasks [t0, t1),
+// chunks [c0, c1), records read as they are needed (the form for several
+// samples per genome, where a round's work covers ST samples).
+//  chunk pass: one lane per (4-edge chunk, sample) into part[];
 //  node pass: one lane per (task, sample): the task's partials combined with
 //    its aggregation (a mean's 1/n is folded into its response), then
-//    v[slot] = act(b + r a).
+//    v[slot] = act(b + r a); lanes past the round's tasks evaluate the last
+//    task again and store nothing.
 template <int ST>
-__device__ __forceinline__ void warp_round(const TaskRec *__restrict__ tasks,
-                                           const uint2 *__restrict__ eslot,
-                                           const float4 *__restrict__ ew, float *part, float *v,
-                                           int t0, int t1, int c0, int c1, int lane) {
+__device__ __forceinline__ void warp_round(const BatchArrays &ba, int t0, int t1, int c0, int c1,
+                                           int lane, uint32_t mask) {
   const int na = (c1 - c0) * ST;
   for (int it = lane; it < na; it += 32) {
-    const int c = c0 + (ST == 1 ? it : it / ST);
-    const int s = ST == 1 ? 0 : it % ST;
-    const uint2 sl = lds_u32x2(eslot + c);
-    const float4 w4 = lds_f32x4(ew + c);
-    const uint32_t e0 = sl.x & 0xffffu;
-    const uint32_t q[4] = {e0 & (LVL_MAX_SLOTS - 1u), sl.x >> 16, sl.y & 0xffffu, sl.y >> 16};
-    const float wq[4] = {w4.x, w4.y, w4.z, w4.w};
-    const int agg = int(e0 >> LVL_SLOT_BITS);
-    float sum = 0.0f, prod = 1.0f, mx = qnan();
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      if (k == 0 || q[k] != 0xffffu) {
-        const float x = lds_f32(v + q[k] * ST + s);
-        sum = fmaf(wq[k], x, sum);
-        const float tv = wq[k] * x;
-        prod *= tv;
-        mx = fmaxf(mx, tv);
-      }
-    }
-    sts_f32(part + it, agg == NEAT_AGG_PRODUCT ? prod : (agg == NEAT_AGG_MAX ? mx : sum));
+    const int c = c0 + it / ST, s = it % ST;
+    sts_f32_a(ba.part + 4u * uint32_t(it), chunk_partial<ST>(ld_chunk(ba, c), ba.v, s));
   }
   __syncwarp();
   const int nt = (t1 - t0) * ST;
   for (int base = 0; base < nt; base += 32) {
-    const int it = base + lane;
-    int act = NEAT_ACT_IDENTITY, dst = -1;
-    float z = 0.0f;
-    if (it < nt) {
-      const int t = t0 + (ST == 1 ? it : it / ST);
-      const int s = ST == 1 ? 0 : it % ST;
-      const TaskRec tk = lds_task(tasks + t);
-      const int cnt = task_cnt(tk.meta), agg = task_agg(tk.meta);
-      const int pc = int(tk.chunk) - c0, nc = (cnt + 3) >> 2;
-      float sum = 0.0f, prod = 1.0f, mx = qnan();
-      // partials four at a time: the loads of a group are in flight together
-      for (int k = 0; k < nc; k += 4) {
-        float p[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) p[u] = k + u < nc ? lds_f32(part + (pc + k + u) * ST + s) : 0.0f;
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-          if (k + u < nc) {
-            sum += p[u];
-            prod *= p[u];
-            mx = fmaxf(mx, p[u]);
-          }
-      }
-      // empty aggregation: 0 for every aggregation
-      const float a = nc == 0 ? 0.0f
-                    : agg == NEAT_AGG_PRODUCT ? prod
-                    : agg == NEAT_AGG_MAX ? mx : sum;
-      z = fmaf(tk.resp, a, tk.bias);
-      act = task_act(tk.meta);
-      dst = task_slot(tk.meta) * ST + s;
-    }
-    const float y = act_warp(act, z);
-    if (dst >= 0) sts_f32(v + dst, y);
+    const int it = min(base + lane, nt - 1);
+    const int t = t0 + it / ST, s = it % ST;
+    const TaskRec tk = ld_task(ba, t);
+    const float y = act_lanes(task_act(tk.meta),
+                              fmaf(tk.resp, task_aggregate<ST>(tk, ba.part, c0, s), tk.bias), mask);
+    if (base + lane < nt) sts_f32_a(ba.v + 4u * uint32_t(task_slot(tk.meta) * ST + s), y);
   }
   __syncwarp();
+}
+
+// ---- one sample per genome (the rollout step).  Round r's records (the
+// lane's chunk c0 + lane and task t0 + lane, and chunk c0 + lane + 32 / task
+// t0 + lane + 32 when the round has more than 32; indices clamped to the
+// round, the extra lanes store nothing) are loaded at the start of round
+// r - 1, the round-table entries three rounds ahead, so that the L2 latency
+// hides under a round.  Rounds beyond 64 chunks or 64 tasks take the rest in
+// a loop.  The loop runs two rounds a trip with two record sets, so that no
+// record is copied between rounds.
+struct RoundRecs {
+  uint32_t ra, rb;  // the round's bounds and the next one's
+  ChunkRec ca, cb;
+  TaskRec ta, tb;
+};
+
+__device__ __forceinline__ void load_round(const BatchArrays &ba, uint32_t ra, uint32_t rb,
+                                           int lane, RoundRecs &x) {
+  const int t0 = int(ra & 0xffffu), t1 = int(rb & 0xffffu), c0 = int(ra >> 16), c1 = int(rb >> 16);
+  x.ra = ra;
+  x.rb = rb;
+  x.ca = ld_chunk(ba, min(c0 + lane, max(c1 - 1, c0)));
+  x.ta = ld_task(ba, min(t0 + lane, max(t1 - 1, t0)));
+  if (c1 - c0 > 32) x.cb = ld_chunk(ba, min(c0 + lane + 32, c1 - 1));
+  if (t1 - t0 > 32) x.tb = ld_task(ba, min(t0 + lane + 32, t1 - 1));
+}
+
+// one round from its records `x`; first loads the records of the next round
+// (bounds x.rb, rc) into `nx` when there is one (r + 1 < nr); `rq` holds the
+// round-table entries of rounds r + 2 and r + 3 (shifted as rounds go)
+__device__ __forceinline__ void one_round(const BatchArrays &ba, int r, int nr, int lane,
+                                          uint32_t mask, const RoundRecs &x, RoundRecs &nx,
+                                          uint32_t (&rq)[2]) {
+  const int t0 = int(x.ra & 0xffffu), t1 = int(x.rb & 0xffffu);
+  const int c0 = int(x.ra >> 16), c1 = int(x.rb >> 16);
+  const int na = c1 - c0, nt = t1 - t0;
+  const uint32_t rc = rq[0];
+  rq[0] = rq[1];
+  rq[1] = r + 4 <= nr ? __ldg(ba.rt + r + 4) : rq[1];
+  if (r + 1 < nr) load_round(ba, x.rb, rc, lane, nx);
+  const uint32_t part_l = ba.part + 4u * uint32_t(lane);
+  // chunk pass
+  if (na > 0) {
+    const float pa = chunk_partial<1>(x.ca, ba.v, 0);
+    if (na > 32) {
+      const float pb = chunk_partial<1>(x.cb, ba.v, 0);
+      if (lane + 32 < na) sts_f32_a(part_l + 128u, pb);
+      for (int it = lane + 64; it < na; it += 32)
+        sts_f32_a(ba.part + 4u * uint32_t(it), chunk_partial<1>(ld_chunk(ba, c0 + it), ba.v, 0));
+    }
+    if (lane < na) sts_f32_a(part_l, pa);
+  }
+  __syncwarp();
+  // node pass
+  if (nt > 32) {
+    float ya, yb;
+    act_lanes2(task_act(x.ta.meta),
+               fmaf(x.ta.resp, task_aggregate<1>(x.ta, ba.part, c0, 0), x.ta.bias),
+               task_act(x.tb.meta),
+               fmaf(x.tb.resp, task_aggregate<1>(x.tb, ba.part, c0, 0), x.tb.bias), mask, ya, yb);
+    if (lane + 32 < nt) sts_f32_a(ba.v + 4u * uint32_t(task_slot(x.tb.meta)), yb);
+    sts_f32_a(ba.v + 4u * uint32_t(task_slot(x.ta.meta)), ya);
+    // (warp-uniform trip count: act_lanes is called by all 32 lanes)
+    for (int base = 64; base < nt; base += 32) {
+      const TaskRec tk = ld_task(ba, t0 + min(base + lane, nt - 1));
+      const float y = act_lanes(task_act(tk.meta),
+                                fmaf(tk.resp, task_aggregate<1>(tk, ba.part, c0, 0), tk.bias),
+                                mask);
+      if (base + lane < nt) sts_f32_a(ba.v + 4u * uint32_t(task_slot(tk.meta)), y);
+    }
+  } else {
+    const float ya = act_lanes(task_act(x.ta.meta),
+                               fmaf(x.ta.resp, task_aggregate<1>(x.ta, ba.part, c0, 0), x.ta.bias),
+                               mask);
+    if (lane < nt) sts_f32_a(ba.v + 4u * uint32_t(task_slot(x.ta.meta)), ya);
+  }
+  __syncwarp();
+}
+
+// all rounds of a batch for one sample; the next batch is claimed when
+// round claim_at starts
+__device__ __forceinline__ void run_rounds_st1(const BatchArrays &ba, int nr, int lane,
+                                               uint32_t mask, int claim_at,
+                                               unsigned long long *claim, unsigned long long &old,
+                                               bool &claimed) {
+  if (nr <= 0) return;
+  uint32_t rq[2] = {nr >= 2 ? __ldg(ba.rt + 2) : 0u, nr >= 3 ? __ldg(ba.rt + 3) : 0u};
+  RoundRecs x0, x1;
+  load_round(ba, __ldg(ba.rt), __ldg(ba.rt + 1), lane, x0);
+  for (int r = 0; r < nr; r += 2) {
+    if (r >= claim_at && !claimed) {  // the next batch, a few rounds before this one ends
+      if (lane == 0) old = atomicAdd(claim, 1ull);
+      claimed = true;
+    }
+    one_round(ba, r, nr, lane, mask, x0, x1, rq);
+    if (r + 1 < nr) one_round(ba, r + 1, nr, lane, mask, x1, x0, rq);
+  }
 }
 
 // NaN outputs for the genomes of batch b (read from the queue, not from the
@@ -544,25 +697,25 @@ __device__ void nan_batch_outputs(const Ws &w, int b, int S, float *__restrict__
 
 constexpr int LVL_MAX_WARPS = 8;
 
+// (launch bound: one CTA of 8 warps per SM suffices for the registers, so the
+// compiler may use up to 255 a thread; a 64-register cap spilled the rounds)
 template <int ST>
-__global__ void __launch_bounds__(32 * LVL_MAX_WARPS) k_forward_lvl(
+__global__ void __launch_bounds__(32 * LVL_MAX_WARPS, 1) k_forward_lvl(
     Ws w, const float *__restrict__ inputs, int64_t stride, int S, float *__restrict__ out,
     int warp_bytes, int vals_bytes, int polls) {
   extern __shared__ __align__(128) unsigned char sm[];
-  __shared__ __align__(8) uint64_t mbar[2 * LVL_MAX_WARPS];
+  __shared__ __align__(8) uint64_t mbar[LVL_MAX_WARPS];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int I = w.I, O = w.O, G = 1 + I + O;
-  const int cap = w.lvl_budget;
-  unsigned char *buf = sm + size_t(wid) * warp_bytes;
-  float *v = reinterpret_cast<float *>(buf + cap);
-  float *part = reinterpret_cast<float *>(buf + cap + vals_bytes);
-  const uint32_t mb0 = uint32_t(__cvta_generic_to_shared(&mbar[2 * wid]));
-  const uint32_t mb1 = uint32_t(__cvta_generic_to_shared(&mbar[2 * wid + 1]));
-  const uint32_t buf_a = uint32_t(__cvta_generic_to_shared(buf));
+  const int hcap = lvl_head_cap(I, O);
+  unsigned char *head = sm + size_t(wid) * warp_bytes;
+  float *v = reinterpret_cast<float *>(head + hcap);
+  const uint32_t v_a = sh_addr(v), part_a = sh_addr(head + hcap + vals_bytes);
+  const uint32_t mb = uint32_t(__cvta_generic_to_shared(&mbar[wid]));
+  const uint32_t head_a = uint32_t(__cvta_generic_to_shared(head));
   const int nbatch = int(w.counters[CTR_NBATCH]);
   if (lane == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb0) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb1) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mb) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncwarp();
@@ -577,36 +730,53 @@ __global__ void __launch_bounds__(32 * LVL_MAX_WARPS) k_forward_lvl(
   }
   const int nwarps = gridDim.x * nw;
   uint32_t parity = 0;
-  // the first batch of each warp is its own index, later ones are claimed in
-  // order of finishing: no contended atomic at the start of the launch
+  // Batches: warp w starts with batch w; each warp claims its next batch
+  // (a few rounds before the current one ends, so the atomic's latency hides
+  // under the last rounds) from a 64-bit epoch counter that the transform
+  // zeroes.  Every launch makes exactly nbatch claims (one per batch
+  // processed: the successful ones plus one failed claim per warp that had a
+  // first batch), so claim index = counter mod nbatch and nothing is reset at
+  // the end.
+  unsigned long long *claim = reinterpret_cast<unsigned long long *>(w.counters + CTR_LVL_ITEM);
+  bool broken = false;  // a drain wait gave up: the buffer may still be written
   int b = blockIdx.x * nw + wid;
+  auto next_batch = [&](unsigned long long old) {
+    const int n = lane == 0 ? nwarps + int(old % (unsigned long long)nbatch) : 0;
+    return __shfl_sync(0xffffffffu, n, 0);
+  };
   while (b < nbatch) {
+    unsigned long long old = 0;
+    bool claimed = false;
+    if (broken) {  // keep the claim count: NaN the batch without staging it
+      if (lane == 0) old = atomicAdd(claim, 1ull);
+      nan_batch_outputs(w, b, S, out, lane);
+      __syncwarp();
+      b = next_batch(old);
+      continue;
+    }
     const BatchLoc loc = w.lvl_loc[b];
     const unsigned char *src = w.lvl_arena + loc.off;
     if (lane == 0) {
-      // the head part (up to off_task) and the rest, each on its own mbarrier;
-      // the previous batch's reads of the buffer are ordered before the copies
+      // the previous batch's reads of the head buffer are ordered before the copy
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb0),
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb),
                    "r"(loc.head)
                    : "memory");
-      bulk_g2s(buf_a, src, loc.head, mb0);
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mb1),
-                   "r"(loc.bytes - loc.head)
-                   : "memory");
-      bulk_g2s(buf_a + uint32_t(loc.head), src + loc.head, loc.bytes - loc.head, mb1);
+      bulk_g2s(head_a, src, loc.head, mb);
     }
-    bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(mb0, parity, polls));
+    // the round table's first entries and the batch's counts come from global
+    // memory while the head is in flight
+    const BatchHead hg = *reinterpret_cast<const BatchHead *>(src);
+    const BatchArrays ba{reinterpret_cast<const uint32_t *>(src + hg.off_round),
+                         reinterpret_cast<const uint4 *>(src + hg.off_task),
+                         reinterpret_cast<const uint2 *>(src + hg.off_eslot),
+                         reinterpret_cast<const uint4 *>(src + hg.off_ew), part_a, v_a};
+    const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(mb, parity, polls));
     if (ok) {
-      const BatchHead hd = *reinterpret_cast<const BatchHead *>(buf);
-      const int *gio = reinterpret_cast<const int *>(buf + hd.off_gio);
-      const uint32_t *rt = reinterpret_cast<const uint32_t *>(buf + hd.off_round);
-      const TaskRec *tasks = reinterpret_cast<const TaskRec *>(buf + hd.off_task);
-      const uint2 *eslot = reinterpret_cast<const uint2 *>(buf + hd.off_eslot);
-      const float4 *ew = reinterpret_cast<const float4 *>(buf + hd.off_ew);
+      const int *gio = reinterpret_cast<const int *>(head + hg.off_gio);
+      if (lane < 2 * ST) v[lane] = lane < ST ? 0.0f : 1.0f;  // the constant slots 0 and 1
       for (int s0 = 0; s0 < S; s0 += ST) {
-        // inputs (for the first tile while tasks and edges are still arriving)
-        for (int it = lane; it < hd.n_genomes * I * ST; it += 32) {
+        for (int it = lane; it < hg.n_genomes * I * ST; it += 32) {
           const int s = it % ST, r = it / ST, k = r / I, i = r - k * I;
           const int slot = gio[k * G + 1 + i];
           if (slot < 0) continue;
@@ -614,15 +784,18 @@ __global__ void __launch_bounds__(32 * LVL_MAX_WARPS) k_forward_lvl(
           v[slot * ST + s] =
               gs < S ? __ldg(inputs + size_t(gio[k * G]) * stride + size_t(gs) * I + i) : 0.0f;
         }
-        if (s0 == 0) ok = __all_sync(0xffffffffu, mbar_wait_bounded(mb1, parity, polls));
         __syncwarp();
-        if (!ok) break;
-        for (int r = 0; r < hd.n_rounds; ++r) {
-          const uint32_t r0 = lds_u32(rt + r), r1 = lds_u32(rt + r + 1);
-          warp_round<ST>(tasks, eslot, ew, part, v, int(r0 & 0xffffu), int(r1 & 0xffffu),
-                         int(r0 >> 16), int(r1 >> 16), lane);
+        if constexpr (ST == 1) {
+          run_rounds_st1(ba, hg.n_rounds, lane, hg.act_mask, max(hg.n_rounds - 3, 0), claim, old,
+                         claimed);
+        } else {
+          for (int r = 0; r < hg.n_rounds; ++r) {
+            const uint32_t r0 = __ldg(ba.rt + r), r1 = __ldg(ba.rt + r + 1);
+            warp_round<ST>(ba, int(r0 & 0xffffu), int(r1 & 0xffffu), int(r0 >> 16),
+                           int(r1 >> 16), lane, hg.act_mask);
+          }
         }
-        for (int it = lane; it < hd.n_genomes * O * ST; it += 32) {
+        for (int it = lane; it < hg.n_genomes * O * ST; it += 32) {
           const int s = it % ST, r = it / ST, k = r / O, j = r - k * O;
           const int gs = s0 + s;
           if (gs >= S) continue;
@@ -631,30 +804,17 @@ __global__ void __launch_bounds__(32 * LVL_MAX_WARPS) k_forward_lvl(
         }
         __syncwarp();
       }
-    }
-    if (!ok) {
-      // a staging wait gave up: report it, let both copies land (bounded)
+    } else {
+      // the staging wait gave up: report it, let the copy land (bounded)
       // before the buffer is reused, and NaN this batch's outputs
       if (lane == 0) atomicOr(w.counters + CTR_ERR, ERR_TMA_TIMEOUT);
-      const bool drained = __all_sync(0xffffffffu, mbar_wait_bounded(mb0, parity, DRAIN_POLLS) &&
-                                                       mbar_wait_bounded(mb1, parity, DRAIN_POLLS));
+      broken = !__all_sync(0xffffffffu, mbar_wait_bounded(mb, parity, DRAIN_POLLS));
       nan_batch_outputs(w, b, S, out, lane);
       __syncwarp();
-      if (!drained) break;  // the buffer may still be written: this warp stops
     }
+    if (!claimed && lane == 0) old = atomicAdd(claim, 1ull);
     parity ^= 1u;
-    int nxt = 0;
-    if (lane == 0) nxt = nwarps + int(atomicAdd(w.counters + CTR_LVL_ITEM, 1u));
-    b = __shfl_sync(0xffffffffu, nxt, 0);
-  }
-  // the last warp to finish resets the claim counters for the next launch
-  if (lane == 0) {
-    __threadfence();
-    const unsigned t = atomicAdd(w.counters + CTR_LVL_DONE, 1u);
-    if (t == unsigned(nwarps) - 1u) {
-      atomicExch(w.counters + CTR_LVL_ITEM, 0u);
-      atomicExch(w.counters + CTR_LVL_DONE, 0u);
-    }
+    b = next_batch(old);
   }
 }
 
@@ -667,8 +827,10 @@ size_t lvl_vals_bytes(const Ws &w, int st_samples) {
 }
 
 size_t lvl_warp_bytes(const Ws &w, int st_samples) {
-  const size_t part = (sizeof(float) * size_t(w.lvl_pcap) * st_samples + 15) & ~size_t(15);
-  return (size_t(w.lvl_budget) + lvl_vals_bytes(w, st_samples) + part + 127) & ~size_t(127);
+  // chunk partials of a round, plus 4 so that a clamped index past the round stays inside
+  const size_t part = (sizeof(float) * size_t(w.lvl_pcap + 4) * st_samples + 15) & ~size_t(15);
+  return (size_t(lvl_head_cap(w.I, w.O)) + lvl_vals_bytes(w, st_samples) + part + 127) &
+         ~size_t(127);
 }
 
 cudaError_t launch_lvl_build(const Ws &w, cudaStream_t st) {

@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/neat.h"
+#include "act_math.cuh"
 
 namespace neat {
 
@@ -86,27 +87,24 @@ __host__ __device__ inline int cpair_cap(int N, int C) { return (C + N) / 2 + 1;
 
 // -- level-synchronous batches (small-S form) --------------------------------------
 // Consecutive genomes of a layer-sorted queue are packed into small batches,
-// one per warp: a warp stages its batch program into its own shared-memory
-// buffer (lvl_budget bytes, fixed per plan) and evaluates the batch round by
-// round, synchronising with __syncwarp only.  A batch program lives in the
-// level arena as one contiguous, 16-byte aligned block:
+// one per warp at a time.  A batch program lives in the level arena as one
+// contiguous, 16-byte aligned block:
 //   BatchHead (48 B)
 //   gio       int32[n_genomes*(1+I+O)] genome id, input slots, output slots
+//   --- off_round: the head part above is staged into the warp's shared
+//       memory (a bulk copy); the rest is read from global memory (L2), each
+//       round's records one round ahead
 //   rounds    uint32[n_rounds + 1]     first task | first chunk << 16
-//   --- off_task: the head part above is staged first, the rest after it
 //   tasks     TaskRec[n_tasks]         non-input nodes, by (layer, act, -cnt)
-//   eslot     uint16[4 * n_chunks]     source value slot of each edge (0xffff: pad);
-//                                      the first entry of a chunk (never padding)
-//                                      carries the task's aggregation in bits 12-13
+//   eslot     uint16[4 * n_chunks]     source value slot of each edge; the first
+//                                      entry of a chunk carries the task's
+//                                      aggregation in bits 12-13
 //   ew        float[4 * n_chunks]      weight of each edge
-// Every task's incoming edges are padded to whole 4-edge chunks.  A round
-// holds tasks of one layer only and at most lvl_pcap chunks (a layer may span
-// several rounds).  Value slot of position p of the k-th genome of the batch
-// = slot_base(k) + p.
 struct __align__(16) BatchHead {
   int n_genomes, n_slots, n_rounds, n_tasks;
   int n_chunks, off_round, off_task, off_eslot;
-  int off_gio, prog_bytes, off_ew, pad;
+  int off_gio, prog_bytes, off_ew;
+  uint32_t act_mask;  // bit a set: some task has activation a
 };
 // where a batch program sits in the arena
 struct __align__(16) BatchLoc {
@@ -127,6 +125,7 @@ struct __align__(16) TaskRec {
 constexpr int LVL_SLOT_BITS = 12;
 constexpr int LVL_MAX_SLOTS = 1 << LVL_SLOT_BITS;  // 4096 value slots per batch
 constexpr int LVL_MAX_GENOMES = 64;                // genomes per batch (hard cap)
+constexpr int LVL_CONST_SLOTS = 2;                 // slots 0 and 1: the constants 0 and 1
 __host__ __device__ inline uint32_t task_meta(int cnt, int act, int agg, int slot) {
   return uint32_t(cnt) | (uint32_t(act) << 14) | (uint32_t(agg) << 17) | (uint32_t(slot) << 19);
 }
@@ -158,13 +157,21 @@ inline int lvl_min_budget(int N, int C, int I, int O) {
 constexpr int LVL_MIN_BUDGET = 8 * 1024;    // smallest budget knob (KiB granularity)
 constexpr int LVL_MAX_BUDGET = 160 * 1024;  // largest budget knob
 inline int lvl_budget(int N, int C, int I, int O, int knob_bytes = 0) {
-  // 12 KiB: about three locomotion-sized genomes per warp batch
-  const int want = knob_bytes > 0 ? knob_bytes : 12 * 1024;
+  // 16 KiB: about five locomotion-sized genomes per warp batch (rounds of
+  // about 21 tasks and 35 chunks); measured best of 12..48 KiB on the
+  // locomotion rollout
+  const int want = knob_bytes > 0 ? knob_bytes : 16 * 1024;
   const int m = lvl_min_budget(N, C, I, O);
   return want > m ? ((want + 127) & ~127) : m;
 }
-// value slots of a batch (>= N: any single genome fits)
-inline int lvl_slots(int N) { return N > 512 ? N : 512; }
+// bytes of a warp's staged head part (header and I/O slots): room for at
+// least one genome; the batch cut keeps every head within it
+__host__ __device__ inline int lvl_head_cap(int I, int O) {
+  const int one = (int(sizeof(BatchHead)) + 4 * (1 + I + O) + 15 + 127) & ~127;
+  return one > 2048 ? one : 2048;
+}
+// value slots of a batch (>= N + the two constants: any single genome fits)
+inline int lvl_slots(int N) { return N + LVL_CONST_SLOTS > 1024 ? N + LVL_CONST_SLOTS : 1024; }
 // chunks of a round (>= the chunks of any one task: in-degree <= min(N - 1, C))
 inline int lvl_pcap(int N, int C) {
   const int t = ((N - 1 < C ? N - 1 : C) + 3) / 4;
@@ -299,7 +306,8 @@ inline Ws make_ws(void *base, const Layout &L, int P, int N, int C, int I, int O
   return w;
 }
 
-// counters[] slots
+// counters[] slots (CTR_LVL_ITEM and CTR_LVL_DONE together: the level
+// forward's 64-bit claim counter)
 constexpr int CTR_FWD_ITEM = 0, CTR_FWD_DONE = 1, CTR_HN_ITEM = 2, CTR_HN_DONE = 3,
               CTR_LVL_ITEM = 4, CTR_LVL_DONE = 5, CTR_FWD_BIG = 6, CTR_SP_NBIG = 7,
               CTR_NBATCH = 8, CTR_ERR = 9, CTR_REC_ITEM = 10, CTR_REC_DONE = 11;
@@ -320,66 +328,89 @@ __host__ __device__ inline int sp_cost(const GenomeHdr &h) {
 // error bits in counters[CTR_ERR] (the NEAT_DEV_* bits of neat.h)
 constexpr uint32_t ERR_TMA_TIMEOUT = NEAT_DEV_TIMEOUT, ERR_SP_NO_SCRATCH = NEAT_DEV_NO_SCRATCH;
 
-// -- activations (textbook forms; accurate libm-style device functions) -----------
-__device__ __forceinline__ float act_apply(int a, float z) {
-  switch (a) {
-    case NEAT_ACT_IDENTITY: return z;
-    case NEAT_ACT_SIGMOID: return 1.0f / (1.0f + expf(-z));
-    case NEAT_ACT_TANH: return tanhf(z);
-    case NEAT_ACT_RELU: return fmaxf(z, 0.0f);
-    case NEAT_ACT_SIN: return sinf(z);
-    case NEAT_ACT_GAUSSIAN: return expf(-(z * z));
-    case NEAT_ACT_ABS: return fabsf(z);
-  }
-  return __int_as_float(0x7fc00000);
+// -- selects on small ids ------------------------------------------------------------
+// `id == K ? x : y` as one predicated select written in PTX.  A chain of plain
+// selects on the same id (activation or aggregation) is merged by the
+// compiler into a multiway switch, i.e. an indirect jump, which costs a warp
+// ~270 cycles on this GPU even when all lanes agree; these stay selects.
+template <int K>
+__device__ __forceinline__ float sel_eq(int id, float x, float y) {
+  float r;
+  asm("{\n\t.reg .pred p;\n\tsetp.eq.s32 p, %1, %2;\n\tselp.f32 %0, %3, %4, p;\n\t}"
+      : "=f"(r)
+      : "r"(id), "n"(K), "f"(x), "f"(y));
+  return r;
+}
+// c ? x : y for a condition the compiler must not turn into a branch
+__device__ __forceinline__ float sel_if(bool c, float x, float y) {
+  float r;
+  asm("{\n\t.reg .pred p;\n\tsetp.ne.s32 p, %1, 0;\n\tselp.f32 %0, %2, %3, p;\n\t}"
+      : "=f"(r)
+      : "r"(int(c)), "f"(x), "f"(y));
+  return r;
+}
+// bit `id` of `mask` (an opaque test: branches on it stay two-way)
+__device__ __forceinline__ bool bit_of(uint32_t mask, int id) {
+  uint32_t r;
+  asm("{\n\t.reg .u32 t;\n\tshr.b32 t, %1, %2;\n\tand.b32 %0, t, 1;\n\t}"
+      : "=r"(r)
+      : "r"(mask), "r"(id));
+  return r != 0u;
 }
 
-// act applied to n values with one dispatch (the same functions as act_apply)
+// -- activations (textbook forms, evaluated by the methods of act_math.cuh) --------
+constexpr uint32_t ACT_BIT_EXP = (1u << NEAT_ACT_SIGMOID) | (1u << NEAT_ACT_TANH) |
+                                 (1u << NEAT_ACT_GAUSSIAN);  // the functions built on e^x
+constexpr uint32_t ACT_BIT_SIN = 1u << NEAT_ACT_SIN;
+
+// argument of the one exponential an activation needs: e^{-z} (sigmoid),
+// e^{2|z|} (tanh), e^{-z^2} (gaussian); 0 for the others
+__device__ __forceinline__ float act_exp_arg(int a, float z) {
+  float x = sel_eq<NEAT_ACT_SIGMOID>(a, -z, 0.0f);
+  x = sel_eq<NEAT_ACT_TANH>(a, 2.0f * fabsf(z), x);
+  return sel_eq<NEAT_ACT_GAUSSIAN>(a, -(z * z), x);
+}
+
+__device__ __forceinline__ float sin_any(float z) {
+  if (fabsf(z) > am::SIN_ARG_MAX) return sinf(z);  // rare: arguments beyond the reduction
+  return am::sin_cw(z);
+}
+
+// tanh z from q = 1 / (e^{2|z|} + 1): the series below |z| = 0.55
+__device__ __forceinline__ float tanh_of(float z, float q) {
+  return sel_if(fabsf(z) < 0.55f, am::tanh_series(z), copysignf(fmaf(-2.0f, q, 1.0f), z));
+}
+
+// act_a(z) for an activation id a in [0, 6] (the transform rejects others);
+// the id is the same on every lane of the warp where this is called
+__device__ __forceinline__ float act_apply(int a, float z) {
+  float y = sel_eq<NEAT_ACT_RELU>(a, fmaxf(z, 0.0f), z);
+  y = sel_eq<NEAT_ACT_ABS>(a, fabsf(z), y);
+  if (bit_of(ACT_BIT_EXP, a)) {
+    const float e = am::exp_cw(act_exp_arg(a, z));
+    const float q = am::rcp_nr(1.0f + e);  // sigmoid; tanh's 1 / (e^{2|z|} + 1)
+    y = sel_eq<NEAT_ACT_SIGMOID>(a, q, sel_eq<NEAT_ACT_GAUSSIAN>(a, e, tanh_of(z, q)));
+  }
+  if (bit_of(ACT_BIT_SIN, a)) y = sin_any(z);
+  return y;
+}
+
+// act applied to n values with one activation id
 template <int n>
 __device__ __forceinline__ void act_apply_n(int a, float (&z)[n]) {
-  switch (a) {
-    case NEAT_ACT_IDENTITY: return;
-    case NEAT_ACT_SIGMOID:
 #pragma unroll
-      for (int j = 0; j < n; ++j) z[j] = 1.0f / (1.0f + expf(-z[j]));
-      return;
-    case NEAT_ACT_TANH:
-#pragma unroll
-      for (int j = 0; j < n; ++j) z[j] = tanhf(z[j]);
-      return;
-    case NEAT_ACT_RELU:
-#pragma unroll
-      for (int j = 0; j < n; ++j) z[j] = fmaxf(z[j], 0.0f);
-      return;
-    case NEAT_ACT_SIN:
-#pragma unroll
-      for (int j = 0; j < n; ++j) z[j] = sinf(z[j]);
-      return;
-    case NEAT_ACT_GAUSSIAN:
-#pragma unroll
-      for (int j = 0; j < n; ++j) z[j] = expf(-(z[j] * z[j]));
-      return;
-    case NEAT_ACT_ABS:
-#pragma unroll
-      for (int j = 0; j < n; ++j) z[j] = fabsf(z[j]);
-      return;
-  }
-#pragma unroll
-  for (int j = 0; j < n; ++j) z[j] = __int_as_float(0x7fc00000);
+  for (int j = 0; j < n; ++j) z[j] = act_apply(a, z[j]);
 }
 
 // d act / dz given z and v = act(z)
 __device__ __forceinline__ float act_deriv(int a, float z, float v) {
-  switch (a) {
-    case NEAT_ACT_IDENTITY: return 1.0f;
-    case NEAT_ACT_SIGMOID: return v * (1.0f - v);
-    case NEAT_ACT_TANH: return 1.0f - v * v;
-    case NEAT_ACT_RELU: return z > 0.0f ? 1.0f : 0.0f;
-    case NEAT_ACT_SIN: return cosf(z);
-    case NEAT_ACT_GAUSSIAN: return -2.0f * z * v;
-    case NEAT_ACT_ABS: return z > 0.0f ? 1.0f : (z < 0.0f ? -1.0f : 0.0f);
-  }
-  return __int_as_float(0x7fc00000);
+  float d = sel_eq<NEAT_ACT_SIGMOID>(a, v * (1.0f - v), 1.0f);
+  d = sel_eq<NEAT_ACT_TANH>(a, 1.0f - v * v, d);
+  d = sel_eq<NEAT_ACT_RELU>(a, z > 0.0f ? 1.0f : 0.0f, d);
+  d = sel_eq<NEAT_ACT_GAUSSIAN>(a, -2.0f * z * v, d);
+  d = sel_eq<NEAT_ACT_ABS>(a, z > 0.0f ? 1.0f : (z < 0.0f ? -1.0f : 0.0f), d);
+  if (bit_of(ACT_BIT_SIN, a)) d = fabsf(z) > am::SIN_ARG_MAX ? cosf(z) : am::cos_cw(z);
+  return d;
 }
 
 __device__ __forceinline__ float qnan() { return __int_as_float(0x7fc00000); }
@@ -449,8 +480,8 @@ int forward_sp_occupancy(int warps, size_t smem, int spl);
 int hyperneat_occupancy(int spl, int warps, size_t smem);
 // level-synchronous small-S form
 cudaError_t launch_lvl_build(const Ws &w, cudaStream_t st);
-// shared memory of one warp of the level-synchronous forward: its batch
-// program buffer, value slots and chunk partials for st_samples per tile
+// shared memory of one warp of the level-synchronous forward: its staged head
+// part, value slots and chunk partials for st_samples per tile
 size_t lvl_warp_bytes(const Ws &w, int st_samples);
 size_t lvl_vals_bytes(const Ws &w, int st_samples);
 // `warps` per CTA, each owning lvl_warp_bytes; a staging wait gives up after
