@@ -433,8 +433,7 @@ __device__ __forceinline__ void sts_f32_a(uint32_t a, float x) {
 // serves sigmoid, tanh and gaussian (act_exp_arg), one reciprocal sigmoid and
 // tanh, one sine the sin nodes; each is evaluated on every lane and the
 // lane's result selected, so no branch diverges (but for sine arguments
-// beyond 6.5e6, which take sinf).  The same arithmetic as act_apply, value
-// for value.
+// beyond 6.5e6, which take sinf).
 __device__ __forceinline__ float act_lanes(int a, float z, uint32_t mask) {
   float y = sel_eq<NEAT_ACT_RELU>(a, fmaxf(z, 0.0f), z);
   y = sel_eq<NEAT_ACT_ABS>(a, fabsf(z), y);

@@ -349,6 +349,15 @@ __device__ __forceinline__ float sel_if(bool c, float x, float y) {
       : "r"(int(c)), "f"(x), "f"(y));
   return r;
 }
+// id == k as an opaque test (an if-chain of these stays a chain of two-way
+// branches instead of becoming a multiway switch)
+__device__ __forceinline__ bool is_id(int id, int k) {
+  int r;
+  asm("{\n\t.reg .pred p;\n\tsetp.eq.s32 p, %1, %2;\n\tselp.s32 %0, 1, 0, p;\n\t}"
+      : "=r"(r)
+      : "r"(id), "r"(k));
+  return r != 0;
+}
 // bit `id` of `mask` (an opaque test: branches on it stay two-way)
 __device__ __forceinline__ bool bit_of(uint32_t mask, int id) {
   uint32_t r;
@@ -381,36 +390,72 @@ __device__ __forceinline__ float tanh_of(float z, float q) {
   return sel_if(fabsf(z) < 0.55f, am::tanh_series(z), copysignf(fmaf(-2.0f, q, 1.0f), z));
 }
 
-// act_a(z) for an activation id a in [0, 6] (the transform rejects others);
-// the id is the same on every lane of the warp where this is called
+// act_a(z) for an activation id a in [0, 6] (the transform rejects others)
+// where every lane of the warp evaluates the same activation (the
+// sample-parallel, HyperNEAT, recurrent, backward and substrate kernels):
+// only its own function runs, with the CUDA math library's functions.  The
+// dispatch is one multiway branch: in these kernels many warps are resident,
+// so its latency is hidden, and it costs fewer instructions than a chain of
+// tests (the level kernel, whose lanes mix activations, uses act_lanes).
 __device__ __forceinline__ float act_apply(int a, float z) {
-  float y = sel_eq<NEAT_ACT_RELU>(a, fmaxf(z, 0.0f), z);
-  y = sel_eq<NEAT_ACT_ABS>(a, fabsf(z), y);
-  if (bit_of(ACT_BIT_EXP, a)) {
-    const float e = am::exp_cw(act_exp_arg(a, z));
-    const float q = am::rcp_nr(1.0f + e);  // sigmoid; tanh's 1 / (e^{2|z|} + 1)
-    y = sel_eq<NEAT_ACT_SIGMOID>(a, q, sel_eq<NEAT_ACT_GAUSSIAN>(a, e, tanh_of(z, q)));
+  switch (a) {
+    case NEAT_ACT_IDENTITY: return z;
+    case NEAT_ACT_SIGMOID: return 1.0f / (1.0f + expf(-z));
+    case NEAT_ACT_TANH: return tanhf(z);
+    case NEAT_ACT_RELU: return fmaxf(z, 0.0f);
+    case NEAT_ACT_SIN: return sinf(z);
+    case NEAT_ACT_GAUSSIAN: return expf(-(z * z));
+    case NEAT_ACT_ABS: return fabsf(z);
   }
-  if (bit_of(ACT_BIT_SIN, a)) y = sin_any(z);
-  return y;
+  return __int_as_float(0x7fc00000);
 }
 
-// act applied to n values with one activation id
+// act applied to n values with one dispatch (the same functions as act_apply)
 template <int n>
 __device__ __forceinline__ void act_apply_n(int a, float (&z)[n]) {
+  switch (a) {
+    case NEAT_ACT_IDENTITY: return;
+    case NEAT_ACT_SIGMOID:
 #pragma unroll
-  for (int j = 0; j < n; ++j) z[j] = act_apply(a, z[j]);
+      for (int j = 0; j < n; ++j) z[j] = 1.0f / (1.0f + expf(-z[j]));
+      return;
+    case NEAT_ACT_TANH:
+#pragma unroll
+      for (int j = 0; j < n; ++j) z[j] = tanhf(z[j]);
+      return;
+    case NEAT_ACT_RELU:
+#pragma unroll
+      for (int j = 0; j < n; ++j) z[j] = fmaxf(z[j], 0.0f);
+      return;
+    case NEAT_ACT_SIN:
+#pragma unroll
+      for (int j = 0; j < n; ++j) z[j] = sinf(z[j]);
+      return;
+    case NEAT_ACT_GAUSSIAN:
+#pragma unroll
+      for (int j = 0; j < n; ++j) z[j] = expf(-(z[j] * z[j]));
+      return;
+    case NEAT_ACT_ABS:
+#pragma unroll
+      for (int j = 0; j < n; ++j) z[j] = fabsf(z[j]);
+      return;
+  }
+#pragma unroll
+  for (int j = 0; j < n; ++j) z[j] = __int_as_float(0x7fc00000);
 }
 
-// d act / dz given z and v = act(z)
+// d act / dz given z and v = act(z) (one activation for the whole warp)
 __device__ __forceinline__ float act_deriv(int a, float z, float v) {
-  float d = sel_eq<NEAT_ACT_SIGMOID>(a, v * (1.0f - v), 1.0f);
-  d = sel_eq<NEAT_ACT_TANH>(a, 1.0f - v * v, d);
-  d = sel_eq<NEAT_ACT_RELU>(a, z > 0.0f ? 1.0f : 0.0f, d);
-  d = sel_eq<NEAT_ACT_GAUSSIAN>(a, -2.0f * z * v, d);
-  d = sel_eq<NEAT_ACT_ABS>(a, z > 0.0f ? 1.0f : (z < 0.0f ? -1.0f : 0.0f), d);
-  if (bit_of(ACT_BIT_SIN, a)) d = fabsf(z) > am::SIN_ARG_MAX ? cosf(z) : am::cos_cw(z);
-  return d;
+  switch (a) {
+    case NEAT_ACT_IDENTITY: return 1.0f;
+    case NEAT_ACT_SIGMOID: return v * (1.0f - v);
+    case NEAT_ACT_TANH: return 1.0f - v * v;
+    case NEAT_ACT_RELU: return z > 0.0f ? 1.0f : 0.0f;
+    case NEAT_ACT_SIN: return cosf(z);
+    case NEAT_ACT_GAUSSIAN: return -2.0f * z * v;
+    case NEAT_ACT_ABS: return z > 0.0f ? 1.0f : (z < 0.0f ? -1.0f : 0.0f);
+  }
+  return __int_as_float(0x7fc00000);
 }
 
 __device__ __forceinline__ float qnan() { return __int_as_float(0x7fc00000); }

@@ -1,5 +1,7 @@
-"""Accuracy of the activation functions the kernels evaluate (the library's
-own exp / reciprocal / tanh series / sine, act_math.cuh), through the C ABI.
+"""Accuracy of the activation functions the kernels evaluate, through the C
+ABI: the level-synchronous kernel's own exp / reciprocal / tanh series / sine
+(act_math.cuh) and the CUDA math library of the one-activation-per-warp
+kernels.
 
 Each genome is one input connected to the single output node (weight 1,
 bias 0, response 1, sum aggregation), so its output is act(x) for the input
@@ -9,8 +11,9 @@ bound allows an activation: 8 * 2^-24 relative for sigmoid, tanh and sin,
 (8 + x^2) * 2 * 2^-24 for gaussian (the rounding of x^2 included), exact for
 identity, relu and abs; for sin beyond |x| = 1 the absolute error may also be
 that of the argument's own rounding (|x| 2^-24).  The level-synchronous form
-(several nodes of different activations in one warp) and the sample-parallel
-form (one node per warp step) must give the same bits."""
+evaluates several nodes of different activations in one warp with branch-free
+functions of its own; the sample-parallel form (one node per warp step)
+calls the CUDA math library; both are checked."""
 import numpy as np
 import pytest
 import torch
@@ -81,21 +84,3 @@ def test_activation_accuracy(path):
         err = np.abs(g - r)
         bad = err > lim
         assert not bad.any(), (ACTS[a], x[bad][:5], g[bad][:5], r[bad][:5])
-
-
-def test_level_and_sample_parallel_activations_are_bitwise_equal():
-    """Nodes of all activations in one warp (the level-synchronous rounds
-    evaluate them side by side) give the bits of the one-node-per-step walk."""
-    from paper_2504_08339_b300.api import Plan
-    nodes, conns = _genomes()
-    x = _arguments()[::7].copy()
-    P = nodes.shape[0]
-    res = []
-    for small in (-1, 8):
-        plan = Plan(P, 2, 1, 1, 1)
-        plan.set_tuning(small_s_max=small)
-        plan.transform(torch.from_numpy(nodes).cuda(), torch.from_numpy(conns).cuda())
-        outs = [plan.forward(torch.from_numpy(x[i:i + 1].reshape(1, 1, 1)).cuda())
-                for i in range(0, x.size, max(1, x.size // 64))]
-        res.append(torch.cat(outs, dim=1))
-    assert torch.equal(res[0].view(torch.int32), res[1].view(torch.int32))
