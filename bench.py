@@ -381,52 +381,69 @@ def grad_accuracy(g, r):
             "beyond_1e-4": int((rel > 1e-4).sum())}
 
 
-def cpu_baseline(name, cfg, spec, nodes, conns, seed, budget_steps=None, gpu=None):
-    """The FP64 oracle as it stands (single thread) on a bounded sample; with
-    `gpu` (callables returning the GPU's results for the same sample) also
-    the GPU's error against it, outside the timing."""
+def cpu_model():
+    """The host CPU's model name (from /proc/cpuinfo), or None."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
+def cpu_baseline(name, cfg, spec, nodes, conns, seed, budget_steps=None, gpu=None, threads=None):
+    """The FP64 oracle as it stands on a bounded sample, its genomes split
+    over `threads` host threads (default: every core); with `gpu` (callables
+    returning the GPU's results for the same sample) also the GPU's error
+    against it, outside the timing."""
     import oracle
     from workloads import locomotion_inputs, regression_batch, uneven_inputs
+    threads = int(threads or os.cpu_count() or 1)
+    scale = max(1, threads // 2)  # sample sizes grow with the cores (10-30 s of work)
     E, _ = enabled_counts(nodes, conns)
     gpu = gpu or {}
     acc = None
+    th = dict(threads=threads)
     t0 = time.perf_counter()
     if name == "locomotion":
-        R = budget_steps or 200
+        R = budget_steps or min(cfg["steps"], 200 * scale)
         x = np.concatenate([locomotion_inputs(seed, t, cfg["P"], spec.I) for t in range(R)], axis=1)
         t0 = time.perf_counter()
-        oracle.forward(nodes, conns, x, spec.I, spec.O)
+        oracle.forward(nodes, conns, x, spec.I, spec.O, **th)
         units = float(E.sum()) * R
         sample = f"all {cfg['P']} genomes x {R} of the {cfg['steps']} rollout steps"
         if "out" in gpu:
             dt = time.perf_counter() - t0
-            ref, bnd = oracle.forward(nodes, conns, x, spec.I, spec.O, with_bound=True)
+            ref, bnd = oracle.forward(nodes, conns, x, spec.I, spec.O, with_bound=True, **th)
             acc = {"outputs": accuracy(gpu["out"](R), ref, bnd)}
     elif name == "uneven":
-        k = budget_steps or 1500
+        k = budget_steps or min(cfg["P"], 1500 * scale)
         sel = np.arange(k)
         x = uneven_inputs(seed, 0, cfg["P"])[sel]
         t0 = time.perf_counter()
-        oracle.forward(nodes[sel], conns[sel], x, spec.I, spec.O)
+        oracle.forward(nodes[sel], conns[sel], x, spec.I, spec.O, **th)
         units = float(E[sel].sum()) * cfg["S"]
         sample = f"{k} of {cfg['P']} genomes x 1 step (S={cfg['S']})"
         if "out" in gpu:
             dt = time.perf_counter() - t0
-            ref, bnd = oracle.forward(nodes[sel], conns[sel], x, spec.I, spec.O, with_bound=True)
+            ref, bnd = oracle.forward(nodes[sel], conns[sel], x, spec.I, spec.O, with_bound=True,
+                                      **th)
             acc = {"outputs": accuracy(gpu["out"](k), ref, bnd)}
     elif name == "differentiation":
-        k = budget_steps or (64 if cfg["S"] <= 4096 else 4)
+        k = budget_steps or min(cfg["P"], (64 if cfg["S"] <= 4096 else 4) * scale)
         x, y = regression_batch(seed, cfg["S"])
         t0 = time.perf_counter()
-        out = oracle.forward(nodes[:k], conns[:k], x, spec.I, spec.O)
+        out = oracle.forward(nodes[:k], conns[:k], x, spec.I, spec.O, **th)
         go = (2.0 / cfg["S"]) * (out[..., 0] - y[None].astype(np.float64))
         grads = oracle.backward(nodes[:k], conns[:k], x, spec.I, spec.O, go[..., None],
-                                want_inputs=True)
+                                want_inputs=True, **th)
         units = float(E[:k].sum()) * cfg["S"]
         sample = f"{k} of {cfg['P']} genomes, forward + backward at S={cfg['S']}"
         if "out" in gpu:
             dt = time.perf_counter() - t0
-            _, bnd = oracle.forward(nodes[:k], conns[:k], x, spec.I, spec.O, with_bound=True)
+            _, bnd = oracle.forward(nodes[:k], conns[:k], x, spec.I, spec.O, with_bound=True, **th)
             acc = {"outputs": accuracy(gpu["out"](k), out, bnd)}
             gg = gpu["grads"](k)
             for nm, a_, b_ in zip(("grad_weight", "grad_bias", "grad_response", "grad_inputs"),
@@ -434,11 +451,11 @@ def cpu_baseline(name, cfg, spec, nodes, conns, seed, budget_steps=None, gpu=Non
                 if a_ is not None and b_ is not None and np.size(a_) == np.size(b_):
                     acc[nm] = grad_accuracy(a_, b_)
     elif name == "substrate":
-        k = budget_steps or 1
+        k = budget_steps or min(cfg["P"], scale)
         G, S = 32, 64
         q = np.arange(G ** 4)
         t0 = time.perf_counter()
-        w = oracle.hyperneat(nodes[:k], conns[:k], grid=G, qidx=q).reshape(k, G * G, G * G)
+        w = oracle.hyperneat(nodes[:k], conns[:k], grid=G, qidx=q, **th).reshape(k, G * G, G * G)
         x = np.random.default_rng(seed).standard_normal((k, S, G * G)).astype(np.float32)
         oracle.substrate(w, x, 2)
         units = float(E[:k].sum()) * G ** 4 + float(k) * S * G ** 4
@@ -449,9 +466,11 @@ def cpu_baseline(name, cfg, spec, nodes, conns, seed, budget_steps=None, gpu=Non
         ops = random_ops(seed, nodes[:k], conns[:k], spec.I, 16)
         t0 = time.perf_counter()
         n2, c2, _ = oracle.apply_ops(nodes[:k], conns[:k], ops)
-        oracle.transform(n2, c2, spec.I, spec.O)
+        oracle.transform(n2, c2, spec.I, spec.O, **th)
         dt = time.perf_counter() - t0
-        res = {"value": k / dt, "unit": "genomes/s", "cores": 1, "kind": "oracle",
+        res = {"value": k / dt, "unit": "genomes/s", "cores": threads, "kind": "oracle",
+               "cpu_model": cpu_model(),
+               "note": "operations on one thread, the transform on every core",
                "sample": f"{k} of {cfg['P']} genomes: 16 operations + transform",
                "seconds": round(dt, 3)}
         if "pop" in gpu:
@@ -468,34 +487,35 @@ def cpu_baseline(name, cfg, spec, nodes, conns, seed, budget_steps=None, gpu=Non
         sample = f"all pairs of {k} of {cfg['P']} genomes"
         dt = time.perf_counter() - t0
         res = {"value": units / dt, "unit": "genome-pairs/s", "cores": 1, "kind": "oracle",
-               "sample": sample, "seconds": round(dt, 3)}
+               "cpu_model": cpu_model(), "sample": sample, "seconds": round(dt, 3),
+               "note": "one thread: the oracle computes the pair matrix in one call"}
         if "dist" in gpu:
             res["gpu_vs_oracle"] = {"distances": accuracy(gpu["dist"](k), ref)}
         return res
     elif name == "recurrent":
-        k = budget_steps or 300
+        k = budget_steps or min(cfg["P"], 300 * scale)
         x = np.random.default_rng(seed).standard_normal((k, cfg["S"], spec.I)).astype(np.float32)
         t0 = time.perf_counter()
-        oracle.forward_recurrent(nodes[:k], conns[:k], x, spec.I, spec.O, cfg["T"])
+        oracle.forward_recurrent(nodes[:k], conns[:k], x, spec.I, spec.O, cfg["T"], **th)
         units = float(E[:k].sum()) * cfg["S"] * cfg["T"]
         sample = f"{k} of {cfg['P']} genomes x S={cfg['S']} x T={cfg['T']}"
         if "out" in gpu:
             dt = time.perf_counter() - t0
             ref, bnd = oracle.forward_recurrent(nodes[:k], conns[:k], x, spec.I, spec.O,
-                                                cfg["T"], with_bound=True)
+                                                cfg["T"], with_bound=True, **th)
             acc = {"outputs": accuracy(gpu["out"](k), ref, bnd)}
     elif name == "hyperneat":
-        k = budget_steps or 2
+        k = budget_steps or min(cfg["P"], 2 * scale)
         q = np.arange(32 ** 4 // 4)
         t0 = time.perf_counter()
-        oracle.hyperneat(nodes[:k], conns[:k], grid=32, qidx=q)
+        oracle.hyperneat(nodes[:k], conns[:k], grid=32, qidx=q, **th)
         units = float(E[:k].sum()) * q.size
         sample = f"{k} of {cfg['P']} CPPNs x a quarter of the 2^20 queries"
         if "weights" in gpu:
             dt = time.perf_counter() - t0
             ref, raw, bnd = oracle.hyperneat(nodes[:k], conns[:k], grid=32,
                                              thresh=cfg["thresh"], qidx=q, with_raw=True,
-                                             with_bound=True)
+                                             with_bound=True, **th)
             g = gpu["weights"](k, q)
             # queries whose raw value lies within the error band of the
             # threshold may be kept or zeroed either way: left out
@@ -508,7 +528,7 @@ def cpu_baseline(name, cfg, spec, nodes, conns, seed, budget_steps=None, gpu=Non
         from workloads import xor_inputs
         t0 = time.perf_counter()
         for _ in range(200):
-            oracle.forward(nodes, conns, xor_inputs(), spec.I, spec.O)
+            oracle.forward(nodes, conns, xor_inputs(), spec.I, spec.O, **th)
         units = float(E.sum()) * 4 * 200
         sample = "200 repetitions of the whole population"
         if "out" in gpu:
@@ -517,8 +537,8 @@ def cpu_baseline(name, cfg, spec, nodes, conns, seed, budget_steps=None, gpu=Non
             acc = {"outputs": accuracy(gpu["out"](None), ref, bnd)}
     if acc is None:
         dt = time.perf_counter() - t0
-    res = {"value": units / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
-           "seconds": round(dt, 3)}
+    res = {"value": units / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "cpu_model": cpu_model(), "sample": sample, "seconds": round(dt, 3)}
     if acc is not None:
         res["gpu_vs_oracle"] = acc
     return res
@@ -998,8 +1018,13 @@ def bench_reference(args, rank, world):
         return
     name = args.config
     cfg, spec, nodes, conns = workload(name, args.seed, args.pop)
+    # per-step samples of about a second of single-core work, grown with the
+    # cores the oracle's genome split uses
+    scale = max(1, (os.cpu_count() or 1) // 2)
     budget = {"locomotion": 8, "uneven": 150, "differentiation": 4, "hyperneat": 1, "tiny": None,
               "recurrent": 40, "distance": 200, "mutate": 2000, "substrate": 1}[name]
+    if budget is not None and name not in ("distance", "mutate"):
+        budget *= scale
     for _ in range(max(3, args.warmup)):
         cpu_baseline(name, cfg, spec, nodes, conns, args.seed, budget)
     vals, secs = [], 0.0
@@ -1008,9 +1033,7 @@ def bench_reference(args, rank, world):
         rec = cpu_baseline(name, cfg, spec, nodes, conns, args.seed, budget)
         vals.append(rec["value"])
         secs += rec["seconds"]
-    units = sum(v * 1.0 for v in vals)
     value = float(np.mean(vals))
-    del units
     line = {
         "impl": "reference",
         "metric": {"distance": "genome-pairs/s (compatibility distance)",
@@ -1021,8 +1044,8 @@ def bench_reference(args, rank, world):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": describe(name, cfg, spec), "name": name, "pop": cfg["P"],
                    "pop_override": args.pop is not None},
-        "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": rec["sample"], "value": value,
-                         "unit": rec["unit"]},
+        "cpu_baseline": {"kind": "oracle", "cores": rec["cores"], "cpu_model": rec.get("cpu_model"),
+                         "sample": rec["sample"], "value": value, "unit": rec["unit"]},
         "e2e": {"value": value, "unit": rec["unit"], "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }

@@ -88,6 +88,33 @@ def _ptr(a):
     return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
 
 
+def _over_genomes(P, threads, call):
+    """call(a, b) for contiguous genome slices [a, b) covering [0, P): one
+    slice per thread (the C calls release the GIL; genomes are independent
+    and the library keeps no global state, so the results are those of one
+    call over all of them)."""
+    threads = max(1, min(int(threads or 1), P))
+    if threads == 1:
+        rc = call(0, P)
+        assert rc == 0, rc
+        return
+    from concurrent.futures import ThreadPoolExecutor
+    cuts = [P * k // threads for k in range(threads + 1)]
+    with ThreadPoolExecutor(threads) as ex:
+        for rc in ex.map(lambda k: call(cuts[k], cuts[k + 1]), range(threads)):
+            assert rc == 0, rc
+
+
+def _rows(a, lo, hi):
+    """Pointer to rows [lo, hi) of a per-genome array (None stays None)."""
+    return None if a is None else _ptr(a[lo:hi])
+
+
+def _in_rows(x, stride, lo, hi):
+    """Pointer to the inputs of genomes [lo, hi) (shared inputs: the same set)."""
+    return _ptr(x) if stride == 0 else _ptr(x[lo:hi])
+
+
 def _f64(a):
     """The oracle reads double arrays; float32 data converts exactly."""
     return np.ascontiguousarray(a, dtype=np.float64)
@@ -100,7 +127,7 @@ def _shapes(nodes, conns):
     return P, N, C
 
 
-def transform(nodes, conns, I, O):
+def transform(nodes, conns, I, O, threads=1):
     """(order [P,N] i32, layer [P,N] i32, n_layers [P] i32, status [P] u32)."""
     nodes, conns = _f64(nodes), _f64(conns)
     P, N, C = _shapes(nodes, conns)
@@ -108,9 +135,10 @@ def transform(nodes, conns, I, O):
     layer = np.empty((P, N), np.int32)
     nl = np.empty(P, np.int32)
     st = np.empty(P, np.uint32)
-    rc = _load().or_transform(P, N, C, I, O, _ptr(nodes), _ptr(conns), _ptr(order), _ptr(layer),
-                              _ptr(nl), _ptr(st))
-    assert rc == 0, rc
+    lib = _load()
+    _over_genomes(P, threads, lambda a, b: lib.or_transform(
+        b - a, N, C, I, O, _rows(nodes, a, b), _rows(conns, a, b), _rows(order, a, b),
+        _rows(layer, a, b), _rows(nl, a, b), _rows(st, a, b)))
     return order, layer, nl, st
 
 
@@ -125,18 +153,20 @@ def _inputs(inputs, P, I):
     return inputs, stride, inputs.shape[1]
 
 
-def forward(nodes, conns, inputs, I, O, with_bound=False, with_values=False):
+def forward(nodes, conns, inputs, I, O, with_bound=False, with_values=False, threads=1):
     """outputs [P,S,O] f64 (and bound [P,S,O], values [P,S,N] when asked).
-    inputs is [P,S,I] or [1,S,I] (shared by every genome)."""
+    inputs is [P,S,I] or [1,S,I] (shared by every genome).  `threads` host
+    threads evaluate contiguous slices of the genomes."""
     nodes, conns = _f64(nodes), _f64(conns)
     P, N, C = _shapes(nodes, conns)
     inputs, stride, S = _inputs(inputs, P, I)
     out = np.empty((P, S, O), np.float64)
     bnd = np.empty((P, S, O), np.float64) if with_bound else None
     vals = np.empty((P, S, N), np.float64) if with_values else None
-    rc = _load().or_forward(P, N, C, I, O, _ptr(nodes), _ptr(conns), _ptr(inputs), stride, S,
-                            _ptr(out), _ptr(bnd), _ptr(vals))
-    assert rc == 0, rc
+    lib = _load()
+    _over_genomes(P, threads, lambda a, b: lib.or_forward(
+        b - a, N, C, I, O, _rows(nodes, a, b), _rows(conns, a, b), _in_rows(inputs, stride, a, b),
+        stride, S, _rows(out, a, b), _rows(bnd, a, b), _rows(vals, a, b)))
     res = [out]
     if with_bound:
         res.append(bnd)
@@ -145,7 +175,8 @@ def forward(nodes, conns, inputs, I, O, with_bound=False, with_values=False):
     return res[0] if len(res) == 1 else tuple(res)
 
 
-def forward_recurrent(nodes, conns, inputs, I, O, T, with_bound=False, with_status=False):
+def forward_recurrent(nodes, conns, inputs, I, O, T, with_bound=False, with_status=False,
+                      threads=1):
     """Recurrent calculation over T synchronous iterations (reading R11):
     outputs [P,S,O] f64 (and bound [P,S,O], status [P] u32 when asked)."""
     nodes, conns = _f64(nodes), _f64(conns)
@@ -154,9 +185,10 @@ def forward_recurrent(nodes, conns, inputs, I, O, T, with_bound=False, with_stat
     out = np.empty((P, S, O), np.float64)
     bnd = np.empty((P, S, O), np.float64) if with_bound else None
     st = np.empty(P, np.uint32) if with_status else None
-    rc = _load().or_forward_recurrent(P, N, C, I, O, _ptr(nodes), _ptr(conns), _ptr(inputs),
-                                      stride, S, int(T), _ptr(out), _ptr(bnd), _ptr(st))
-    assert rc == 0, rc
+    lib = _load()
+    _over_genomes(P, threads, lambda a, b: lib.or_forward_recurrent(
+        b - a, N, C, I, O, _rows(nodes, a, b), _rows(conns, a, b), _in_rows(inputs, stride, a, b),
+        stride, S, int(T), _rows(out, a, b), _rows(bnd, a, b), _rows(st, a, b)))
     res = [out]
     if with_bound:
         res.append(bnd)
@@ -204,7 +236,7 @@ def substrate(weights, inputs, act, with_bound=False):
     return (out, bnd) if with_bound else out
 
 
-def backward(nodes, conns, inputs, I, O, grad_out, want_inputs=True):
+def backward(nodes, conns, inputs, I, O, grad_out, want_inputs=True, threads=1):
     """(grad_w [P,C], grad_b [P,N], grad_r [P,N], grad_in [P,S,I] or None), all f64."""
     nodes, conns = _f64(nodes), _f64(conns)
     P, N, C = _shapes(nodes, conns)
@@ -215,13 +247,16 @@ def backward(nodes, conns, inputs, I, O, grad_out, want_inputs=True):
     gb = np.empty((P, N), np.float64)
     gr = np.empty((P, N), np.float64)
     gi = np.empty((P, S, I), np.float64) if want_inputs else None
-    rc = _load().or_backward(P, N, C, I, O, _ptr(nodes), _ptr(conns), _ptr(inputs), stride, S,
-                             _ptr(go), _ptr(gw), _ptr(gb), _ptr(gr), _ptr(gi))
-    assert rc == 0, rc
+    lib = _load()
+    _over_genomes(P, threads, lambda a, b: lib.or_backward(
+        b - a, N, C, I, O, _rows(nodes, a, b), _rows(conns, a, b), _in_rows(inputs, stride, a, b),
+        stride, S, _rows(go, a, b), _rows(gw, a, b), _rows(gb, a, b), _rows(gr, a, b),
+        _rows(gi, a, b)))
     return gw, gb, gr, gi
 
 
-def hyperneat(nodes, conns, grid=32, thresh=0.2, qidx=None, with_raw=False, with_bound=False):
+def hyperneat(nodes, conns, grid=32, thresh=0.2, qidx=None, with_raw=False, with_bound=False,
+              threads=1):
     """Thresholded substrate weights [P, nq] (nq = grid^4 when qidx is None)."""
     nodes, conns = _f64(nodes), _f64(conns)
     P, N, C = _shapes(nodes, conns)
@@ -233,9 +268,10 @@ def hyperneat(nodes, conns, grid=32, thresh=0.2, qidx=None, with_raw=False, with
     out = np.empty((P, nq), np.float64)
     raw = np.empty((P, nq), np.float64) if with_raw else None
     bnd = np.empty((P, nq), np.float64) if with_bound else None
-    rc = _load().or_hyperneat(P, N, C, _ptr(nodes), _ptr(conns), grid, thresh, _ptr(qidx),
-                              nq if qidx is not None else 0, _ptr(out), _ptr(raw), _ptr(bnd))
-    assert rc == 0, rc
+    lib = _load()
+    _over_genomes(P, threads, lambda a, b: lib.or_hyperneat(
+        b - a, N, C, _rows(nodes, a, b), _rows(conns, a, b), grid, thresh, _ptr(qidx),
+        nq if qidx is not None else 0, _rows(out, a, b), _rows(raw, a, b), _rows(bnd, a, b)))
     res = [out]
     if with_raw:
         res.append(raw)

@@ -219,4 +219,6 @@ def test_fp32_error_bound_covers_independent_fp32_evaluation():
                 fin = np.isfinite(ref[g, s])
                 assert (err[fin] <= 2 * bnd[g, s][fin] + 1e-30).all(), (g, s, err, bnd[g, s])
                 worst = max(worst, float((err[fin] / (bnd[g, s][fin] + 1e-300)).max(initial=0)))
-    assert worst > 1e-3   # the bound is not vacuous
+    # the bound is tight: an independent fp32 evaluation reaches 0.96 of it on
+    # this population, so a bound four times too loose fails here
+    assert worst > 0.25
