@@ -119,6 +119,9 @@ def parse_args():
                     choices=["locomotion", "uneven", "differentiation", "hyperneat", "tiny",
                              "recurrent", "distance", "mutate", "substrate"])
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--tune", default="auto", choices=["auto", "default"],
+                    help="auto: run the autotuner on the workload before timing "
+                         "(the chosen tuning is recorded in config.tuning)")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -418,6 +421,8 @@ def cpu_baseline(name, cfg, spec, nodes, conns, seed, budget_steps=None, gpu=Non
             dt = time.perf_counter() - t0
             ref, bnd = oracle.forward(nodes, conns, x, spec.I, spec.O, with_bound=True, **th)
             acc = {"outputs": accuracy(gpu["out"](R), ref, bnd)}
+            if "plain" in gpu:
+                acc["plain_outputs"] = accuracy(gpu["plain"](R), ref, bnd)
     elif name == "uneven":
         k = budget_steps or min(cfg["P"], 1500 * scale)
         sel = np.arange(k)
@@ -431,6 +436,8 @@ def cpu_baseline(name, cfg, spec, nodes, conns, seed, budget_steps=None, gpu=Non
             ref, bnd = oracle.forward(nodes[sel], conns[sel], x, spec.I, spec.O, with_bound=True,
                                       **th)
             acc = {"outputs": accuracy(gpu["out"](k), ref, bnd)}
+            if "plain" in gpu:
+                acc["plain_outputs"] = accuracy(gpu["plain"](k), ref, bnd)
     elif name == "differentiation":
         k = budget_steps or min(cfg["P"], (64 if cfg["S"] <= 4096 else 4) * scale)
         x, y = regression_batch(seed, cfg["S"])
@@ -535,6 +542,8 @@ def cpu_baseline(name, cfg, spec, nodes, conns, seed, budget_steps=None, gpu=Non
             dt = time.perf_counter() - t0
             ref, bnd = oracle.forward(nodes, conns, xor_inputs(), spec.I, spec.O, with_bound=True)
             acc = {"outputs": accuracy(gpu["out"](None), ref, bnd)}
+            if "plain" in gpu:
+                acc["plain_outputs"] = accuracy(gpu["plain"](None), ref, bnd)
     if acc is None:
         dt = time.perf_counter() - t0
     res = {"value": units / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
@@ -565,6 +574,21 @@ def bench_ours(args, rank, world, local, pg):
         plan.set_tuning(prune_dead=1)
     launches_per_step = 4  # transform, rank, offsets, pack
     extra = {}
+    tuning = {"mode": args.tune, "chosen": {}}
+
+    def autotune_on(x_dev):
+        """Run the autotuner on this population and one step's inputs (no
+        cache: every run measures), keeping the prune setting."""
+        if args.tune != "auto":
+            return
+        from paper_2504_08339_b300.autotune import autotune
+        d_n = torch.from_numpy(nodes).to(dev)
+        d_c = torch.from_numpy(conns).to(dev)
+        base = {"prune_dead": 1} if args.prune else {}
+        r = autotune(plan, d_n, d_c, x_dev, use_cache=False, base=base)
+        tuning["chosen"] = r["tuning"]
+        tuning["trials_us"] = {json.dumps(t["tuning"], sort_keys=True): round(1e3 * t["ms"], 2)
+                               for t in r["trials"]}
 
     if name in ("locomotion", "uneven", "tiny"):
         if name == "locomotion":
@@ -577,6 +601,7 @@ def bench_ours(args, rank, world, local, pg):
             from workloads import xor_inputs
             T, S, ring = 1, 4, 1
             host_in = np.repeat(xor_inputs(), P, 0)[None]
+        autotune_on(torch.from_numpy(np.ascontiguousarray(host_in[0])).to(dev))
         ro = Rollout(plan, T, S=S, ring=ring)
         ro.load(torch.from_numpy(nodes), torch.from_numpy(conns), torch.from_numpy(host_in),
                 non_blocking=False)
@@ -614,6 +639,7 @@ def bench_ours(args, rank, world, local, pg):
         saved = None if cfg.get("recompute") else torch.empty((P, spec.N, S), device=dev)
         out = torch.empty((P, S, spec.O), device=dev)
         go = torch.empty((P, S, spec.O), device=dev)
+        autotune_on(d_x)
         tr = plan.transform(d_nodes, d_conns)
         # ev[0]: the backward (the dominant kernel, the roofline's); ev_f: the forward
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))]
@@ -882,8 +908,11 @@ def bench_ours(args, rank, world, local, pg):
         torch.cuda.synchronize()
         pms = a.elapsed_time(b) / K
         plain = {"value": units_per_step / (pms / 1e3), "ms_per_step": round(pms, 3),
-                 "form": "padded programs, one CTA per (genome, 32 samples), one launch per "
-                         "rollout step, eager (no graph)", "steps": K}
+                 "form": ("padded programs, all N positions, one warp per (genome, sample) "
+                          "with lanes over a node's incoming edges"
+                          if S <= 8 else
+                          "padded programs, all N positions, one warp per (genome, 32 samples)")
+                 + ", one launch per rollout step, eager (no graph)", "steps": K}
 
     # ---- end to end through the public API from pinned host buffers
     e2e = None
@@ -984,6 +1013,16 @@ def bench_ours(args, rank, world, local, pg):
             gpu["dist"] = lambda k: np_(dist[:k, :k])
         elif name == "mutate":
             gpu["pop"] = lambda k: (np_(d_nodes[:k]), np_(d_conns[:k]))
+        if plain is not None:
+            # the plain form's outputs for the same sample (the plan holds the
+            # population's programs after the rollout)
+            def plain_out(k):
+                if name == "locomotion":
+                    o = torch.stack([plan.forward(ro.inputs[t], plain=True) for t in range(k)])
+                    return np_(o[:, :, 0, :].permute(1, 0, 2))
+                o = plan.forward(ro.inputs[0], plain=True)
+                return np_(o if name == "tiny" else o[:k])
+            gpu["plain"] = plain_out
         cpu = cpu_baseline(name, cfg, spec, nodes, conns, args.seed, gpu=gpu)
 
     gpu_launches = launches_per_step * args.steps
@@ -997,7 +1036,7 @@ def bench_ours(args, rank, world, local, pg):
         "data": "synthetic (seeded generators; random genomes shaped like the workload)",
         "config": {"workload": describe(name, cfg, spec), "name": name, "pop": P,
                    "pop_override": args.pop is not None,
-                   "prune_dead": bool(args.prune),
+                   "prune_dead": bool(args.prune), "tuning": tuning,
                    "enabled_conns_per_genome_mean": round(float(E.mean()), 2),
                    "valid_nodes_per_genome_mean": round(float(Vn.mean()), 2),
                    "form": "batched: persistent size-sorted queue over ragged-packed programs, "

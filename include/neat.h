@@ -153,7 +153,12 @@ neat_status neat_plan_destroy(neat_plan *plan);
  *                    which exercises the failure path).  A batch given up on
  *                    gets NaN outputs and sets NEAT_DEV_TIMEOUT; the warp
  *                    still waits (bounded) for its copies before it reuses
- *                    its buffer. */
+ *                    its buffer.
+ *   bwd_global       0 (default): the backward keeps each warp's value,
+ *                    aggregate and adjoint arrays in shared memory when a
+ *                    genome of the plan's N, C fits there, else in workspace
+ *                    slots (global memory, L2-resident); 1: always in
+ *                    workspace slots. */
 typedef struct {
   int warps_per_cta;
   int samples_per_lane;
@@ -162,6 +167,7 @@ typedef struct {
   int lvl_budget_kb;
   int prune_dead;
   int wait_polls;
+  int bwd_global;
 } neat_tuning;
 neat_status neat_plan_set_tuning(neat_plan *plan, const neat_tuning *t);
 neat_status neat_plan_get_tuning(const neat_plan *plan, neat_tuning *t);
@@ -227,8 +233,11 @@ neat_status neat_transform_recurrent(neat_plan *plan, const float *nodes, const 
 neat_status neat_forward_recurrent(neat_plan *plan, const float *inputs, int64_t in_pop_stride,
                                    int S, int T, float *outputs, cudaStream_t stream);
 
-/* Calculation stage, plain padded form (the comparison baseline): one CTA per
- * (genome, 32 samples) walking all N padded positions; no queue, no packing.
+/* Calculation stage, plain padded form (the comparison baseline): every
+ * genome walks all N padded positions of its padded program; no queue, no
+ * packing, no compiled programs.  Up to 8 samples per genome a one-warp CTA
+ * per (genome, sample) puts its lanes over each node's incoming edges; above
+ * that a one-warp CTA per (genome, 32 samples) puts them over samples.
  * Same arguments and results as neat_forward (no saved buffer). */
 neat_status neat_forward_plain(neat_plan *plan, const float *inputs, int64_t in_pop_stride, int S,
                                float *outputs, cudaStream_t stream);
@@ -243,12 +252,23 @@ neat_status neat_forward_plain(neat_plan *plan, const float *inputs, int64_t in_
  *   grad_weight  [P, C] f32 out, by connection row (0 on padding/disabled rows)
  *   grad_bias, grad_response [P, N] f32 out, by node row (0 on inputs/padding)
  *   grad_inputs  optional [P, S, I] f32 out (NULL to skip); with a shared input
- *                set (in_pop_stride 0) it is still written per genome.
+ *                set (in_pop_stride 0) it is still written per genome, and
+ *                neat_sum_genomes gives the shared set's gradient [S, I].
  * Sums over samples are deterministic (no floating-point atomics). */
 neat_status neat_backward(neat_plan *plan, const float *inputs, int64_t in_pop_stride, int S,
                           const float *grad_outputs, const float *saved, float *grad_weight,
                           float *grad_bias, float *grad_response, float *grad_inputs,
                           cudaStream_t stream);
+
+/* Sum over genomes: out[j] = sum_{g = 0 .. P-1} x[g * n + j] for 0 <= j < n,
+ * accumulated in double precision in ascending genome order and rounded to
+ * f32 once (deterministic).  Turns neat_backward's per-genome grad_inputs of
+ * an input set that every genome shares (in_pop_stride 0) into that set's
+ * gradient: the chain rule through the one tensor all genomes read.
+ *   x [P, n] f32 device, out [n] f32 device out (the ranges may not overlap).
+ * P = 0 writes zeros.  NEAT_ERR_ARG for negative sizes, NULL or unaligned
+ * pointers, or overlapping ranges (nothing launched). */
+neat_status neat_sum_genomes(const float *x, int P, int64_t n, float *out, cudaStream_t stream);
 
 /* HyperNEAT substrate query (the CPPN use of NEAT networks).  Requires I = 5,
  * O = 1.  For every genome and every (source, target) pair of a grid x grid

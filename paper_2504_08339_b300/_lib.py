@@ -25,7 +25,8 @@ SYMBOLS = ("neat_version", "neat_status_string", "neat_last_cuda_error",
            "neat_workspace_bytes", "neat_plan_create",
            "neat_plan_destroy", "neat_plan_set_tuning", "neat_plan_get_tuning",
            "neat_plan_device_errors", "neat_plan_check", "neat_transform",
-           "neat_forward", "neat_forward_plain", "neat_backward", "neat_hyperneat_query",
+           "neat_forward", "neat_forward_plain", "neat_backward", "neat_sum_genomes",
+           "neat_hyperneat_query",
            "neat_forward_noalloc", "neat_probe_smem_read", "neat_transform_recurrent",
            "neat_forward_recurrent", "neat_distance_scratch_bytes", "neat_distance",
            "neat_apply_ops", "neat_mutate_transform", "neat_substrate_forward",
@@ -40,7 +41,8 @@ class neat_tuning(ctypes.Structure):
     _fields_ = [("warps_per_cta", ctypes.c_int), ("samples_per_lane", ctypes.c_int),
                 ("lvl_threads", ctypes.c_int), ("small_s_max", ctypes.c_int),
                 ("lvl_budget_kb", ctypes.c_int),
-                ("prune_dead", ctypes.c_int), ("wait_polls", ctypes.c_int)]
+                ("prune_dead", ctypes.c_int), ("wait_polls", ctypes.c_int),
+                ("bwd_global", ctypes.c_int)]
 
 
 _lock = threading.Lock()
@@ -73,6 +75,7 @@ def load(path: str = LIB_PATH):
             "neat_transform": (i32, [vp, vp, vp, vp, vp, vp, vp, vp]),
             "neat_forward": (i32, [vp, vp, i64, i32, vp, vp, vp]),
             "neat_forward_plain": (i32, [vp, vp, i64, i32, vp, vp]),
+            "neat_sum_genomes": (i32, [vp, i32, i64, vp, vp]),
             "neat_backward": (i32, [vp, vp, i64, i32, vp, vp, vp, vp, vp, vp, vp]),
             "neat_hyperneat_query": (i32, [vp, i32, f32, vp, vp]),
             "neat_forward_noalloc": (i32, [vp, vp, i32, i32, i32, i32, i32, vp, i64, i32, vp, vp,

@@ -239,6 +239,23 @@ class Plan:
         _lib.check(code, "neat_backward")
         return gw, gb, gr, gi
 
+    def sum_genomes(self, x, out=None, stream=None):
+        """[P, ...] -> [...]: the sum over genomes (neat_sum_genomes), e.g. the
+        gradient of an input set all genomes share from backward()'s
+        per-genome grad_inputs."""
+        _need(x, "x", torch.float32)
+        if x.shape[0] != self.P:
+            raise ValueError(f"x: expected {self.P} genomes, got {x.shape[0]}")
+        n = 1
+        for d in x.shape[1:]:
+            n *= int(d)
+        if out is None:
+            out = torch.empty(x.shape[1:], dtype=torch.float32, device=x.device)
+        _need(out, "out", torch.float32, tuple(x.shape[1:]))
+        _lib.check(self._lib.neat_sum_genomes(_ptr(x), self.P, n, _ptr(out), _stream(stream)),
+                   "neat_sum_genomes")
+        return out
+
     def hyperneat(self, grid=32, thresh=0.2, out=None, stream=None):
         """Substrate weights [P, grid^2, grid^2] of every CPPN (I=5, O=1)."""
         G2 = grid * grid
@@ -306,16 +323,36 @@ def distance(nodes, conns, I, O, status=None, c_disjoint=1.0, c_homologous=0.5, 
     return out
 
 
+# Default cap on the per-node aggregates an autograd forward keeps for its
+# backward ([P, N, S] f32): above it the backward recomputes the forward
+# values inside its kernel instead of reading them.
+SAVED_BUDGET_BYTES = 8 << 30
+
+
+def saved_bytes(plan: Plan, S: int) -> int:
+    """Bytes of the aggregates a forward over S samples per genome saves."""
+    return 4 * plan.P * plan.N * int(S)
+
+
+def choose_store(plan: Plan, S: int, budget: int | None = None) -> bool:
+    """True when the saved aggregates fit the budget (default
+    SAVED_BUDGET_BYTES), False to recompute them in the backward."""
+    return saved_bytes(plan, S) <= (SAVED_BUDGET_BYTES if budget is None else int(budget))
+
+
 class NeatFunction(torch.autograd.Function):
     """outputs = network(nodes, conns)(inputs), differentiable with respect to
     the bias/response columns of nodes, the weight column of conns and the
-    inputs.  Stores the per-node aggregates when they fit (`store=True`),
-    otherwise the backward recomputes the forward values in the kernel."""
+    inputs.  Stores the per-node aggregates when `store` is True; recomputes
+    the forward values in the backward kernel when it is False; with `store`
+    None it stores them if they fit `budget` bytes (choose_store)."""
 
     @staticmethod
-    def forward(ctx, plan: Plan, nodes, conns, inputs, store: bool = True):
+    def forward(ctx, plan: Plan, nodes, conns, inputs, store=None, budget=None):
         plan.transform(nodes, conns)
         S = inputs.shape[1]
+        if store is None:
+            store = choose_store(plan, S, budget)
         saved = None
         if store:
             saved = torch.empty((plan.P, plan.N, S), dtype=torch.float32, device=inputs.device)
@@ -346,10 +383,12 @@ class NeatFunction(torch.autograd.Function):
             g_conns = torch.zeros_like(conns)
             g_conns[..., 2] = gw
         if ctx.needs_input_grad[3]:
-            g_inputs = gi if inputs.shape[0] == plan.P else gi.sum(0, keepdim=True)
-        return None, g_nodes, g_conns, g_inputs, None
+            g_inputs = gi if inputs.shape[0] == plan.P else plan.sum_genomes(gi).unsqueeze(0)
+        return None, g_nodes, g_conns, g_inputs, None, None
 
 
-def evaluate(plan: Plan, nodes, conns, inputs, store: bool = True):
-    """Differentiable population evaluation (see NeatFunction)."""
-    return NeatFunction.apply(plan, nodes, conns, inputs, store)
+def evaluate(plan: Plan, nodes, conns, inputs, store=None, budget=None):
+    """Differentiable population evaluation (see NeatFunction): `store` True
+    keeps the aggregates, False recomputes them in the backward, None (the
+    default) keeps them if 4 P N S bytes fit `budget` (SAVED_BUDGET_BYTES)."""
+    return NeatFunction.apply(plan, nodes, conns, inputs, store, budget)

@@ -59,14 +59,16 @@ def _time_forward(plan: Plan, inputs, out, reps: int) -> float:
 
 
 def autotune(plan: Plan, nodes, conns, inputs, reps: int = 20, use_cache: bool = True,
-             verbose: bool = False) -> dict:
+             verbose: bool = False, base: dict | None = None) -> dict:
     """Pick and apply the fastest tuning for this population and input shape.
+    `base` holds knobs every candidate keeps (e.g. prune_dead=1).
     Returns {"tuning": {...}, "ms": best forward time, "trials": [...]}."""
+    base = dict(base or {})
     S = inputs.shape[1]
     en = (~torch.isnan(conns[..., 0])) & (conns[..., 3] != 0) & ~torch.isnan(conns[..., 3])
     n_edges = float(en.sum(dim=1).float().mean())
     n_nodes = float((~torch.isnan(nodes[..., 0])).sum(dim=1).float().mean())
-    sig = _signature(plan, S, n_edges, n_nodes)
+    sig = _signature(plan, S, n_edges, n_nodes) + "|" + json.dumps(base, sort_keys=True)
     path = _cache_path()
     cache = {}
     if use_cache and os.path.exists(path):
@@ -83,6 +85,7 @@ def autotune(plan: Plan, nodes, conns, inputs, reps: int = 20, use_cache: bool =
     out = torch.empty((plan.P, S, plan.O), dtype=torch.float32, device=inputs.device)
     trials = []
     for cand in candidates(plan, S):
+        cand = {**base, **cand}
         plan.set_tuning(**cand)
         plan.transform(nodes, conns)
         ms = _time_forward(plan, inputs, out, reps)

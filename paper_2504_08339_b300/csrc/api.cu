@@ -105,6 +105,8 @@ int wait_polls(const neat_plan *p) {
 // genome runs on as many warps as its per-warp blocks fit (smaller genomes,
 // more warps).
 constexpr int kBackwardWarps = 16;
+// warps of a backward CTA whose warp arrays sit in workspace slots
+constexpr int kBackwardGlobalWarps = 8;
 
 neat_status check_inputs(const neat_plan *p, const float *inputs, int64_t stride, int S) {
   if (S < 0) return NEAT_ERR_ARG;
@@ -218,6 +220,7 @@ neat_status neat_plan_set_tuning(neat_plan *plan, const neat_tuning *t) {
     return NEAT_ERR_ARG;
   if (t->prune_dead != 0 && t->prune_dead != 1) return NEAT_ERR_ARG;
   if (t->wait_polls < -1) return NEAT_ERR_ARG;
+  if (t->bwd_global != 0 && t->bwd_global != 1) return NEAT_ERR_ARG;
   plan->tune = *t;
   return NEAT_OK;
 }
@@ -339,13 +342,45 @@ neat_status neat_backward(neat_plan *plan, const float *inputs, int64_t in_pop_s
       (grad_outputs && !aligned(grad_outputs, 4)) || (saved && !aligned(saved, 4)) ||
       (grad_inputs && !aligned(grad_inputs, 4)))
     return NEAT_ERR_ARG;
-  if (neat::backward_smem(plan->N, plan->C, 1) > size_t(plan->smem_optin))
-    return NEAT_ERR_UNSUPPORTED;
-  const int smem = int(std::min<size_t>(size_t(plan->smem_optin),
-                                        neat::backward_smem(plan->N, plan->C, kBackwardWarps)));
+  const bool fits = neat::backward_smem(plan->N, plan->C, 1) <= size_t(plan->smem_optin);
+  if (fits && plan->tune.bwd_global == 0) {
+    const int smem = int(std::min<size_t>(size_t(plan->smem_optin),
+                                          neat::backward_smem(plan->N, plan->C, kBackwardWarps)));
+    return cuda_status(neat::launch_backward(plan->w, inputs, in_pop_stride, S, grad_outputs,
+                                             saved, grad_weight, grad_bias, grad_response,
+                                             grad_inputs, kBackwardWarps, smem, false, 0, stream));
+  }
+  // per-warp arrays in workspace slots: the records and pull lists must still
+  // fit in shared memory, and one CTA's slots in the workspace
+  const size_t fixed = neat::backward_fixed_smem(plan->N, plan->C);
+  if (fixed > size_t(plan->smem_optin)) return NEAT_ERR_UNSUPPORTED;
+  const size_t cta_floats = size_t(kBackwardGlobalWarps) *
+                            neat::backward_slot_floats(plan->N, plan->C);
+  const int64_t slots = plan->w.sp_scratch ? int64_t(plan->w.sp_scratch_floats / cta_floats) : 0;
+  const int occ = neat::backward_occupancy(true, kBackwardGlobalWarps, int(fixed));
+  int64_t ctas = std::min<int64_t>({int64_t(plan->P), int64_t(plan->sm_count) * std::max(1, occ),
+                                    slots});
+  if (ctas < 1) return NEAT_ERR_WORKSPACE;
   return cuda_status(neat::launch_backward(plan->w, inputs, in_pop_stride, S, grad_outputs, saved,
                                            grad_weight, grad_bias, grad_response, grad_inputs,
-                                           kBackwardWarps, smem, stream));
+                                           kBackwardGlobalWarps, int(fixed), true, int(ctas),
+                                           stream));
+}
+
+neat_status neat_sum_genomes(const float *x, int P, int64_t n, float *out, cudaStream_t stream) {
+  if (P < 0 || n < 0) return NEAT_ERR_ARG;
+  if (n == 0) return NEAT_OK;
+  if (out == nullptr || !aligned(out, 4) || (P > 0 && (x == nullptr || !aligned(x, 4))))
+    return NEAT_ERR_ARG;
+  // the two ranges may not overlap
+  const uintptr_t xb = reinterpret_cast<uintptr_t>(x), ob = reinterpret_cast<uintptr_t>(out);
+  if (P > 0 && xb < ob + sizeof(float) * size_t(n) && ob < xb + sizeof(float) * size_t(P) * size_t(n))
+    return NEAT_ERR_ARG;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = neat::launch_sum_genomes(x, P, n, out, sms, stream);
+  return cuda_status(e);
 }
 
 neat_status neat_hyperneat_query(neat_plan *plan, int grid, float thresh, float *weights,

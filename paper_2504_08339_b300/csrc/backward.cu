@@ -29,6 +29,7 @@
 // lane) and a lane's row (row p, columns s) both hit 32 distinct banks.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "neat_internal.cuh"
@@ -135,6 +136,22 @@ __device__ __forceinline__ uint2 lds_u32x2(unsigned a) {
   return r;
 }
 
+// Reads of a warp's [V][RS] arrays: explicit shared loads when the arrays sit
+// in shared memory, plain loads when they sit in a workspace slot in global
+// memory (the path of genomes too large for shared memory).
+template <bool GM>
+struct WArr {
+  unsigned a;
+  __device__ __forceinline__ explicit WArr(const float *p) : a(sh_addr(p)) {}
+  __device__ __forceinline__ float operator[](unsigned i) const { return lds_f32(a + 4u * i); }
+};
+template <>
+struct WArr<true> {
+  const float *p;
+  __device__ __forceinline__ explicit WArr(const float *q) : p(q) {}
+  __device__ __forceinline__ float operator[](unsigned i) const { return p[i]; }
+};
+
 // One pulled edge: consumer position and c_e * w_e.
 struct __align__(8) PullRec {
   int dst;
@@ -148,16 +165,23 @@ struct __align__(8) PullRec {
 // bwd_warp_floats(V, E) floats: v, a, adjoint [V][RS] and the warp's
 // accumulators for dL/dw [E], dL/db [V], dL/dr [V].  As many warps work as
 // blocks of this genome's size fit; the others only join the barriers.
-__host__ __device__ inline size_t bwd_fixed_bytes(int N, int C) {
+// (with_keys false: the sort keys live in the CTA's workspace slots instead)
+__host__ __device__ inline size_t bwd_fixed_bytes(int N, int C, bool with_keys = true) {
   return sizeof(NodeRec) * size_t(N) + sizeof(EdgeRec) * size_t(C) +
          2 * sizeof(float) * size_t(C) + sizeof(PullRec) * size_t(C) +
-         2 * sizeof(int) * size_t(N) + sizeof(uint32_t) * size_t(pow2_at_least(C));
+         2 * sizeof(int) * size_t(N) +
+         (with_keys ? sizeof(uint32_t) * size_t(pow2_at_least(C)) : 0);
 }
 __host__ __device__ inline size_t bwd_warp_floats(int V, int E) {
   return 3 * size_t(V) * RS + size_t(E) + 2 * size_t(V);
 }
 
-template <bool STORED>
+// GM = false: one CTA per genome (grid P), the warp arrays in shared memory
+// after the records.  GM = true: a grid of fewer CTAs, each walking genomes
+// blockIdx.x, blockIdx.x + gridDim.x, ... of the queue with its warps' arrays
+// in its own workspace slots (blockDim / 32 blocks of bwd_warp_floats(N, C)
+// floats at sp_scratch + blockIdx.x * that).
+template <bool STORED, bool GM>
 __global__ void k_backward(Ws w, const float *__restrict__ inputs, int64_t stride, int S,
                            const float *__restrict__ gout, const float *__restrict__ saved,
                            float *__restrict__ gw_out, float *__restrict__ gb_out,
@@ -166,7 +190,15 @@ __global__ void k_backward(Ws w, const float *__restrict__ inputs, int64_t strid
   extern __shared__ __align__(16) float sm[];
   const int N = w.N, C = w.C, I = w.I, O = w.O;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int g = w.qorder[blockIdx.x];
+  const size_t cta_floats = size_t(blockDim.x >> 5) * bwd_warp_floats(N, C);
+  if (GM && (w.sp_scratch == nullptr || (size_t(blockIdx.x) + 1) * cta_floats > w.sp_scratch_floats)) {
+    // no slot for this CTA (the host sizes the grid so that this never
+    // happens): report it; its genomes keep the gradients they had
+    if (threadIdx.x == 0) atomicOr(w.counters + CTR_ERR, ERR_SP_NO_SCRATCH);
+    return;
+  }
+  for (int qi = blockIdx.x; qi < w.P; qi += gridDim.x) {
+  const int g = w.qorder[qi];
   const GenomeHdr h = w.hdr[g];
   for (int j = threadIdx.x; j < C; j += blockDim.x) gw_out[size_t(g) * C + j] = 0.0f;
   for (int r = threadIdx.x; r < N; r += blockDim.x) {
@@ -178,7 +210,7 @@ __global__ void k_backward(Ws w, const float *__restrict__ inputs, int64_t strid
     if (gi_out != nullptr)
       for (size_t i = threadIdx.x; i < size_t(S) * I; i += blockDim.x)
         gi_out[size_t(g) * S * I + i] = 0.0f;
-    return;
+    continue;  // (uniform over the CTA: nothing shared was touched)
   }
   const int V = h.V, E = h.E;
   NodeRec *nr = reinterpret_cast<NodeRec *>(sm);          // [N] node records
@@ -188,11 +220,16 @@ __global__ void k_backward(Ws w, const float *__restrict__ inputs, int64_t strid
   PullRec *pull = reinterpret_cast<PullRec *>(edst + C);  // [C] pull lists
   int *pbeg = reinterpret_cast<int *>(pull + C);          // [N] pull list of position p:
   int *pend = pbeg + N;                                   // [N]   pull[pbeg[p] .. pend[p])
-  uint32_t *keys = reinterpret_cast<uint32_t *>(pend + N);  // [pow2(C)] sort keys
-  float *wbase = reinterpret_cast<float *>(keys + pow2_at_least(C));
+  // [pow2(C)] sort keys: in shared memory after the lists, or (GM) at the
+  // start of the CTA's slots, which the warps' arrays only use after the sort
+  float *wbase = GM ? w.sp_scratch + size_t(blockIdx.x) * cta_floats
+                    : reinterpret_cast<float *>(reinterpret_cast<uint32_t *>(pend + N) +
+                                                pow2_at_least(C));
+  uint32_t *keys = GM ? reinterpret_cast<uint32_t *>(wbase) : reinterpret_cast<uint32_t *>(pend + N);
   const size_t pw = bwd_warp_floats(V, E);
-  const int nwa = min(int(blockDim.x >> 5),
-                      int((size_t(smem_bytes) - bwd_fixed_bytes(N, C)) / (pw * sizeof(float))));
+  const int nwa = GM ? int(blockDim.x >> 5)
+                     : min(int(blockDim.x >> 5),
+                           int((size_t(smem_bytes) - bwd_fixed_bytes(N, C)) / (pw * sizeof(float))));
   float *v = wbase + size_t(wid) * pw + lane;  // values   [V][RS] (this lane's column)
   float *av = v + V * RS;                      // agg      [V][RS]
   float *dv = av + V * RS;                     // adjoints [V][RS]; u once a node is done
@@ -210,7 +247,8 @@ __global__ void k_backward(Ws w, const float *__restrict__ inputs, int64_t strid
     pend[p] = 0;
   }
   for (int k = threadIdx.x; k < E; k += blockDim.x) er[k] = w.kedge[h.edge_off + k];
-  for (size_t i = threadIdx.x; i < size_t(nwa) * pw; i += blockDim.x) wbase[i] = 0.0f;
+  if (!GM)
+    for (size_t i = threadIdx.x; i < size_t(nwa) * pw; i += blockDim.x) wbase[i] = 0.0f;
   for (int p = threadIdx.x; p < V; p += blockDim.x) {
     const NodeRec n = w.knode[h.node_off + p];
     if (n.meta & META_INPUT) continue;
@@ -241,6 +279,15 @@ __global__ void k_backward(Ws w, const float *__restrict__ inputs, int64_t strid
       pend[src] = i + 1;
   }
   __syncthreads();
+  if (GM) {
+    // the keys are done with; only the accumulators start at zero: every
+    // value row a walk reads is written first in each tile (the rows of dead
+    // positions are never read)
+    const size_t acc = size_t(E) + 2 * size_t(V);
+    for (size_t i = threadIdx.x; i < size_t(nwa) * acc; i += blockDim.x)
+      wbase[(i / acc) * pw + 3 * size_t(V) * RS + i % acc] = 0.0f;
+    __syncthreads();
+  }
 
   for (int tile = wid; wid < nwa && tile < tiles; tile += nwa) {
     const int s = tile * 32 + lane;
@@ -252,13 +299,18 @@ __global__ void k_backward(Ws w, const float *__restrict__ inputs, int64_t strid
       // saved[g][p][s]: every position's line requested at once, straight
       // into shared memory
       const float *col = saved + size_t(g) * N * S + s;
-      if (active) {
+      if (GM) {
         for (int p = 0; p < V; ++p)
-          if (!(nr[p].meta & META_DEAD)) cp_async4(av + p * RS, col + size_t(p) * S);
+          if (!(nr[p].meta & META_DEAD)) av[p * RS] = active ? __ldg(col + size_t(p) * S) : 0.0f;
       } else {
-        for (int p = 0; p < V; ++p) av[p * RS] = 0.0f;
+        if (active) {
+          for (int p = 0; p < V; ++p)
+            if (!(nr[p].meta & META_DEAD)) cp_async4(av + p * RS, col + size_t(p) * S);
+        } else {
+          for (int p = 0; p < V; ++p) av[p * RS] = 0.0f;
+        }
+        cp_async_wait();
       }
-      cp_async_wait();
       // v = act(b + r a) of every node, four positions at a time
       for (int p = 0; p < V; p += 4) {
         NodeRec n[4];
@@ -293,11 +345,12 @@ __global__ void k_backward(Ws w, const float *__restrict__ inputs, int64_t strid
         } else if (agg == NEAT_AGG_SUM || agg == NEAT_AGG_MEAN) {
           float a0 = 0.0f, a1 = 0.0f;
           int k = 0;
-          const unsigned ea = sh_addr(e), va = sh_addr(v);
+          const unsigned ea = sh_addr(e);
+          const WArr<GM> va(v);
           for (; k + 1 < cnt; k += 2) {
             const uint2 e0 = lds_u32x2(ea + 8u * unsigned(k)), e1 = lds_u32x2(ea + 8u * unsigned(k + 1));
-            a0 = fmaf(__uint_as_float(e0.y), lds_f32(va + 4u * RS * e0.x), a0);
-            a1 = fmaf(__uint_as_float(e1.y), lds_f32(va + 4u * RS * e1.x), a1);
+            a0 = fmaf(__uint_as_float(e0.y), va[RS * e0.x], a0);
+            a1 = fmaf(__uint_as_float(e1.y), va[RS * e1.x], a1);
           }
           if (k < cnt) a0 = fmaf(e[k].w, v[e[k].src * RS], a0);
           a = a0 + a1;
@@ -325,12 +378,13 @@ __global__ void k_backward(Ws w, const float *__restrict__ inputs, int64_t strid
       const int b = pbeg[p], en = pend[p];
       float d0 = dv[p * RS], d1 = 0.0f;
       int i = b;
-      const unsigned pla = sh_addr(pull), dva = sh_addr(dv);
+      const unsigned pla = sh_addr(pull);
+      const WArr<GM> dva(dv);
       for (; i + 3 < en; i += 4) {
         const uint2 r0 = lds_u32x2(pla + 8u * unsigned(i)), r1 = lds_u32x2(pla + 8u * unsigned(i + 1)),
                     r2 = lds_u32x2(pla + 8u * unsigned(i + 2)), r3 = lds_u32x2(pla + 8u * unsigned(i + 3));
-        const float u0 = lds_f32(dva + 4u * RS * r0.x), u1 = lds_f32(dva + 4u * RS * r1.x),
-                    u2 = lds_f32(dva + 4u * RS * r2.x), u3 = lds_f32(dva + 4u * RS * r3.x);
+        const float u0 = dva[RS * r0.x], u1 = dva[RS * r1.x], u2 = dva[RS * r2.x],
+                    u3 = dva[RS * r3.x];
         d0 = fmaf(__uint_as_float(r0.y), u0, d0);
         d1 = fmaf(__uint_as_float(r1.y), u1, d1);
         d0 = fmaf(__uint_as_float(r2.y), u2, d0);
@@ -338,7 +392,7 @@ __global__ void k_backward(Ws w, const float *__restrict__ inputs, int64_t strid
       }
       for (; i < en; ++i) {
         const uint2 r0 = lds_u32x2(pla + 8u * unsigned(i));
-        d0 = fmaf(__uint_as_float(r0.y), lds_f32(dva + 4u * RS * r0.x), d0);
+        d0 = fmaf(__uint_as_float(r0.y), dva[RS * r0.x], d0);
       }
       const float d = d0 + d1;
       if (n.meta & META_INPUT) {
@@ -410,12 +464,12 @@ __global__ void k_backward(Ws w, const float *__restrict__ inputs, int64_t strid
     const float *vw = v - lane, *aww = av - lane, *dw = dv - lane;  // warp arrays
     for (int p = lane; p < V; p += 32) {
       if (nr[p].meta & (META_INPUT | META_DEAD)) continue;
-      const unsigned up = sh_addr(dw + p * RS), ap = sh_addr(aww + p * RS);
+      const WArr<GM> up(dw + p * RS), ap(aww + p * RS);
       float sb0 = 0.0f, sb1 = 0.0f, sr0 = 0.0f, sr1 = 0.0f;
 #pragma unroll 8
       for (int q = 0; q < 32; q += 2) {
-        const float u0 = lds_f32(up + 4u * q), u1 = lds_f32(up + 4u * (q + 1));
-        const float x0 = lds_f32(ap + 4u * q), x1 = lds_f32(ap + 4u * (q + 1));
+        const float u0 = up[q], u1 = up[q + 1];
+        const float x0 = ap[q], x1 = ap[q + 1];
         sb0 += u0;
         sb1 += u1;
         sr0 = fmaf(u0, x0, sr0);
@@ -426,15 +480,17 @@ __global__ void k_backward(Ws w, const float *__restrict__ inputs, int64_t strid
     }
     for (int k = lane; k < E; k += 32) {
       const int dd = edst[k];
-      if (dd < 0) continue;
-      const unsigned up = sh_addr(dw + dd * RS), vp = sh_addr(vw + er[k].src * RS);
+      // (an edge into a node no output depends on has a zero gradient: its
+      // accumulator stays 0, and the values of dead sources are never read)
+      if (dd < 0 || (nr[dd].meta & META_DEAD)) continue;
+      const WArr<GM> up(dw + dd * RS), vp(vw + er[k].src * RS);
       float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
 #pragma unroll 8
       for (int q = 0; q < 32; q += 4) {
-        s0 = fmaf(lds_f32(up + 4u * q), lds_f32(vp + 4u * q), s0);
-        s1 = fmaf(lds_f32(up + 4u * (q + 1)), lds_f32(vp + 4u * (q + 1)), s1);
-        s2 = fmaf(lds_f32(up + 4u * (q + 2)), lds_f32(vp + 4u * (q + 2)), s2);
-        s3 = fmaf(lds_f32(up + 4u * (q + 3)), lds_f32(vp + 4u * (q + 3)), s3);
+        s0 = fmaf(up[q], vp[q], s0);
+        s1 = fmaf(up[q + 1], vp[q + 1], s1);
+        s2 = fmaf(up[q + 2], vp[q + 2], s2);
+        s3 = fmaf(up[q + 3], vp[q + 3], s3);
       }
       accw[k] = fmaf(ecoef[k], (s0 + s1) + (s2 + s3), accw[k]);
     }
@@ -460,31 +516,84 @@ __global__ void k_backward(Ws w, const float *__restrict__ inputs, int64_t strid
     gb_out[size_t(g) * N + row] = sb;
     gr_out[size_t(g) * N + row] = sr;
   }
+  __syncthreads();  // the next genome overwrites the records and the accumulators
+  }
+}
+
+// out[j] = sum over genomes g in ascending order of x[g n + j], accumulated in
+// double precision and rounded once: thread per element, eight genomes' loads
+// in flight per step (coalesced across the warp: consecutive j).
+__global__ void k_sum_genomes(const float *__restrict__ x, int P, int64_t n,
+                              float *__restrict__ out) {
+  for (int64_t j = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; j < n;
+       j += int64_t(gridDim.x) * blockDim.x) {
+    double acc = 0.0;
+    int g = 0;
+    for (; g + 8 <= P; g += 8) {
+      float t[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) t[q] = __ldg(x + size_t(g + q) * size_t(n) + size_t(j));
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc += double(t[q]);
+    }
+    for (; g < P; ++g) acc += double(__ldg(x + size_t(g) * size_t(n) + size_t(j)));
+    out[j] = float(acc);
+  }
 }
 
 }  // namespace
+
+cudaError_t launch_sum_genomes(const float *x, int P, int64_t n, float *out, int sm_count,
+                               cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const int64_t blocks = std::min<int64_t>((n + 255) / 256, int64_t(std::max(1, sm_count)) * 8);
+  k_sum_genomes<<<unsigned(blocks), 256, 0, st>>>(x, P, n, out);
+  return cudaGetLastError();
+}
 
 size_t backward_smem(int N, int C, int warps) {
   return bwd_fixed_bytes(N, C) + sizeof(float) * bwd_warp_floats(N, C) * size_t(warps);
 }
 
+size_t backward_fixed_smem(int N, int C) { return bwd_fixed_bytes(N, C, false); }
+
+size_t backward_slot_floats(int N, int C) { return bwd_warp_floats(N, C); }
+
+int backward_occupancy(bool global_values, int warps, int smem_bytes) {
+  int occ = 0;
+  const cudaError_t e =
+      global_values ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_backward<true, true>,
+                                                                    warps * 32, size_t(smem_bytes))
+                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_backward<true, false>,
+                                                                    warps * 32, size_t(smem_bytes));
+  return e == cudaSuccess ? occ : 0;
+}
+
 cudaError_t launch_backward(const Ws &w, const float *inputs, int64_t stride, int S,
                             const float *grad_out, const float *saved, float *gw, float *gb,
-                            float *gr, float *gi, int warps, int smem_bytes, cudaStream_t st) {
+                            float *gr, float *gi, int warps, int smem_bytes, bool global_values,
+                            int grid_ctas, cudaStream_t st) {
   if (w.P == 0) return cudaSuccess;
-  const dim3 grid(unsigned(w.P)), block(unsigned(warps * 32));
-  if (saved != nullptr)
-    k_backward<true><<<grid, block, smem_bytes, st>>>(w, inputs, stride, S, grad_out, saved, gw,
-                                                      gb, gr, gi, smem_bytes);
-  else
-    k_backward<false><<<grid, block, smem_bytes, st>>>(w, inputs, stride, S, grad_out, nullptr,
-                                                       gw, gb, gr, gi, smem_bytes);
+  const dim3 grid(unsigned(global_values ? grid_ctas : w.P)), block(unsigned(warps * 32));
+#define NEAT_BWD(ST, GM)                                                                  \
+  k_backward<ST, GM><<<grid, block, smem_bytes, st>>>(w, inputs, stride, S, grad_out, saved, gw, \
+                                                      gb, gr, gi, smem_bytes)
+  if (saved != nullptr) {
+    if (global_values) NEAT_BWD(true, true);
+    else NEAT_BWD(true, false);
+  } else {
+    if (global_values) NEAT_BWD(false, true);
+    else NEAT_BWD(false, false);
+  }
+#undef NEAT_BWD
   return cudaGetLastError();
 }
 
 cudaError_t backward_set_smem_limit(int bytes) {
-  cudaError_t e = set_dyn_smem_limit(k_backward<true>, bytes);
-  if (e == cudaSuccess) e = set_dyn_smem_limit(k_backward<false>, bytes);
+  cudaError_t e = set_dyn_smem_limit(k_backward<true, false>, bytes);
+  if (e == cudaSuccess) e = set_dyn_smem_limit(k_backward<false, false>, bytes);
+  if (e == cudaSuccess) e = set_dyn_smem_limit(k_backward<true, true>, bytes);
+  if (e == cudaSuccess) e = set_dyn_smem_limit(k_backward<false, true>, bytes);
   return e;
 }
 

@@ -13,6 +13,9 @@
 //                   values in the warp's workspace slot, cached by L1.
 //  k_forward_plain  one CTA per (genome, tile) over the padded programs,
 //                   visiting all N padded positions (the plain form).
+//  k_forward_plain_edges  the plain form for S <= PLAIN_EDGE_S_MAX: one warp
+//                   per (genome, sample), lanes over a node's incoming edges
+//                   (a butterfly combines their partial aggregates).
 //  k_hyperneat      the batched form with inputs generated in the kernel
 //                   (substrate coordinates), several queries per lane and a
 //                   threshold epilogue.
@@ -695,6 +698,94 @@ __global__ void __launch_bounds__(32) k_forward_plain(Ws w, const float *__restr
     for (int j = 0; j < O; ++j) orow[j] = smv[io[I + j] * 32 + lane];
 }
 
+// Plain form with lanes over edges: warp (genome g = blockIdx.x, sample s =
+// blockIdx.y) walks all N padded positions; the node records of 32 positions
+// are loaded at once (lane j holds position p0 + j) and handed out by
+// shuffles; lane l folds edges l, l + 32, ... of the node, the warp combines
+// the 32 partial aggregates with a butterfly and lane 0 stores the value.
+// Lanes without an edge hold the aggregation's neutral element (0 for sums,
+// 1 for products, NaN for max: fmaxf ignores it, and a max over edges that
+// are all NaN stays NaN, as the edge-order fold gives).
+__device__ __forceinline__ float bfly_sum(float x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+__device__ __forceinline__ float bfly_prod(float x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x *= __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+__device__ __forceinline__ float bfly_max(float x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, o));
+  return x;
+}
+
+__global__ void __launch_bounds__(32) k_forward_plain_edges(Ws w, const float *__restrict__ inputs,
+                                                            int64_t stride, int S,
+                                                            float *__restrict__ out) {
+  extern __shared__ __align__(16) float smv[];  // [N] this sample's node values
+  const int lane = threadIdx.x;
+  const int N = w.N, C = w.C, I = w.I, O = w.O;
+  const int g = blockIdx.x, s = blockIdx.y;
+  const GenomeHdr h = w.hdr[g];
+  float *orow = out + (size_t(g) * S + s) * O;
+  if (h.status != 0u) {
+    for (int j = lane; j < O; j += 32) orow[j] = qnan();
+    return;
+  }
+  const int32_t *io = w.pio + size_t(g) * (I + O);
+  const float *in = inputs + size_t(g) * stride + size_t(s) * I;
+  for (int i = lane; i < I; i += 32) smv[io[i]] = __ldg(in + i);
+  __syncwarp();
+  const NodeRec *nr = w.pnode + size_t(g) * N;
+  const EdgeRec *er = w.pedge + size_t(g) * C;
+  for (int p0 = 0; p0 < N; p0 += 32) {
+    NodeRec mine{};
+    if (p0 + lane < N) mine = ld_node(nr + p0 + lane);
+    const int nq = min(32, N - p0);
+    for (int q = 0; q < nq; ++q) {
+      const uint32_t meta = __shfl_sync(0xffffffffu, mine.meta, q);
+      if (!(meta & META_VALID) || (meta & META_INPUT)) continue;  // warp-uniform
+      const float bias = __shfl_sync(0xffffffffu, mine.bias, q);
+      const float resp = __shfl_sync(0xffffffffu, mine.resp, q);
+      const int beg = __shfl_sync(0xffffffffu, mine.in_begin, q);
+      const int cnt = meta_cnt(meta), agg = meta_agg(meta);
+      float a = 0.0f;
+      if (cnt > 0) {
+        if (agg == NEAT_AGG_SUM || agg == NEAT_AGG_MEAN) {
+          float part = 0.0f;
+          for (int k = lane; k < cnt; k += 32) {
+            const EdgeRec e = ld_edge(er + beg + k);
+            part = fmaf(e.w, smv[e.src], part);
+          }
+          a = bfly_sum(part);
+          if (agg == NEAT_AGG_MEAN) a = a / float(cnt);
+        } else if (agg == NEAT_AGG_PRODUCT) {
+          float part = 1.0f;
+          for (int k = lane; k < cnt; k += 32) {
+            const EdgeRec e = ld_edge(er + beg + k);
+            part *= e.w * smv[e.src];
+          }
+          a = bfly_prod(part);
+        } else {
+          float part = qnan();
+          for (int k = lane; k < cnt; k += 32) {
+            const EdgeRec e = ld_edge(er + beg + k);
+            part = fmaxf(part, e.w * smv[e.src]);
+          }
+          a = bfly_max(part);
+        }
+      }
+      const float v = act_apply(meta_act(meta), fmaf(resp, a, bias));
+      if (lane == 0) smv[p0 + q] = v;
+      __syncwarp();
+    }
+  }
+  for (int j = lane; j < O; j += 32) orow[j] = smv[io[I + j]];
+}
+
 // ---- HyperNEAT substrate query ---------------------------------------------
 // Query q = s * G^2 + t; cell c = j * G + i sits at (-1 + 2i/(G-1),
 // -1 + 2j/(G-1)); the CPPN inputs are (x_s, y_s, x_t, y_t, 1).  G <= 128 keeps
@@ -878,6 +969,12 @@ cudaError_t launch_forward_sp(const Ws &w, const float *inputs, int64_t stride, 
 cudaError_t launch_forward_plain(const Ws &w, const float *inputs, int64_t stride, int S,
                                  float *outputs, cudaStream_t st) {
   if (w.P == 0 || S == 0) return cudaSuccess;
+  if (S <= PLAIN_EDGE_S_MAX) {
+    const dim3 grid(unsigned(w.P), unsigned(S));
+    k_forward_plain_edges<<<grid, 32, size_t(w.N) * sizeof(float), st>>>(w, inputs, stride, S,
+                                                                        outputs);
+    return cudaGetLastError();
+  }
   const size_t smem = size_t(w.N) * 32 * sizeof(float);
   const dim3 grid(unsigned(w.P), unsigned((S + 31) / 32));
   k_forward_plain<<<grid, 32, smem, st>>>(w, inputs, stride, S, outputs);

@@ -125,6 +125,9 @@ struct __align__(16) TaskRec {
 constexpr int LVL_SLOT_BITS = 12;
 constexpr int LVL_MAX_SLOTS = 1 << LVL_SLOT_BITS;  // 4096 value slots per batch
 constexpr int LVL_MAX_GENOMES = 64;                // genomes per batch (hard cap)
+// the plain form puts lanes over a node's incoming edges (one warp per
+// sample) up to this many samples per genome, over samples above it
+constexpr int PLAIN_EDGE_S_MAX = 8;
 constexpr int LVL_CONST_SLOTS = 2;                 // slots 0 and 1: the constants 0 and 1
 __host__ __device__ inline uint32_t task_meta(int cnt, int act, int agg, int slot) {
   return uint32_t(cnt) | (uint32_t(act) << 14) | (uint32_t(agg) << 17) | (uint32_t(slot) << 19);
@@ -498,13 +501,25 @@ cudaError_t launch_substrate(const float *w, int P, int K, const float *x, int64
 // tensorized operations (Sec. 3.2) in place, one warp per genome
 cudaError_t launch_apply_ops(float *nodes, float *conns, int P, int N, int C, const float *ops,
                              int K, uint32_t *op_status, cudaStream_t st);
-// Backward: `warps` per CTA, `smem_bytes` of dynamic shared memory (at least
-// backward_smem(N, C, 1)); a genome runs on as many warps as blocks of its
-// size fit in smem_bytes.
+// out [n] = sum over the P genomes of x [P, n] (ascending genome order,
+// double-precision accumulation, one rounding)
+cudaError_t launch_sum_genomes(const float *x, int P, int64_t n, float *out, int sm_count,
+                               cudaStream_t st);
+// Backward: `warps` per CTA.  global_values = false: one CTA per genome with
+// smem_bytes of dynamic shared memory (at least backward_smem(N, C, 1)); a
+// genome runs on as many warps as blocks of its size fit in smem_bytes.
+// global_values = true: grid_ctas CTAs with backward_fixed_smem(N, C) bytes of
+// shared memory (the records and pull lists) walk the queue, each warp's
+// arrays in a workspace slot of backward_slot_floats(N, C) floats (grid_ctas *
+// warps slots must fit in sp_scratch).
 cudaError_t launch_backward(const Ws &w, const float *inputs, int64_t stride, int S,
                             const float *grad_out, const float *saved, float *gw, float *gb,
-                            float *gr, float *gi, int warps, int smem_bytes, cudaStream_t st);
+                            float *gr, float *gi, int warps, int smem_bytes, bool global_values,
+                            int grid_ctas, cudaStream_t st);
 size_t backward_smem(int N, int C, int warps);
+size_t backward_fixed_smem(int N, int C);
+size_t backward_slot_floats(int N, int C);
+int backward_occupancy(bool global_values, int warps, int smem_bytes);
 // HyperNEAT query: spl queries per lane (1, 2 or 4), `ctas` CTAs of `warps`
 // warps with smem_bytes of dynamic shared memory (>= hn_prog_bytes(N, C): a
 // compiled program's records and pairs).  A genome whose value array does not

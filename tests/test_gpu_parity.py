@@ -220,9 +220,9 @@ def test_pruning_changes_no_result(name, P, S):
         plan.set_tuning(prune_dead=prune, small_s_max=-1)
         out_sp = plan.forward(dx)
         go = torch.ones((P, S, spec.O), device="cuda")
-        # (the backward keeps a genome's records in shared memory: up to
-        # N = 1024, C = 4096 it does not fit, and says so)
-        grads = plan.backward(dx, go) if name != "uneven" else ()
+        # (uneven genomes, N = 1024 and C = 4096, take the backward whose
+        # per-warp arrays sit in workspace slots)
+        grads = plan.backward(dx, go)
         res.append((out, out_sp, grads))
     bits = lambda t: t.view(torch.int32)  # noqa: E731
     assert torch.equal(bits(res[0][0]), bits(res[1][0]))
@@ -317,6 +317,61 @@ def test_backward_parity(name, P, S, stored):
     compare_grads(gi.cpu().numpy(), ri, "grad_inputs")
 
 
+@pytest.mark.parametrize("stored", [True, False])
+@pytest.mark.parametrize("name,P,S", [("differentiation", 96, 77), ("locomotion", 48, 40)])
+def test_backward_parity_workspace_slots(name, P, S, stored):
+    """bwd_global = 1: the per-warp arrays in workspace slots (the path of
+    genomes too large for shared memory) on genomes that also fit in shared
+    memory: the same gradients against the oracle, and with the records and
+    sort keys reused across the genomes a CTA walks."""
+    nodes, conns, spec, x = _fwd_case(name, P, S, seed=5)
+    plan = _plan(spec, P)
+    plan.set_tuning(bwd_global=1)
+    plan.transform(_dev(nodes), _dev(conns))
+    xd = _dev(x)
+    saved = None
+    if stored:
+        saved = torch.empty((P, spec.N, S), device="cuda")
+        plan.forward(xd, saved=saved)
+    go = np.random.default_rng(9).standard_normal((P, S, spec.O)).astype(np.float32)
+    gw, gb, gr, gi = plan.backward(xd, _dev(go), saved=saved)
+    plan.check()
+    rw, rb, rr, ri = oracle.backward(nodes, conns, x, spec.I, spec.O, go)
+    compare_grads(gw.cpu().numpy(), rw, "grad_weight")
+    compare_grads(gb.cpu().numpy(), rb, "grad_bias")
+    compare_grads(gr.cpu().numpy(), rr, "grad_response")
+    compare_grads(gi.cpu().numpy(), ri, "grad_inputs")
+
+
+@pytest.mark.parametrize("stored", [True, False])
+def test_backward_parity_uneven_largest_genomes(stored):
+    """Uneven-shaped genomes (N = 1024, C = 4096: too large for the backward's
+    shared-memory arrays) through the workspace-slot backward, against the
+    oracle; the largest genomes of the population included."""
+    P, S = 40, 70
+    nodes, conns, spec = population_for("uneven", seed=14, P=P)
+    assert (spec.N, spec.C) == (1024, 4096)
+    en = (~np.isnan(conns[:, :, 0]) & ~np.isnan(conns[:, :, 1]) & ~np.isnan(conns[:, :, 3]) &
+          (conns[:, :, 3] != 0)).sum(1)
+    assert en.max() >= 2000  # some genomes near the size limit
+    x = np.random.default_rng(14).standard_normal((P, S, spec.I)).astype(np.float32)
+    go = np.random.default_rng(15).standard_normal((P, S, spec.O)).astype(np.float32)
+    plan = _plan(spec, P)
+    plan.transform(_dev(nodes), _dev(conns))
+    xd = _dev(x)
+    saved = None
+    if stored:
+        saved = torch.empty((P, spec.N, S), device="cuda")
+        plan.forward(xd, saved=saved)
+    gw, gb, gr, gi = plan.backward(xd, _dev(go), saved=saved)
+    plan.check()
+    rw, rb, rr, ri = oracle.backward(nodes, conns, x, spec.I, spec.O, go)
+    compare_grads(gw.cpu().numpy(), rw, "grad_weight")
+    compare_grads(gb.cpu().numpy(), rb, "grad_bias")
+    compare_grads(gr.cpu().numpy(), rr, "grad_response")
+    compare_grads(gi.cpu().numpy(), ri, "grad_inputs")
+
+
 @pytest.mark.parametrize("S", [77, 300])
 def test_backward_parity_every_aggregation(S):
     """Product and max nodes (per-sample factors, summed with warp reductions
@@ -401,6 +456,32 @@ def test_autograd_function_matches_oracle():
         compare_grads(gn[..., 2].cpu().numpy(), rr, "r")
         compare_grads(gx.cpu().numpy(), ri.sum(0, keepdims=True), "x")
         assert torch.count_nonzero(gn[..., 0]) == 0 and torch.count_nonzero(gc[..., 3]) == 0
+
+
+def test_autograd_switches_to_recompute_above_the_budget():
+    """evaluate() without `store`: the aggregates are kept while 4 P N S bytes
+    fit the budget and recomputed in the backward above it; the gradients
+    match the oracle either way."""
+    from paper_2504_08339_b300.api import evaluate, saved_bytes
+    P, S = 24, 96
+    nodes, conns, spec, x = _fwd_case("differentiation", P, S, seed=9)
+    plan = _plan(spec, P)
+    y = _dev(regression_batch(9, S)[1])
+    need = saved_bytes(plan, S)
+    assert need == 4 * P * spec.N * S
+    ref = oracle.forward(nodes, conns, x, spec.I, spec.O)
+    gout = (2.0 / S) * (ref[..., 0] - y.cpu().numpy()[None].astype(np.float64))
+    rw, rb, rr, _ = oracle.backward(nodes, conns, x, spec.I, spec.O, gout[..., None])
+    for budget, kept in ((need, True), (need - 1, False), (None, True)):
+        n = _dev(nodes).requires_grad_(True)
+        c = _dev(conns).requires_grad_(True)
+        out = evaluate(plan, n, c, _dev(x), budget=budget)
+        assert (out.grad_fn.saved_agg is not None) == kept, budget
+        loss = ((out[..., 0] - y) ** 2).mean(dim=1).sum()
+        gn, gc = torch.autograd.grad(loss, (n, c))
+        compare_grads(gc[..., 2].cpu().numpy(), rw, "w")
+        compare_grads(gn[..., 1].cpu().numpy(), rb, "b")
+        compare_grads(gn[..., 2].cpu().numpy(), rr, "r")
 
 
 def test_hyperneat_full_grid_small():
