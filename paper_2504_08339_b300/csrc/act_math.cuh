@@ -4,13 +4,17 @@
 // library's general-purpose expf / tanhf / sinf carry slow paths and
 // branches that a warp evaluating nodes of mixed activations pays for in
 // full.  Methods (all in fp32):
-//   exp   Cody and Waite's argument reduction x = k ln2 + r, |r| <= ln2 / 2
-//         (ln2 split in a 15-bit high part, so k ln2_hi is exact, and a low
-//         part), e^r by its Taylor polynomial of degree 7 (truncation below
-//         1e-8 relative), scaled by 2^k exactly.  Results below 2^-125 flush
-//         to 0; NaN propagates.
-//   1/d   (d >= 1) the hardware reciprocal approximation refined by one
-//         Newton-Raphson step, y = y0 + y0 (1 - d y0); 1/inf = 0.
+//   exp   the argument clamped to [-87, 88] (NaN passes through), then Cody
+//         and Waite's reduction x = k ln2 + r, |r| <= ln2 / 2 (ln2 split in a
+//         15-bit high part, so k ln2_hi is exact, and a low part), e^r by its
+//         Taylor polynomial of degree 7 (truncation below 1e-8 relative),
+//         scaled by 2^k, k in [-126, 127], exactly.  The clamp keeps every
+//         result finite and normal: below e^-87 the result is e^-87 (1.6e-38)
+//         and above e^88 it is e^88, which moves sigmoid, tanh and gaussian
+//         by less than 2e-38 where it applies.
+//   1/d   (1 <= d < 2^128) the hardware reciprocal approximation refined by
+//         one Newton-Raphson step, y = y0 + y0 (1 - d y0); a result below
+//         2^-126 flushes to 0.
 //   tanh  |z| >= 0.55: 1 - 2 / (e^{2|z|} + 1) (no cancellation: tanh >= 0.5);
 //         |z| < 0.55: the odd Taylor series z + sum_{n=2..10} c_n z^{2n-1},
 //         c_n = 2^{2n} (2^{2n} - 1) B_{2n} / (2n)! (Bernoulli numbers; the
@@ -45,7 +49,9 @@ constexpr float SIN_ARG_MAX = 6.5e6f;
 
 // e^x (see the header comment)
 __device__ __forceinline__ float exp_cw(float x) {
-  const float xc = fminf(fmaxf(x, -87.0f), 89.0f);
+  float xc;
+  asm("max.NaN.f32 %0, %1, %2;" : "=f"(xc) : "f"(x), "f"(-87.0f));
+  asm("min.NaN.f32 %0, %1, %2;" : "=f"(xc) : "f"(xc), "f"(88.0f));
   const float t = fmaf(xc, LOG2E, MAGIC);
   const float k = t - MAGIC;
   const int ki = __float_as_int(t) - MAGIC_BITS;
@@ -59,18 +65,15 @@ __device__ __forceinline__ float exp_cw(float x) {
   p = fmaf(p, r, 0.5f);
   p = fmaf(p, r, 1.0f);
   p = fmaf(p, r, 1.0f);
-  // 2^k as (p 2^(k-1)) 2: k - 1 in [-126, 128] keeps 2^(k-1) a normal number
-  // (k = 129 gives the infinity bits, for arguments that overflow anyway)
-  const float e = (p * __int_as_float((ki + 126) << 23)) * 2.0f;
-  return x != x ? x : (x < -87.0f ? 0.0f : e);
+  // (a NaN argument leaves p NaN, whatever the scale's bits)
+  return p * __int_as_float((ki + 127) << 23);
 }
 
-// 1 / d for d >= 1, +inf or NaN
+// 1 / d for finite d >= 1, or NaN
 __device__ __forceinline__ float rcp_nr(float d) {
   float y0;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(d));
-  const float y = fmaf(fmaf(-d, y0, 1.0f), y0, y0);
-  return d == __int_as_float(0x7f800000) ? 0.0f : y;
+  return fmaf(fmaf(-d, y0, 1.0f), y0, y0);
 }
 
 // tanh z for |z| < 0.55: z + z^3 P(z^2)

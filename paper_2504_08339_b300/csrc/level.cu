@@ -196,8 +196,12 @@ __global__ void __launch_bounds__(BLD_THREADS) k_lvl_build(Ws w) {
   // sort keys over the genome slots (slot i + LVL_CONST_SLOTS)
   const int ngs = nslots - LVL_CONST_SLOTS;
   const int n2 = pow2_ceil_d(max(ngs, 1));
-  // task keys: (layer, act, -cnt, genome, position); inputs and the nodes no
-  // output depends on sort last (they are not tasks)
+  // task keys: (layer, activation class, act, -cnt, genome, position), the
+  // classes ordered exp-family (sigmoid, tanh, gaussian), cheap (identity,
+  // relu, abs), sine: a round's first 32 tasks then rarely hold a sine and
+  // the next 32 rarely an exp-family node, and the forward evaluates only
+  // the functions a 32-task pass holds.  Inputs and the nodes no output
+  // depends on sort last (they are not tasks).
   for (int i = tid; i < n2; i += T) {
     uint64_t key = ~0ull;
     if (i < ngs) {
@@ -207,7 +211,9 @@ __global__ void __launch_bounds__(BLD_THREADS) k_lvl_build(Ws w) {
       const NodeRec n = w.knode[g_noff[k] + p];
       if (!(n.meta & (META_INPUT | META_DEAD))) {
         const uint64_t lay = uint64_t(w.player[size_t(g_id[k]) * w.N + p]);
-        key = (lay << 33) | (uint64_t(meta_act(n.meta)) << 30) |
+        const int a = meta_act(n.meta);
+        const uint64_t cls = ((ACT_BIT_EXP >> a) & 1u) ? 0u : (a == NEAT_ACT_SIN ? 2u : 1u);
+        key = (lay << 35) | (cls << 33) | (uint64_t(a) << 30) |
               (uint64_t(16383 - meta_cnt(n.meta)) << 16) | (uint64_t(k) << 10) | uint64_t(p);
       }
     }
@@ -269,7 +275,7 @@ __global__ void __launch_bounds__(BLD_THREADS) k_lvl_build(Ws w) {
   // rounds: one layer each, split where a layer exceeds pcap chunks (a single
   // task never does: pcap >= the chunks of a node's in-degree)
   auto new_round = [&](int j, int cur, int in, int nc) {
-    return j == 0 || int(keys[j] >> 33) != cur || in + nc > pcap;
+    return j == 0 || int(keys[j] >> 35) != cur || in + nc > pcap;
   };
   if (tid == 0) {
     int R = 0, in = 0, cur = -1;
@@ -278,7 +284,7 @@ __global__ void __launch_bounds__(BLD_THREADS) k_lvl_build(Ws w) {
       if (new_round(j, cur, in, nc)) {
         ++R;
         in = 0;
-        cur = int(keys[j] >> 33);
+        cur = int(keys[j] >> 35);
       }
       in += nc;
     }
@@ -321,7 +327,7 @@ __global__ void __launch_bounds__(BLD_THREADS) k_lvl_build(Ws w) {
       if (new_round(j, cur, in, nc)) {
         rt[R++] = uint32_t(j) | (uint32_t(cnt[j]) << 16);
         in = 0;
-        cur = int(keys[j] >> 33);
+        cur = int(keys[j] >> 35);
       }
       in += nc;
     }
@@ -428,8 +434,9 @@ __device__ __forceinline__ void sts_f32_a(uint32_t a, float x) {
 }
 
 // Activation of one value per lane, the lanes holding nodes of mixed
-// activations.  `mask` (bit a: some task of the batch has activation a; the
-// same on every lane) names the evaluations needed: one exponential per lane
+// activations.  `mask` (bit a: some task of the pass, or of a superset such
+// as the whole batch, has activation a; the same on every lane) names the
+// evaluations needed: one exponential per lane
 // serves sigmoid, tanh and gaussian (act_exp_arg), one reciprocal sigmoid and
 // tanh, one sine the sin nodes; each is evaluated on every lane and the
 // lane's result selected, so no branch diverges (but for sine arguments
@@ -451,35 +458,6 @@ __device__ __forceinline__ float act_lanes(int a, float z, uint32_t mask) {
     y = sel_eq<NEAT_ACT_SIN>(a, sn, y);
   }
   return y;
-}
-
-// the same for two values per lane, evaluated side by side
-__device__ __forceinline__ void act_lanes2(int a0, float z0, int a1, float z1, uint32_t mask,
-                                           float &y0, float &y1) {
-  y0 = sel_eq<NEAT_ACT_RELU>(a0, fmaxf(z0, 0.0f), z0);
-  y0 = sel_eq<NEAT_ACT_ABS>(a0, fabsf(z0), y0);
-  y1 = sel_eq<NEAT_ACT_RELU>(a1, fmaxf(z1, 0.0f), z1);
-  y1 = sel_eq<NEAT_ACT_ABS>(a1, fabsf(z1), y1);
-  if (mask & ACT_BIT_EXP) {
-    const float e0 = am::exp_cw(act_exp_arg(a0, z0)), e1 = am::exp_cw(act_exp_arg(a1, z1));
-    const float q0 = am::rcp_nr(1.0f + e0), q1 = am::rcp_nr(1.0f + e1);
-    y0 = sel_eq<NEAT_ACT_SIGMOID>(a0, q0, y0);
-    y0 = sel_eq<NEAT_ACT_GAUSSIAN>(a0, e0, y0);
-    y1 = sel_eq<NEAT_ACT_SIGMOID>(a1, q1, y1);
-    y1 = sel_eq<NEAT_ACT_GAUSSIAN>(a1, e1, y1);
-    if (mask & (1u << NEAT_ACT_TANH)) {
-      y0 = sel_eq<NEAT_ACT_TANH>(a0, tanh_of(z0, q0), y0);
-      y1 = sel_eq<NEAT_ACT_TANH>(a1, tanh_of(z1, q1), y1);
-    }
-  }
-  if (mask & ACT_BIT_SIN) {
-    const float zs0 = sel_eq<NEAT_ACT_SIN>(a0, z0, 0.0f), zs1 = sel_eq<NEAT_ACT_SIN>(a1, z1, 0.0f);
-    float s0 = am::sin_cw(zs0), s1 = am::sin_cw(zs1);
-    if (fabsf(zs0) > am::SIN_ARG_MAX) s0 = sinf(zs0);  // rare
-    if (fabsf(zs1) > am::SIN_ARG_MAX) s1 = sinf(zs1);
-    y0 = sel_eq<NEAT_ACT_SIN>(a0, s0, y0);
-    y1 = sel_eq<NEAT_ACT_SIN>(a1, s1, y1);
-  }
 }
 
 // A batch program's arrays: the round table, task records and edge chunks in
@@ -615,8 +593,7 @@ __device__ __forceinline__ void load_round(const BatchArrays &ba, uint32_t ra, u
 // (bounds x.rb, rc) into `nx` when there is one (r + 1 < nr); `rq` holds the
 // round-table entries of rounds r + 2 and r + 3 (shifted as rounds go)
 __device__ __forceinline__ void one_round(const BatchArrays &ba, int r, int nr, int lane,
-                                          uint32_t mask, const RoundRecs &x, RoundRecs &nx,
-                                          uint32_t (&rq)[2]) {
+                                          const RoundRecs &x, RoundRecs &nx, uint32_t (&rq)[2]) {
   const int t0 = int(x.ra & 0xffffu), t1 = int(x.rb & 0xffffu);
   const int c0 = int(x.ra >> 16), c1 = int(x.rb >> 16);
   const int na = c1 - c0, nt = t1 - t0;
@@ -637,27 +614,30 @@ __device__ __forceinline__ void one_round(const BatchArrays &ba, int r, int nr, 
     if (lane < na) sts_f32_a(part_l, pa);
   }
   __syncwarp();
-  // node pass
+  // node pass: a 32-task pass evaluates only the activation functions its
+  // own tasks hold (a warp OR of their activation bits; lanes past the round
+  // repeat its last task)
+  const int aa = task_act(x.ta.meta);
+  const float za = fmaf(x.ta.resp, task_aggregate<1>(x.ta, ba.part, c0, 0), x.ta.bias);
+  const uint32_t ma = __reduce_or_sync(0xffffffffu, 1u << aa);
   if (nt > 32) {
-    float ya, yb;
-    act_lanes2(task_act(x.ta.meta),
-               fmaf(x.ta.resp, task_aggregate<1>(x.ta, ba.part, c0, 0), x.ta.bias),
-               task_act(x.tb.meta),
-               fmaf(x.tb.resp, task_aggregate<1>(x.tb, ba.part, c0, 0), x.tb.bias), mask, ya, yb);
+    const int ab = task_act(x.tb.meta);
+    const float zb = fmaf(x.tb.resp, task_aggregate<1>(x.tb, ba.part, c0, 0), x.tb.bias);
+    const uint32_t mb = __reduce_or_sync(0xffffffffu, 1u << ab);
+    const float ya = act_lanes(aa, za, ma);
+    const float yb = act_lanes(ab, zb, mb);
     if (lane + 32 < nt) sts_f32_a(ba.v + 4u * uint32_t(task_slot(x.tb.meta)), yb);
     sts_f32_a(ba.v + 4u * uint32_t(task_slot(x.ta.meta)), ya);
     // (warp-uniform trip count: act_lanes is called by all 32 lanes)
     for (int base = 64; base < nt; base += 32) {
       const TaskRec tk = ld_task(ba, t0 + min(base + lane, nt - 1));
-      const float y = act_lanes(task_act(tk.meta),
-                                fmaf(tk.resp, task_aggregate<1>(tk, ba.part, c0, 0), tk.bias),
-                                mask);
+      const int a = task_act(tk.meta);
+      const float y = act_lanes(a, fmaf(tk.resp, task_aggregate<1>(tk, ba.part, c0, 0), tk.bias),
+                                __reduce_or_sync(0xffffffffu, 1u << a));
       if (base + lane < nt) sts_f32_a(ba.v + 4u * uint32_t(task_slot(tk.meta)), y);
     }
   } else {
-    const float ya = act_lanes(task_act(x.ta.meta),
-                               fmaf(x.ta.resp, task_aggregate<1>(x.ta, ba.part, c0, 0), x.ta.bias),
-                               mask);
+    const float ya = act_lanes(aa, za, ma);
     if (lane < nt) sts_f32_a(ba.v + 4u * uint32_t(task_slot(x.ta.meta)), ya);
   }
   __syncwarp();
@@ -665,8 +645,7 @@ __device__ __forceinline__ void one_round(const BatchArrays &ba, int r, int nr, 
 
 // all rounds of a batch for one sample; the next batch is claimed when
 // round claim_at starts
-__device__ __forceinline__ void run_rounds_st1(const BatchArrays &ba, int nr, int lane,
-                                               uint32_t mask, int claim_at,
+__device__ __forceinline__ void run_rounds_st1(const BatchArrays &ba, int nr, int lane, int claim_at,
                                                unsigned long long *claim, unsigned long long &old,
                                                bool &claimed) {
   if (nr <= 0) return;
@@ -678,8 +657,8 @@ __device__ __forceinline__ void run_rounds_st1(const BatchArrays &ba, int nr, in
       if (lane == 0) old = atomicAdd(claim, 1ull);
       claimed = true;
     }
-    one_round(ba, r, nr, lane, mask, x0, x1, rq);
-    if (r + 1 < nr) one_round(ba, r + 1, nr, lane, mask, x1, x0, rq);
+    one_round(ba, r, nr, lane, x0, x1, rq);
+    if (r + 1 < nr) one_round(ba, r + 1, nr, lane, x1, x0, rq);
   }
 }
 
@@ -696,10 +675,10 @@ __device__ void nan_batch_outputs(const Ws &w, int b, int S, float *__restrict__
 
 constexpr int LVL_MAX_WARPS = 8;
 
-// (launch bound: one CTA of 8 warps per SM suffices for the registers, so the
-// compiler may use up to 255 a thread; a 64-register cap spilled the rounds)
+// (launch bound: two CTAs of 8 warps per SM, at most 128 registers a thread;
+// a 64-register cap spilled the rounds, and above 128 only 12 warps fit)
 template <int ST>
-__global__ void __launch_bounds__(32 * LVL_MAX_WARPS, 1) k_forward_lvl(
+__global__ void __launch_bounds__(32 * LVL_MAX_WARPS, 2) k_forward_lvl(
     Ws w, const float *__restrict__ inputs, int64_t stride, int S, float *__restrict__ out,
     int warp_bytes, int vals_bytes, int polls) {
   extern __shared__ __align__(128) unsigned char sm[];
@@ -728,6 +707,14 @@ __global__ void __launch_bounds__(32 * LVL_MAX_WARPS, 1) k_forward_lvl(
       asm volatile("prefetch.L2 [%0];" ::"l"(inputs + l * 32));
   }
   const int nwarps = gridDim.x * nw;
+  // lane walks of the (genome k, input i / output j, sample s) items, item
+  // it = (k * I + i) * ST + s for it = lane, lane + 32, ...: ST divides 32,
+  // so s = lane % ST throughout and (k, i) advance by 32 / ST items a step
+  // (one division per launch instead of one per item)
+  constexpr int STEP = 32 / ST;
+  const int s_l = lane % ST, r_l = lane / ST;
+  const int ki0 = r_l / I, ii0 = r_l % I, dki = STEP / I, dii = STEP % I;
+  const int ko0 = r_l / O, jo0 = r_l % O, dko = STEP / O, djo = STEP % O;
   uint32_t parity = 0;
   // Batches: warp w starts with batch w; each warp claims its next batch
   // (a few rounds before the current one ends, so the atomic's latency hides
@@ -775,18 +762,19 @@ __global__ void __launch_bounds__(32 * LVL_MAX_WARPS, 1) k_forward_lvl(
       const int *gio = reinterpret_cast<const int *>(head + hg.off_gio);
       if (lane < 2 * ST) v[lane] = lane < ST ? 0.0f : 1.0f;  // the constant slots 0 and 1
       for (int s0 = 0; s0 < S; s0 += ST) {
-        for (int it = lane; it < hg.n_genomes * I * ST; it += 32) {
-          const int s = it % ST, r = it / ST, k = r / I, i = r - k * I;
+        for (int it = lane, k = ki0, i = ii0; it < hg.n_genomes * I * ST; it += 32) {
           const int slot = gio[k * G + 1 + i];
-          if (slot < 0) continue;
-          const int gs = s0 + s;
-          v[slot * ST + s] =
-              gs < S ? __ldg(inputs + size_t(gio[k * G]) * stride + size_t(gs) * I + i) : 0.0f;
+          const int gs = s0 + s_l;
+          if (slot >= 0)
+            v[slot * ST + s_l] =
+                gs < S ? __ldg(inputs + size_t(gio[k * G]) * stride + size_t(gs) * I + i) : 0.0f;
+          k += dki;
+          i += dii;
+          if (i >= I) { i -= I; ++k; }
         }
         __syncwarp();
         if constexpr (ST == 1) {
-          run_rounds_st1(ba, hg.n_rounds, lane, hg.act_mask, max(hg.n_rounds - 3, 0), claim, old,
-                         claimed);
+          run_rounds_st1(ba, hg.n_rounds, lane, max(hg.n_rounds - 3, 0), claim, old, claimed);
         } else {
           for (int r = 0; r < hg.n_rounds; ++r) {
             const uint32_t r0 = __ldg(ba.rt + r), r1 = __ldg(ba.rt + r + 1);
@@ -794,12 +782,15 @@ __global__ void __launch_bounds__(32 * LVL_MAX_WARPS, 1) k_forward_lvl(
                            int(r1 >> 16), lane, hg.act_mask);
           }
         }
-        for (int it = lane; it < hg.n_genomes * O * ST; it += 32) {
-          const int s = it % ST, r = it / ST, k = r / O, j = r - k * O;
-          const int gs = s0 + s;
-          if (gs >= S) continue;
-          const int slot = gio[k * G + 1 + I + j];
-          out[(size_t(gio[k * G]) * S + gs) * O + j] = slot < 0 ? qnan() : v[slot * ST + s];
+        for (int it = lane, k = ko0, j = jo0; it < hg.n_genomes * O * ST; it += 32) {
+          const int gs = s0 + s_l;
+          if (gs < S) {
+            const int slot = gio[k * G + 1 + I + j];
+            out[(size_t(gio[k * G]) * S + gs) * O + j] = slot < 0 ? qnan() : v[slot * ST + s_l];
+          }
+          k += dko;
+          j += djo;
+          if (j >= O) { j -= O; ++k; }
         }
         __syncwarp();
       }
