@@ -52,9 +52,16 @@ __device__ __forceinline__ int pow2_ceil_d(int x) {
 // genome byte bounds in queue order.
 constexpr int PLAN_THREADS = 1024;
 
+// Populations of at most PLAN_STAGED genomes first stage every genome's
+// (byte bound, slots) pair in shared memory, all loads independent, so that
+// the runs' sequential cuts read shared memory instead of waiting on two
+// dependent global loads a genome.
+constexpr int PLAN_STAGED = 20480;
+
 __global__ void __launch_bounds__(PLAN_THREADS) k_lvl_plan(Ws w) {
   __shared__ long long sb[32];
   __shared__ int sn[32];
+  extern __shared__ int2 sgen[];  // [P] (byte bound, slots) when staged
   const int P = w.P, T = blockDim.x, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int I = w.I, O = w.O, cap = w.lvl_budget, scap = w.lvl_slots - LVL_CONST_SLOTS;
   const int per = max(128, (P + T - 1) / T);
@@ -63,11 +70,21 @@ __global__ void __launch_bounds__(PLAN_THREADS) k_lvl_plan(Ws w) {
   const int gmax = min(LVL_MAX_GENOMES,
                        (lvl_head_cap(I, O) - int(sizeof(BatchHead)) - 15) / (4 * (1 + I + O)));
   const int q0 = min(tid * per, P), q1 = min(q0 + per, P);
-  auto genome = [&](int q, int &pb, int &V) {
+  auto load = [&](int q) {
     const GenomeHdr h = w.hdr[w.qlvl[q]];
     const bool ok = h.status == 0u;
-    pb = lvl_genome_bytes(h.nlive, h.nch, h.L, I, O, ok);  // tasks: the evaluated nodes
-    V = ok ? h.V : 0;
+    // tasks: the evaluated nodes
+    return make_int2(lvl_genome_bytes(h.nlive, h.nch, h.L, I, O, ok), ok ? h.V : 0);
+  };
+  const bool staged = P <= PLAN_STAGED;
+  if (staged) {
+    for (int q = tid; q < P; q += T) sgen[q] = load(q);
+    __syncthreads();
+  }
+  auto genome = [&](int q, int &pb, int &V) {
+    const int2 x = staged ? sgen[q] : load(q);
+    pb = x.x;
+    V = x.y;
   };
   // pass 1: batches and bytes of this thread's run
   int nb = 0;
@@ -153,10 +170,14 @@ __global__ void __launch_bounds__(BLD_THREADS) k_lvl_build(Ws w) {
   __shared__ int g_slot[LVL_MAX_GENOMES + 1], g_NL[LVL_MAX_GENOMES + 1];
   __shared__ int s_nslots, s_ntasks, s_nrounds, s_bad;
   __shared__ unsigned s_acts;
+  __shared__ uint32_t rsb[LVL_MAX_SLOTS / 32];  // round-start bits of the tasks
+  __shared__ int wpre[LVL_MAX_SLOTS / 32];      // round starts before each word
   __shared__ int wbuf[33];
   extern __shared__ __align__(16) unsigned char dsm[];
-  uint64_t *keys = reinterpret_cast<uint64_t *>(dsm);               // [LVL_MAX_SLOTS]
-  int *cnt = reinterpret_cast<int *>(dsm + 8 * LVL_MAX_SLOTS);      // [LVL_MAX_SLOTS + 1]
+  // sort keys [pow2(lvl_slots)], chunk offsets [lvl_slots + 1]: a batch holds
+  // at most lvl_slots value slots, and so fewer tasks
+  uint64_t *keys = reinterpret_cast<uint64_t *>(dsm);
+  int *cnt = reinterpret_cast<int *>(dsm + 8 * size_t(pow2_ceil_d(w.lvl_slots)));
 
   const int b = blockIdx.x, tid = threadIdx.x, T = blockDim.x;
   const int nb = int(w.counters[CTR_NBATCH]);
@@ -273,22 +294,50 @@ __global__ void __launch_bounds__(BLD_THREADS) k_lvl_build(Ws w) {
   }
   const int nchunks = cnt[ntasks];
   // rounds: one layer each, split where a layer exceeds pcap chunks (a single
-  // task never does: pcap >= the chunks of a node's in-degree)
-  auto new_round = [&](int j, int cur, int in, int nc) {
-    return j == 0 || int(keys[j] >> 35) != cur || in + nc > pcap;
-  };
-  if (tid == 0) {
-    int R = 0, in = 0, cur = -1;
-    for (int j = 0; j < ntasks; ++j) {
-      const int nc = cnt[j + 1] - cnt[j];
-      if (new_round(j, cur, in, nc)) {
-        ++R;
+  // task never does: pcap >= the chunks of a node's in-degree).  Round starts
+  // are bits of rsb: every layer start, and the splits that the thread owning
+  // a layer's start finds by walking that layer (layers in parallel); a
+  // round's index is the number of starts before it (word prefix + popc).
+  for (int i = tid; i < LVL_MAX_SLOTS / 32; i += T) rsb[i] = 0u;
+  __syncthreads();
+  auto lay_of = [&](int j) { return int(keys[j] >> 35); };
+  for (int j = tid; j < ntasks; j += T) {
+    if (j > 0 && lay_of(j) == lay_of(j - 1)) continue;
+    atomicOr(&rsb[j >> 5], 1u << (j & 31));
+    const int l = lay_of(j);
+    int in = cnt[j + 1] - cnt[j];
+    for (int k = j + 1; k < ntasks && lay_of(k) == l; ++k) {
+      const int nc = cnt[k + 1] - cnt[k];
+      if (in + nc > pcap) {
+        atomicOr(&rsb[k >> 5], 1u << (k & 31));
         in = 0;
-        cur = int(keys[j] >> 35);
       }
       in += nc;
     }
-    s_nrounds = R;
+  }
+  __syncthreads();
+  const int nwords = (ntasks + 31) >> 5;
+  if (tid < 32) {  // exclusive prefix of the words' start counts (4 words a lane)
+    int c[4], tot = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int wi = 4 * tid + q;
+      c[q] = wi < nwords ? __popc(rsb[wi]) : 0;
+      tot += c[q];
+    }
+    int x = tot;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, d);
+      if (tid >= d) x += y;
+    }
+    int base = x - tot;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      wpre[4 * tid + q] = base;
+      base += c[q];
+    }
+    if (tid == 31) s_nrounds = x;
   }
   __syncthreads();
   const int nrounds = s_nrounds;
@@ -320,18 +369,13 @@ __global__ void __launch_bounds__(BLD_THREADS) k_lvl_build(Ws w) {
     loc.head = off_round;
     loc.pad = 0;
     w.lvl_loc[b] = loc;
-    // round table (same walk as above)
-    int R = 0, in = 0, cur = -1;
-    for (int j = 0; j < ntasks; ++j) {
-      const int nc = cnt[j + 1] - cnt[j];
-      if (new_round(j, cur, in, nc)) {
-        rt[R++] = uint32_t(j) | (uint32_t(cnt[j]) << 16);
-        in = 0;
-        cur = int(keys[j] >> 35);
-      }
-      in += nc;
-    }
-    rt[R] = uint32_t(ntasks) | (uint32_t(nchunks) << 16);
+    rt[nrounds] = uint32_t(ntasks) | (uint32_t(nchunks) << 16);
+  }
+  // round table: the first task and chunk of every round
+  for (int j = tid; j < ntasks; j += T) {
+    const uint32_t word = rsb[j >> 5], bit = 1u << (j & 31);
+    if (word & bit)
+      rt[wpre[j >> 5] + __popc(word & (bit - 1u))] = uint32_t(j) | (uint32_t(cnt[j]) << 16);
   }
   // task records and their padded edge chunks
   for (int j = tid; j < ntasks; j += T) {
@@ -825,8 +869,11 @@ size_t lvl_warp_bytes(const Ws &w, int st_samples) {
 
 cudaError_t launch_lvl_build(const Ws &w, cudaStream_t st) {
   if (w.P == 0) return cudaSuccess;
-  k_lvl_plan<<<1, PLAN_THREADS, 0, st>>>(w);
-  const size_t smem = 8 * size_t(LVL_MAX_SLOTS) + 4 * size_t(LVL_MAX_SLOTS + 1);
+  const size_t plan_smem = w.P <= PLAN_STAGED ? sizeof(int2) * size_t(w.P) : 0;
+  k_lvl_plan<<<1, PLAN_THREADS, plan_smem, st>>>(w);
+  int slots2 = 1;
+  while (slots2 < w.lvl_slots) slots2 <<= 1;
+  const size_t smem = 8 * size_t(slots2) + 4 * size_t(w.lvl_slots + 1);
   k_lvl_build<<<w.lvl_max_batches, BLD_THREADS, smem, st>>>(w);
   return cudaGetLastError();
 }
@@ -852,6 +899,7 @@ cudaError_t lvl_set_smem_limit(int bytes) {
   if (e == cudaSuccess) e = set_dyn_smem_limit(k_forward_lvl<2>, bytes);
   if (e == cudaSuccess) e = set_dyn_smem_limit(k_forward_lvl<4>, bytes);
   if (e == cudaSuccess) e = set_dyn_smem_limit(k_lvl_build, bytes);
+  if (e == cudaSuccess) e = set_dyn_smem_limit(k_lvl_plan, bytes);
   return e;
 }
 
