@@ -51,14 +51,14 @@ PEAKS_FALLBACK = {"hbm_gbs": 6400.0, "source": "fallback"}
 # on).  A capture on a smaller population is scaled by population (the
 # traffic grows with the genomes processed); the figure is reported only
 # while those sources are unchanged.
-_INTERNAL = ("paper_2504_08339_b300/csrc/neat_internal.cuh", "b0c429a08cd68ae5")
+_INTERNAL = ("paper_2504_08339_b300/csrc/neat_internal.cuh", "bb4235501a3fd269")
 TRAFFIC = {
-    ("locomotion", "k_forward_lvl"): (6490880, 2000, dict([
-        ("paper_2504_08339_b300/csrc/level.cu", "613a45af98c30e3a"), _INTERNAL])),
-    ("uneven", "k_forward_sp"): (106829056, 2048, dict([
-        ("paper_2504_08339_b300/csrc/forward.cu", "206a6d7795853bb2"), _INTERNAL])),
-    ("differentiation", "k_backward"): (360216576, 512, dict([
-        ("paper_2504_08339_b300/csrc/backward.cu", "221df7ba2447ddd9"), _INTERNAL])),
+    ("locomotion", "k_forward_lvl"): (32804864, 10000, dict([
+        ("paper_2504_08339_b300/csrc/level.cu", "69edb52bbdb8ceb6"), _INTERNAL])),
+    ("uneven", "k_forward_sp"): (107301376, 2048, dict([
+        ("paper_2504_08339_b300/csrc/forward.cu", "2f34e42f8cc43478"), _INTERNAL])),
+    ("differentiation", "k_backward"): (359663104, 512, dict([
+        ("paper_2504_08339_b300/csrc/backward.cu", "ae1c59197d133899"), _INTERNAL])),
 }
 
 
@@ -134,6 +134,9 @@ def parse_args():
     ap.add_argument("--pop", type=int, default=None,
                     help="population override (profiling captures and small cases; the line's "
                          "config then says so)")
+    ap.add_argument("--horizon", type=int, default=None,
+                    help="rollout steps override (profiling captures of the full population "
+                         "with a short rollout; the line's config then says so)")
     return ap.parse_args()
 
 
@@ -305,13 +308,15 @@ def live_note(E, E_live, V_live):
                     "the live part"}
 
 
-def workload(name, seed, pop=None):
+def workload(name, seed, pop=None, horizon=None):
     from workloads import CONFIGS, make_population
     # the distance workload is the locomotion population, all pairs
     base = {"distance": "locomotion", "mutate": "locomotion", "substrate": "hyperneat"}
     cfg = dict(CONFIGS[base.get(name, name)])
     if pop is not None:
         cfg["P"] = pop
+    if horizon is not None and "steps" in cfg:
+        cfg["steps"] = horizon
     spec = cfg["spec"]
     nodes, conns = make_population(spec, cfg["P"], seed=seed)
     return cfg, spec, nodes, conns
@@ -564,7 +569,7 @@ def bench_ours(args, rank, world, local, pg):
     dev = torch.device("cuda", local)
     peaks = load_peaks()
     name = args.config
-    cfg, spec, nodes, conns = workload(name, args.seed + rank, args.pop)
+    cfg, spec, nodes, conns = workload(name, args.seed + rank, args.pop, args.horizon)
     if name == "differentiation" and args.recompute:
         cfg["S"], cfg["recompute"] = cfg["S_recompute"], True
     P = cfg["P"]
@@ -1036,6 +1041,7 @@ def bench_ours(args, rank, world, local, pg):
         "data": "synthetic (seeded generators; random genomes shaped like the workload)",
         "config": {"workload": describe(name, cfg, spec), "name": name, "pop": P,
                    "pop_override": args.pop is not None,
+                   "horizon_override": args.horizon is not None,
                    "prune_dead": bool(args.prune), "tuning": tuning,
                    "enabled_conns_per_genome_mean": round(float(E.mean()), 2),
                    "valid_nodes_per_genome_mean": round(float(Vn.mean()), 2),
@@ -1056,7 +1062,7 @@ def bench_reference(args, rank, world):
     if rank != 0:
         return
     name = args.config
-    cfg, spec, nodes, conns = workload(name, args.seed, args.pop)
+    cfg, spec, nodes, conns = workload(name, args.seed, args.pop, args.horizon)
     # per-step samples of about a second of single-core work, grown with the
     # cores the oracle's genome split uses
     scale = max(1, (os.cpu_count() or 1) // 2)
