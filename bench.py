@@ -51,7 +51,7 @@ PEAKS_FALLBACK = {"hbm_gbs": 6400.0, "source": "fallback"}
 # on).  A capture on a smaller population is scaled by population (the
 # traffic grows with the genomes processed); the figure is reported only
 # while those sources are unchanged.
-_INTERNAL = ("paper_2504_08339_b300/csrc/neat_internal.cuh", "bb4235501a3fd269")
+_INTERNAL = ("paper_2504_08339_b300/csrc/neat_internal.cuh", "a02a314aa4749d6d")
 TRAFFIC = {
     ("locomotion", "k_forward_lvl"): (32804864, 10000, dict([
         ("paper_2504_08339_b300/csrc/level.cu", "69edb52bbdb8ceb6"), _INTERNAL])),

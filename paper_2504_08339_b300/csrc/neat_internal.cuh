@@ -95,7 +95,8 @@ __host__ __device__ inline int cpair_cap(int N, int C) { return (C + N) / 2 + 1;
 //       memory (a bulk copy); the rest is read from global memory (L2), each
 //       round's records one round ahead
 //   rounds    uint32[n_rounds + 1]     first task | first chunk << 16
-//   tasks     TaskRec[n_tasks]         non-input nodes, by (layer, act, -cnt)
+//   tasks     TaskRec[n_tasks]         non-input nodes, by (layer, activation
+//                                      class, act, -cnt)
 //   eslot     uint16[4 * n_chunks]     source value slot of each edge; the first
 //                                      entry of a chunk carries the task's
 //                                      aggregation in bits 12-13
@@ -110,7 +111,7 @@ struct __align__(16) BatchHead {
 struct __align__(16) BatchLoc {
   int off;    // byte offset in the arena
   int bytes;  // program bytes (multiple of 16)
-  int head;   // bytes of the head part (= off_task, multiple of 16)
+  int head;   // bytes of the head part (= off_round, multiple of 16)
   int pad;
 };
 
