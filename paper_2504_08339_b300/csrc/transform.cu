@@ -17,6 +17,8 @@ namespace neat {
 namespace {
 
 constexpr float KEY_LIMIT = 16777216.0f;  // 2^24
+// genomes of at most this many valid nodes run Kahn's loop on one warp
+constexpr int KAHN_WARP_MAX_V = 256;
 
 __device__ __forceinline__ bool is_int_in(float x, float lo, float hi) {
   return x == x && x >= lo && x < hi && x == floorf(x);
@@ -125,7 +127,7 @@ __global__ void __launch_bounds__(256) k_transform(Ws w, const float *__restrict
   extern __shared__ __align__(16) unsigned char sm[];
   __shared__ int wbuf[33];
   __shared__ unsigned s_status;
-  __shared__ int s_V, s_E, s_nch, s_nlive, s_elive, s_crows;
+  __shared__ int s_V, s_E, s_nch, s_nlive, s_elive, s_crows, s_emit, s_t;
 
   const int N = w.N, C = w.C, I = w.I, O = w.O;
   const int g = blockIdx.x, tid = threadIdx.x, T = blockDim.x;
@@ -291,6 +293,55 @@ __global__ void __launch_bounds__(256) k_transform(Ws w, const float *__restrict
       emitted = V;
       t = V > 0 ? 1 : 0;
     }
+  } else if ((status0 & ~NEAT_G_CYCLE) == 0u && V <= KAHN_WARP_MAX_V) {
+    // one warp: a frontier is the ready flags of 32-node chunks as ballots,
+    // each emitted node's position the popc of the ready bits below it; no
+    // CTA barrier inside the loop (the other warps wait at the one after it)
+    if (tid < 32) {
+      const int lane = tid;
+      for (int s = lane; s < V; s += 32) {
+        rem[s] = indeg[s];
+        ready[s] = indeg[s] == 0;
+      }
+      __syncwarp();
+      const unsigned below = (1u << lane) - 1u;
+      for (int round = 0; round <= V; ++round) {  // bounded: each round emits >= 1 node
+        int F = 0;
+        for (int c = 0; c < V; c += 32) {
+          const int s = c + lane;
+          const bool r = s < V && ready[s] != 0;
+          const unsigned m = __ballot_sync(0xffffffffu, r);
+          if (r) {
+            const int p = emitted + F + __popc(m & below);
+            order_s[p] = s;
+            layer_s[s] = t;
+            pos_of[s] = p;
+            ready[s] = 0;
+          }
+          F += __popc(m);
+        }
+        if (F == 0) break;
+        __syncwarp();
+        for (int p = emitted + lane; p < emitted + F; p += 32) {
+          const int s = order_s[p];
+          for (int k = outbeg[s]; k < outbeg[s] + outfill[s]; ++k) {
+            const int d = outlist[k];
+            if (atomicSub(&rem[d], 1) == 1) ready[d] = 1;
+          }
+        }
+        __syncwarp();
+        emitted += F;
+        ++t;
+      }
+      if (lane == 0) {
+        s_emit = emitted;
+        s_t = t;
+        if (emitted < V) atomicOr(&s_status, NEAT_G_CYCLE);
+      }
+    }
+    __syncthreads();
+    emitted = s_emit;
+    t = s_t;
   } else if ((status0 & ~NEAT_G_CYCLE) == 0u) {
     for (int s = tid; s < V; s += T) {
       rem[s] = indeg[s];
