@@ -21,6 +21,9 @@ struct neat_plan {
   int smem_optin;
   neat_tuning tune;
   int transformed;  // 0: none, 1: feed-forward (neat_transform), 2: recurrent
+  // 1 while the plan's last call was a transform: a level forward then must
+  // not overlap the kernel before it (the batch programs' writer)
+  int after_transform;
 };
 
 namespace {
@@ -273,6 +276,7 @@ neat_status neat_transform(neat_plan *plan, const float *nodes, const float *con
         !aligned(n_layers, 4) || !aligned(gstatus, 4))
       return NEAT_ERR_ARG;
   }
+  plan->after_transform = 1;  // (set before any launch: also on a failure below)
   // the batch budget is fixed by the transform that builds the batches
   plan->w.prune = plan->tune.prune_dead == 1 ? 1 : 0;
   plan->w.lvl_budget =
@@ -304,8 +308,11 @@ neat_status neat_forward(neat_plan *plan, const float *inputs, int64_t in_pop_st
     const int warps = lvl_warps(plan, st, &occ);
     const int64_t want = (int64_t(plan->P) + warps - 1) / warps;  // batches <= P
     const int grid = int(std::max<int64_t>(1, std::min<int64_t>(int64_t(plan->sm_count) * occ, want)));
+    // programmatic dependent launch unless the previous call was a transform
+    const int pdl = plan->after_transform ? 0 : 1;
+    plan->after_transform = 0;
     return cuda_status(neat::launch_forward_lvl(plan->w, inputs, in_pop_stride, S, outputs, warps,
-                                                grid, wait_polls(plan), stream));
+                                                grid, wait_polls(plan), pdl, stream));
   }
   const neat::SpShape sh = sp_shape(plan, S);
   if (int64_t(sh.grid) * sh.warps > neat::sp_scratch_slots(plan->w, sh.spl))
@@ -458,6 +465,7 @@ neat_status neat_transform_recurrent(neat_plan *plan, const float *nodes, const 
   if (e == cudaSuccess) e = neat::launch_queue_build(plan->w, 0, stream);
   if (e != cudaSuccess) return cuda_status(e);
   plan->transformed = 2;
+  plan->after_transform = 1;
   return NEAT_OK;
 }
 

@@ -722,9 +722,18 @@ constexpr int LVL_MAX_WARPS = 8;
 // (launch bound: two CTAs of 8 warps per SM, at most 128 registers a thread;
 // a 64-register cap spilled the rounds, and above 128 only 12 warps fit)
 template <int ST>
+//
+// pdl (the launch follows a forward of the same batches in its stream, with
+// programmatic serialization): the CTAs may start while the previous launch's
+// last warps still run, on the SMs it has left; they let the next launch do
+// the same at once, stage their first batch's head (batch programs are not
+// written by a forward), and wait for the previous grid (griddepcontrol.wait:
+// its completion and memory) before reading inputs, claiming batches or
+// writing anything.
 __global__ void __launch_bounds__(32 * LVL_MAX_WARPS, 2) k_forward_lvl(
     Ws w, const float *__restrict__ inputs, int64_t stride, int S, float *__restrict__ out,
-    int warp_bytes, int vals_bytes, int polls) {
+    int warp_bytes, int vals_bytes, int polls, int pdl) {
+  if (pdl) asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   extern __shared__ __align__(128) unsigned char sm[];
   __shared__ __align__(8) uint64_t mbar[LVL_MAX_WARPS];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -802,6 +811,10 @@ __global__ void __launch_bounds__(32 * LVL_MAX_WARPS, 2) k_forward_lvl(
                          reinterpret_cast<const uint2 *>(src + hg.off_eslot),
                          reinterpret_cast<const uint4 *>(src + hg.off_ew), part_a, v_a};
     const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(mb, parity, polls));
+    if (pdl) {  // (once: the first batch; later ones come after it)
+      asm volatile("griddepcontrol.wait;" ::: "memory");
+      pdl = 0;
+    }
     if (ok) {
       const int *gio = reinterpret_cast<const int *>(head + hg.off_gio);
       if (lane < 2 * ST) v[lane] = lane < ST ? 0.0f : 1.0f;  // the constant slots 0 and 1
@@ -879,19 +892,29 @@ cudaError_t launch_lvl_build(const Ws &w, cudaStream_t st) {
 }
 
 cudaError_t launch_forward_lvl(const Ws &w, const float *inputs, int64_t stride, int S,
-                               float *outputs, int warps, int grid, int polls, cudaStream_t st) {
+                               float *outputs, int warps, int grid, int polls, int pdl,
+                               cudaStream_t st) {
   if (w.P == 0 || S == 0) return cudaSuccess;
   const int ST = lvl_tile(S);
   const int wb = int(lvl_warp_bytes(w, ST)), vb = int(lvl_vals_bytes(w, ST));
-  const size_t smem = size_t(wb) * warps;
-  const int threads = 32 * warps;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(grid));
+  cfg.blockDim = dim3(unsigned(32 * warps));
+  cfg.dynamicSmemBytes = size_t(wb) * warps;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl ? 1 : 0;
   if (ST == 1)
-    k_forward_lvl<1><<<grid, threads, smem, st>>>(w, inputs, stride, S, outputs, wb, vb, polls);
-  else if (ST == 2)
-    k_forward_lvl<2><<<grid, threads, smem, st>>>(w, inputs, stride, S, outputs, wb, vb, polls);
-  else
-    k_forward_lvl<4><<<grid, threads, smem, st>>>(w, inputs, stride, S, outputs, wb, vb, polls);
-  return cudaGetLastError();
+    return cudaLaunchKernelEx(&cfg, k_forward_lvl<1>, w, inputs, stride, S, outputs, wb, vb, polls,
+                              pdl);
+  if (ST == 2)
+    return cudaLaunchKernelEx(&cfg, k_forward_lvl<2>, w, inputs, stride, S, outputs, wb, vb, polls,
+                              pdl);
+  return cudaLaunchKernelEx(&cfg, k_forward_lvl<4>, w, inputs, stride, S, outputs, wb, vb, polls,
+                            pdl);
 }
 
 cudaError_t lvl_set_smem_limit(int bytes) {

@@ -548,7 +548,8 @@ size_t lvl_vals_bytes(const Ws &w, int st_samples);
 // `warps` per CTA, each owning lvl_warp_bytes; a staging wait gives up after
 // `polls` polls (0: at once)
 cudaError_t launch_forward_lvl(const Ws &w, const float *inputs, int64_t stride, int S,
-                               float *outputs, int warps, int grid, int polls, cudaStream_t st);
+                               float *outputs, int warps, int grid, int polls, int pdl,
+                               cudaStream_t st);
 cudaError_t lvl_set_smem_limit(int bytes);
 int forward_lvl_occupancy(int warps, size_t smem, int st_samples);
 int lvl_tile(int S);

@@ -484,6 +484,45 @@ def test_autograd_switches_to_recompute_above_the_budget():
         compare_grads(gn[..., 2].cpu().numpy(), rr, "r")
 
 
+def test_back_to_back_level_forwards_each_match_the_oracle():
+    """Consecutive level-synchronous forwards on one plan (programmatic
+    dependent launch: each may start while the previous one ends), eager and
+    in a captured graph, with a transform of another population in between:
+    every launch's outputs match the oracle on its own inputs."""
+    P = 1500
+    na, ca, spec = population_for("locomotion", seed=21, P=P)
+    nb, cb, _ = population_for("locomotion", seed=22, P=P)
+    xs = [locomotion_inputs(21, t, P, spec.I) for t in range(6)]
+    plan = _plan(spec, P)
+    for nodes, conns in ((na, ca), (nb, cb)):
+        plan.transform(_dev(nodes), _dev(conns))
+        outs = [plan.forward(_dev(x)) for x in xs[:3]]
+        torch.cuda.synchronize()
+        for x, o in zip(xs[:3], outs):
+            ref, bnd = oracle.forward(nodes, conns, x, spec.I, spec.O, with_bound=True)
+            compare_outputs(o.cpu().numpy(), ref, bnd)
+    # captured: three launches in one graph, replayed after a fresh transform
+    xd = [_dev(x) for x in xs[3:]]
+    od = [torch.empty((P, 1, spec.O), device="cuda") for _ in xd]
+    plan.transform(_dev(na), _dev(ca))
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        plan.forward(xd[0], out=od[0])  # the first after the transform, outside the graph
+        s.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            for x, o in zip(xd, od):
+                plan.forward(x, out=o)
+    for o in od:
+        o.fill_(float("nan"))
+    g.replay()
+    torch.cuda.synchronize()
+    plan.check()
+    for x, o in zip(xs[3:], od):
+        ref, bnd = oracle.forward(na, ca, x, spec.I, spec.O, with_bound=True)
+        compare_outputs(o.cpu().numpy(), ref, bnd)
+
+
 def test_hyperneat_full_grid_small():
     nodes, conns, spec = population_for("hyperneat", seed=6, P=12)
     plan = _plan(spec, 12)
