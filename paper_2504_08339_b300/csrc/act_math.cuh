@@ -6,19 +6,20 @@
 // full.  Methods (all in fp32):
 //   exp   the argument clamped to [-87, 88] (NaN passes through), then Cody
 //         and Waite's reduction x = k ln2 + r, |r| <= ln2 / 2 (ln2 split in a
-//         15-bit high part, so k ln2_hi is exact, and a low part), e^r by its
-//         Taylor polynomial of degree 7 (truncation below 1e-8 relative),
-//         scaled by 2^k, k in [-126, 127], exactly.  The clamp keeps every
-//         result finite and normal: below e^-87 the result is e^-87 (1.6e-38)
-//         and above e^88 it is e^88, which moves sigmoid, tanh and gaussian
-//         by less than 2e-38 where it applies.
+//         15-bit high part, so k ln2_hi is exact, and a low part);
+//         e^r - 1 = r Q(r) with Q the Taylor series of (e^r - 1) / r to
+//         degree 6 (truncation below 2e-8 relative); e^x = (r Q(r) + 1) 2^k,
+//         k in [-126, 127], scaled exactly; e^x - 1 = r Q(r) itself when
+//         k = 0 (no cancellation near x = 0), else e^x - 1 (|e^x - 1| >= 0.29:
+//         no cancellation either).  The clamp keeps every result finite and
+//         normal: below e^-87 the result is e^-87 (1.6e-38) and above e^88 it
+//         is e^88, which moves sigmoid, tanh and gaussian by less than 2e-38
+//         where it applies.
 //   1/d   (1 <= d < 2^128) the hardware reciprocal approximation refined by
 //         one Newton-Raphson step, y = y0 + y0 (1 - d y0); a result below
 //         2^-126 flushes to 0.
-//   tanh  |z| >= 0.55: 1 - 2 / (e^{2|z|} + 1) (no cancellation: tanh >= 0.5);
-//         |z| < 0.55: the odd Taylor series z + sum_{n=2..10} c_n z^{2n-1},
-//         c_n = 2^{2n} (2^{2n} - 1) B_{2n} / (2n)! (Bernoulli numbers; the
-//         dropped terms are below 1e-9 there).
+//   tanh  tanh |z| = -m / (2 + m) with m = e^{-2|z|} - 1 from the above (the
+//         reciprocal shared with sigmoid's 1 / (2 + (e^{-z} - 1))), sign of z.
 //   sin   Cody-Waite reduction by pi/2 with a three-part constant, each step a
 //         fused multiply-add (the product k c_i exact inside it, one rounding
 //         of a result below 1 in magnitude), then the Taylor polynomials of
@@ -47,8 +48,8 @@ constexpr float PIO2_2 = -4.371138828673793e-08f;  // fp32(pi/2 - PIO2_1)
 constexpr float PIO2_3 = -1.7151245100058819e-15f; // fp32(pi/2 - PIO2_1 - PIO2_2)
 constexpr float SIN_ARG_MAX = 6.5e6f;
 
-// e^x (see the header comment)
-__device__ __forceinline__ float exp_cw(float x) {
+// e^x and e^x - 1 (see the header comment)
+__device__ __forceinline__ void exp_expm1_cw(float x, float &e, float &m) {
   float xc;
   asm("max.NaN.f32 %0, %1, %2;" : "=f"(xc) : "f"(x), "f"(-87.0f));
   asm("min.NaN.f32 %0, %1, %2;" : "=f"(xc) : "f"(xc), "f"(88.0f));
@@ -57,16 +58,17 @@ __device__ __forceinline__ float exp_cw(float x) {
   const int ki = __float_as_int(t) - MAGIC_BITS;
   float r = fmaf(k, -LN2_HI, xc);
   r = fmaf(k, -LN2_LO, r);
-  float p = 1.98412698412698413e-4f;  // 1/7!
+  float p = 1.98412698412698413e-4f;        // 1/7!
   p = fmaf(p, r, 1.38888888888888889e-3f);  // 1/6!
   p = fmaf(p, r, 8.33333333333333333e-3f);  // 1/5!
   p = fmaf(p, r, 4.16666666666666667e-2f);  // 1/4!
   p = fmaf(p, r, 1.66666666666666667e-1f);  // 1/3!
   p = fmaf(p, r, 0.5f);
   p = fmaf(p, r, 1.0f);
-  p = fmaf(p, r, 1.0f);
-  // (a NaN argument leaves p NaN, whatever the scale's bits)
-  return p * __int_as_float((ki + 127) << 23);
+  const float rq = r * p;  // e^r - 1
+  // (a NaN argument leaves rq NaN, whatever the scale's bits)
+  e = (rq + 1.0f) * __int_as_float((ki + 127) << 23);
+  m = ki == 0 ? rq : e - 1.0f;
 }
 
 // 1 / d for finite d >= 1, or NaN
@@ -74,21 +76,6 @@ __device__ __forceinline__ float rcp_nr(float d) {
   float y0;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"(d));
   return fmaf(fmaf(-d, y0, 1.0f), y0, y0);
-}
-
-// tanh z for |z| < 0.55: z + z^3 P(z^2)
-__device__ __forceinline__ float tanh_series(float z) {
-  const float w = z * z;
-  float p = -2.39129114243552482e-4f;        // c10
-  p = fmaf(p, w, 5.90027440945585880e-4f);   // c9
-  p = fmaf(p, w, -1.45583438705131827e-3f);  // c8
-  p = fmaf(p, w, 3.59212803657248102e-3f);   // c7
-  p = fmaf(p, w, -8.86323552990219657e-3f);  // c6
-  p = fmaf(p, w, 2.18694885361552028e-2f);   // c5
-  p = fmaf(p, w, -5.39682539682539683e-2f);  // c4
-  p = fmaf(p, w, 1.33333333333333333e-1f);   // c3
-  p = fmaf(p, w, -3.33333333333333333e-1f);  // c2
-  return fmaf(z * w, p, z);
 }
 
 // sin z and cos z for |z| <= SIN_ARG_MAX (quadrant k mod 4 of the reduction)

@@ -480,7 +480,7 @@ __device__ __forceinline__ void sts_f32_a(uint32_t a, float x) {
 // Activation of one value per lane, the lanes holding nodes of mixed
 // activations.  `mask` (bit a: some task of the pass, or of a superset such
 // as the whole batch, has activation a; the same on every lane) names the
-// evaluations needed: one exponential per lane
+// evaluations needed: one exponential (and e^x - 1) per lane
 // serves sigmoid, tanh and gaussian (act_exp_arg), one reciprocal sigmoid and
 // tanh, one sine the sin nodes; each is evaluated on every lane and the
 // lane's result selected, so no branch diverges (but for sine arguments
@@ -489,11 +489,13 @@ __device__ __forceinline__ float act_lanes(int a, float z, uint32_t mask) {
   float y = sel_eq<NEAT_ACT_RELU>(a, fmaxf(z, 0.0f), z);
   y = sel_eq<NEAT_ACT_ABS>(a, fabsf(z), y);
   if (mask & ACT_BIT_EXP) {
-    const float e = am::exp_cw(act_exp_arg(a, z));
-    const float q = am::rcp_nr(1.0f + e);
+    float e, m;  // e^x and e^x - 1 of the lane's argument
+    am::exp_expm1_cw(act_exp_arg(a, z), e, m);
+    const float q = am::rcp_nr(2.0f + m);  // 1 / (1 + e^x)
     y = sel_eq<NEAT_ACT_SIGMOID>(a, q, y);
     y = sel_eq<NEAT_ACT_GAUSSIAN>(a, e, y);
-    if (mask & (1u << NEAT_ACT_TANH)) y = sel_eq<NEAT_ACT_TANH>(a, tanh_of(z, q), y);
+    // tanh |z| = -(e^{-2|z|} - 1) / (1 + e^{-2|z|})
+    if (mask & (1u << NEAT_ACT_TANH)) y = sel_eq<NEAT_ACT_TANH>(a, copysignf(-m * q, z), y);
   }
   if (mask & ACT_BIT_SIN) {
     const float zs = sel_eq<NEAT_ACT_SIN>(a, z, 0.0f);

@@ -377,22 +377,13 @@ constexpr uint32_t ACT_BIT_EXP = (1u << NEAT_ACT_SIGMOID) | (1u << NEAT_ACT_TANH
 constexpr uint32_t ACT_BIT_SIN = 1u << NEAT_ACT_SIN;
 
 // argument of the one exponential an activation needs: e^{-z} (sigmoid),
-// e^{2|z|} (tanh), e^{-z^2} (gaussian); 0 for the others
+// e^{-2|z|} (tanh), e^{-z^2} (gaussian); 0 for the others
 __device__ __forceinline__ float act_exp_arg(int a, float z) {
   float x = sel_eq<NEAT_ACT_SIGMOID>(a, -z, 0.0f);
-  x = sel_eq<NEAT_ACT_TANH>(a, 2.0f * fabsf(z), x);
+  x = sel_eq<NEAT_ACT_TANH>(a, -2.0f * fabsf(z), x);
   return sel_eq<NEAT_ACT_GAUSSIAN>(a, -(z * z), x);
 }
 
-__device__ __forceinline__ float sin_any(float z) {
-  if (fabsf(z) > am::SIN_ARG_MAX) return sinf(z);  // rare: arguments beyond the reduction
-  return am::sin_cw(z);
-}
-
-// tanh z from q = 1 / (e^{2|z|} + 1): the series below |z| = 0.55
-__device__ __forceinline__ float tanh_of(float z, float q) {
-  return sel_if(fabsf(z) < 0.55f, am::tanh_series(z), copysignf(fmaf(-2.0f, q, 1.0f), z));
-}
 
 // act_a(z) for an activation id a in [0, 6] (the transform rejects others)
 // where every lane of the warp evaluates the same activation (the
