@@ -33,9 +33,10 @@ def candidates(plan: Plan, S: int):
     """Candidate tunings for S samples per genome."""
     out = []
     if S <= 8:
-        for kb in (8, 10, 12, 16, 24):
+        for kb in (8, 10, 12, 16, 18, 24):
             out.append(dict(lvl_budget_kb=kb))
         out.append(dict(lvl_budget_kb=12, lvl_threads=64))
+        out.append(dict(lvl_budget_kb=16, lvl_threads=128))
     for spl in (1, 2, 4):
         if spl > 1 and S < 32 * spl:
             continue
