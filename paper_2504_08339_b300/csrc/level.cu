@@ -691,13 +691,20 @@ __device__ __forceinline__ void one_round(const BatchArrays &ba, int r, int nr, 
 
 // all rounds of a batch for one sample; the next batch is claimed when
 // round claim_at starts
+// the first round's records and the round-table entries of rounds 2 and 3,
+// loaded before the batch's staging and input waits
+__device__ __forceinline__ void first_round(const BatchArrays &ba, int nr, int lane, RoundRecs &x0,
+                                            uint32_t (&rq)[2]) {
+  rq[0] = nr >= 2 ? __ldg(ba.rt + 2) : 0u;
+  rq[1] = nr >= 3 ? __ldg(ba.rt + 3) : 0u;
+  if (nr > 0) load_round(ba, __ldg(ba.rt), __ldg(ba.rt + 1), lane, x0);
+}
+
 __device__ __forceinline__ void run_rounds_st1(const BatchArrays &ba, int nr, int lane, int claim_at,
                                                unsigned long long *claim, unsigned long long &old,
-                                               bool &claimed) {
+                                               bool &claimed, RoundRecs &x0, uint32_t (&rq)[2]) {
   if (nr <= 0) return;
-  uint32_t rq[2] = {nr >= 2 ? __ldg(ba.rt + 2) : 0u, nr >= 3 ? __ldg(ba.rt + 3) : 0u};
-  RoundRecs x0, x1;
-  load_round(ba, __ldg(ba.rt), __ldg(ba.rt + 1), lane, x0);
+  RoundRecs x1;
   for (int r = 0; r < nr; r += 2) {
     if (r >= claim_at && !claimed) {  // the next batch, a few rounds before this one ends
       if (lane == 0) old = atomicAdd(claim, 1ull);
@@ -812,6 +819,10 @@ __global__ void __launch_bounds__(32 * LVL_MAX_WARPS, 2) k_forward_lvl(
                          reinterpret_cast<const uint4 *>(src + hg.off_task),
                          reinterpret_cast<const uint2 *>(src + hg.off_eslot),
                          reinterpret_cast<const uint4 *>(src + hg.off_ew), part_a, v_a};
+    // (one sample per genome: the first round's records load during the waits)
+    RoundRecs x0;
+    uint32_t rq[2];
+    if constexpr (ST == 1) first_round(ba, hg.n_rounds, lane, x0, rq);
     const bool ok = __all_sync(0xffffffffu, mbar_wait_bounded(mb, parity, polls));
     if (pdl) {  // (once: the first batch; later ones come after it)
       asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -833,7 +844,8 @@ __global__ void __launch_bounds__(32 * LVL_MAX_WARPS, 2) k_forward_lvl(
         }
         __syncwarp();
         if constexpr (ST == 1) {
-          run_rounds_st1(ba, hg.n_rounds, lane, max(hg.n_rounds - 3, 0), claim, old, claimed);
+          run_rounds_st1(ba, hg.n_rounds, lane, max(hg.n_rounds - 3, 0), claim, old, claimed,
+                         x0, rq);
         } else {
           for (int r = 0; r < hg.n_rounds; ++r) {
             const uint32_t r0 = __ldg(ba.rt + r), r1 = __ldg(ba.rt + r + 1);
