@@ -727,6 +727,7 @@ __device__ void nan_batch_outputs(const Ws &w, int b, int S, float *__restrict__
 }
 
 constexpr int LVL_MAX_WARPS = 8;
+constexpr int IN_FLIGHT = 8;  // input loads a lane issues before storing them
 
 // (launch bound: two CTAs of 8 warps per SM, at most 128 registers a thread;
 // a 64-register cap spilled the rounds, and above 128 only 12 warps fit)
@@ -832,15 +833,30 @@ __global__ void __launch_bounds__(32 * LVL_MAX_WARPS, 2) k_forward_lvl(
       const int *gio = reinterpret_cast<const int *>(head + hg.off_gio);
       if (lane < 2 * ST) v[lane] = lane < ST ? 0.0f : 1.0f;  // the constant slots 0 and 1
       for (int s0 = 0; s0 < S; s0 += ST) {
-        for (int it = lane, k = ki0, i = ii0; it < hg.n_genomes * I * ST; it += 32) {
-          const int slot = gio[k * G + 1 + i];
-          const int gs = s0 + s_l;
-          if (slot >= 0)
-            v[slot * ST + s_l] =
-                gs < S ? __ldg(inputs + size_t(gio[k * G]) * stride + size_t(gs) * I + i) : 0.0f;
-          k += dki;
-          i += dii;
-          if (i >= I) { i -= I; ++k; }
+        // the lane's items in groups of IN_FLIGHT: all of a group's loads are
+        // issued before its stores, so their L2 latencies overlap
+        const int n_in = hg.n_genomes * I * ST;
+        for (int it = lane, k = ki0, i = ii0; it < n_in;) {
+          float xv[IN_FLIGHT];
+          int sl[IN_FLIGHT];
+#pragma unroll
+          for (int u = 0; u < IN_FLIGHT; ++u) {
+            sl[u] = -1;
+            xv[u] = 0.0f;
+            if (it < n_in) {
+              const int gs = s0 + s_l;
+              sl[u] = gio[k * G + 1 + i];
+              if (sl[u] >= 0 && gs < S)
+                xv[u] = __ldg(inputs + size_t(gio[k * G]) * stride + size_t(gs) * I + i);
+            }
+            it += 32;
+            k += dki;
+            i += dii;
+            if (i >= I) { i -= I; ++k; }
+          }
+#pragma unroll
+          for (int u = 0; u < IN_FLIGHT; ++u)
+            if (sl[u] >= 0) v[sl[u] * ST + s_l] = xv[u];
         }
         __syncwarp();
         if constexpr (ST == 1) {
