@@ -53,8 +53,8 @@ PEAKS_FALLBACK = {"hbm_gbs": 6400.0, "source": "fallback"}
 # while those sources are unchanged.
 _INTERNAL = ("paper_2504_08339_b300/csrc/neat_internal.cuh", "5be1bbcbb9251329")
 TRAFFIC = {
-    ("locomotion", "k_forward_lvl"): (32796672, 10000, dict([
-        ("paper_2504_08339_b300/csrc/level.cu", "e7cf1b3a027ec5bb"), _INTERNAL])),
+    ("locomotion", "k_forward_lvl"): (32797440, 10000, dict([
+        ("paper_2504_08339_b300/csrc/level.cu", "4d90ee09c2054b8d"), _INTERNAL])),
     ("uneven", "k_forward_sp"): (107301376, 2048, dict([
         ("paper_2504_08339_b300/csrc/forward.cu", "2f34e42f8cc43478"), _INTERNAL])),
     ("differentiation", "k_backward"): (359663104, 512, dict([
