@@ -137,10 +137,12 @@ neat_status neat_plan_destroy(neat_plan *plan);
  *                    -1 = never; default 8); larger S, calls that ask for the
  *                    saved aggregates, and batches that do not fit in shared
  *                    memory use the sample-parallel forward
- *   lvl_budget_kb    program bytes (KiB, 8..160) of a level-synchronous batch,
- *                    the shared-memory buffer of one warp (raised to what the
- *                    largest possible genome of the plan needs); applied by the
- *                    next neat_transform
+ *   lvl_budget_kb    program bytes (KiB, 8..160) of a level-synchronous batch
+ *                    (raised to what the largest possible genome of the plan
+ *                    needs); applied by the next neat_transform.  0 (default,
+ *                    reported as 0): each transform picks the smallest budget,
+ *                    in 128-byte steps, whose batches do not outnumber the
+ *                    warps a one-sample forward keeps resident
  *   prune_dead       0 (default): every valid node is evaluated, as the
  *                    paper's calculation does; 1: forwards that return only the
  *                    outputs, the HyperNEAT query and the backward skip the

@@ -33,6 +33,7 @@ def candidates(plan: Plan, S: int):
     """Candidate tunings for S samples per genome."""
     out = []
     if S <= 8:
+        out.append(dict())  # the default: batches cut to the resident warps
         for kb in (8, 10, 12, 16, 18, 24):
             out.append(dict(lvl_budget_kb=kb))
         out.append(dict(lvl_budget_kb=12, lvl_threads=64))

@@ -236,8 +236,7 @@ neat_status neat_plan_get_tuning(const neat_plan *plan, neat_tuning *t) {
   if (t->samples_per_lane == 0) t->samples_per_lane = sh.spl;
   if (t->lvl_threads == 0) t->lvl_threads = 32 * lvl_warps(plan, 1, nullptr);
   if (t->small_s_max == 0) t->small_s_max = small_s_max(plan);
-  if (t->lvl_budget_kb == 0)
-    t->lvl_budget_kb = (neat::lvl_budget(plan->N, plan->C, plan->I, plan->O) + 1023) / 1024;
+  // (lvl_budget_kb 0 stays 0: the transform picks the budget per population)
   if (t->wait_polls == 0) t->wait_polls = wait_polls(plan);
   return NEAT_OK;
 }
@@ -286,7 +285,17 @@ neat_status neat_transform(neat_plan *plan, const float *nodes, const float *con
   if (e == cudaSuccess) e = neat::launch_transform(plan->w, nodes, conns, order, layer, n_layers, gstatus,
                                          stream);
   if (e == cudaSuccess) e = neat::launch_queue_build(plan->w, 0, stream);
-  if (e == cudaSuccess) e = neat::launch_lvl_build(plan->w, stream);
+  // without a budget knob the batches are cut to fill the resident warps of a
+  // one-sample forward (the rollout step's form)
+  int target = 0;
+  if (plan->tune.lvl_budget_kb == 0) {
+    int occ = 1;
+    const int warps = lvl_warps(plan, 1, &occ);
+    target = plan->sm_count * std::max(1, occ) * warps;
+  }
+  if (e == cudaSuccess)
+    e = neat::launch_lvl_build(plan->w, target,
+                               neat::lvl_min_budget(plan->N, plan->C, plan->I, plan->O), stream);
   if (e != cudaSuccess) return cuda_status(e);
   plan->transformed = 1;
   return NEAT_OK;

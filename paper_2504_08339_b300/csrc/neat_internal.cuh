@@ -161,9 +161,10 @@ inline int lvl_min_budget(int N, int C, int I, int O) {
 constexpr int LVL_MIN_BUDGET = 8 * 1024;    // smallest budget knob (KiB granularity)
 constexpr int LVL_MAX_BUDGET = 160 * 1024;  // largest budget knob
 inline int lvl_budget(int N, int C, int I, int O, int knob_bytes = 0) {
-  // 16 KiB: about five locomotion-sized genomes per warp batch (rounds of
-  // about 21 tasks and 35 chunks); measured best of 12..48 KiB on the
-  // locomotion rollout
+  // the budget of an explicit knob; without one the transform searches for
+  // the budget that fills the resident warps (k_lvl_plan), and this 16 KiB
+  // (about five locomotion-sized genomes per warp batch, rounds of about 21
+  // tasks and 35 chunks) is only the fallback value kept in the workspace
   const int want = knob_bytes > 0 ? knob_bytes : 16 * 1024;
   const int m = lvl_min_budget(N, C, I, O);
   return want > m ? ((want + 127) & ~127) : m;
@@ -531,7 +532,9 @@ cudaError_t backward_set_smem_limit(int bytes);
 int forward_sp_occupancy(int warps, size_t smem, int spl);
 int hyperneat_occupancy(int spl, int warps, size_t smem);
 // level-synchronous small-S form
-cudaError_t launch_lvl_build(const Ws &w, cudaStream_t st);
+// level batches: target > 0 picks the smallest budget (from budget_lo up)
+// whose cut gives at most `target` batches; target 0 uses w.lvl_budget
+cudaError_t launch_lvl_build(const Ws &w, int target, int budget_lo, cudaStream_t st);
 // shared memory of one warp of the level-synchronous forward: its staged head
 // part, value slots and chunk partials for st_samples per tile
 size_t lvl_warp_bytes(const Ws &w, int st_samples);
