@@ -51,10 +51,10 @@ PEAKS_FALLBACK = {"hbm_gbs": 6400.0, "source": "fallback"}
 # on).  A capture on a smaller population is scaled by population (the
 # traffic grows with the genomes processed); the figure is reported only
 # while those sources are unchanged.
-_INTERNAL = ("paper_2504_08339_b300/csrc/neat_internal.cuh", "5be1bbcbb9251329")
+_INTERNAL = ("paper_2504_08339_b300/csrc/neat_internal.cuh", "07bc367562034a61")
 TRAFFIC = {
     ("locomotion", "k_forward_lvl"): (32797440, 10000, dict([
-        ("paper_2504_08339_b300/csrc/level.cu", "4d90ee09c2054b8d"), _INTERNAL])),
+        ("paper_2504_08339_b300/csrc/level.cu", "9c35aa382f0efee0"), _INTERNAL])),
     ("uneven", "k_forward_sp"): (107301376, 2048, dict([
         ("paper_2504_08339_b300/csrc/forward.cu", "2f34e42f8cc43478"), _INTERNAL])),
     ("differentiation", "k_backward"): (359663104, 512, dict([
