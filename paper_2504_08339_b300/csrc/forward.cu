@@ -604,17 +604,22 @@ __global__ void __launch_bounds__(512, 3)
 }
 
 // Recurrent calculation (T synchronous iterations; inputs clamped, v^0 = 0
-// elsewhere, outputs v^T).  Warps claim (genome, 32-sample tile) items from
-// the size-sorted queue; the warp's workspace slot holds two [N][32] value
-// buffers, v^{t-1} (read) and v^t (written), swapped after every iteration.
-__global__ void __launch_bounds__(512, 3)
+// elsewhere, outputs v^T).  Warps claim (genome, 32 * SPL-sample tile) items
+// from the size-sorted queue; lane l evaluates samples tile * 32 * SPL +
+// j * 32 + l, j < SPL (every record load serves SPL samples).  The warp's
+// workspace slot holds two [N][SPL][32] value buffers, v^{t-1} (read) and
+// v^t (written), swapped after every iteration.
+// (launch bound: the workspace slots keep the grid near 24 warps per SM)
+template <int SPL>
+__global__ void __launch_bounds__(256, 4)
     k_forward_rec(Ws w, const float *__restrict__ inputs, int64_t stride, int S, int T,
                   float *__restrict__ out, int tiles) {
+  constexpr int RS = 32 * SPL;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int N = w.N, I = w.I, O = w.O;
   const size_t slot = size_t(blockIdx.x) * (blockDim.x >> 5) + wid;
-  float *buf = (w.sp_scratch != nullptr && (slot + 1) * 2 * size_t(N) * 32 <= w.sp_scratch_floats)
-                   ? w.sp_scratch + slot * 2 * size_t(N) * 32
+  float *buf = (w.sp_scratch != nullptr && (slot + 1) * 2 * size_t(N) * RS <= w.sp_scratch_floats)
+                   ? w.sp_scratch + slot * 2 * size_t(N) * RS
                    : nullptr;
   const int total = w.P * tiles;
   for (;;) {
@@ -625,27 +630,35 @@ __global__ void __launch_bounds__(512, 3)
     const int q = item / tiles, tile = item - q * tiles;
     const int g = w.qorder[q];
     const GenomeHdr h = w.hdr[g];
-    const int s = tile * 32 + lane;
-    const bool active = s < S;
-    float *orow = out + (size_t(g) * S + (active ? s : 0)) * O;
+    int sj[SPL];
+#pragma unroll
+    for (int j = 0; j < SPL; ++j) sj[j] = tile * RS + j * 32 + lane;
     if (h.status != 0u || buf == nullptr) {
       if (buf == nullptr && lane == 0) atomicOr(w.counters + CTR_ERR, ERR_SP_NO_SCRATCH);
-      if (active)
-        for (int o = 0; o < O; ++o) orow[o] = qnan();
+#pragma unroll
+      for (int j = 0; j < SPL; ++j)
+        if (sj[j] < S)
+          for (int o = 0; o < O; ++o) out[(size_t(g) * S + sj[j]) * O + o] = qnan();
       continue;
     }
-    float *a = buf + lane, *b = buf + size_t(N) * 32 + lane;
+    float *a = buf + lane, *b = buf + size_t(N) * RS + lane;  // value (p, j) at [(p * SPL + j) * 32]
     const int V = h.V;
-    for (int p = 0; p < V; ++p) {
-      a[p * 32] = 0.0f;
-      b[p * 32] = 0.0f;
-    }
+    for (int p = 0; p < V; ++p)
+#pragma unroll
+      for (int j = 0; j < SPL; ++j) {
+        a[(p * SPL + j) * 32] = 0.0f;
+        b[(p * SPL + j) * 32] = 0.0f;
+      }
     const int32_t *io = w.pio + size_t(g) * (I + O);
-    const float *in = inputs + size_t(g) * stride + size_t(active ? s : 0) * I;
-    for (int i = 0; i < I; ++i) {
-      const float x = active ? __ldg(in + i) : 0.0f;
-      a[io[i] * 32] = x;
-      b[io[i] * 32] = x;
+#pragma unroll
+    for (int j = 0; j < SPL; ++j) {
+      const bool active = sj[j] < S;
+      const float *in = inputs + size_t(g) * stride + size_t(active ? sj[j] : 0) * I;
+      for (int i = 0; i < I; ++i) {
+        const float x = active ? __ldg(in + i) : 0.0f;
+        a[(io[i] * SPL + j) * 32] = x;
+        b[(io[i] * SPL + j) * 32] = x;
+      }
     }
     const NodeRec *nr = w.knode + h.node_off;
     const EdgeRec *er = w.kedge + h.edge_off;
@@ -653,16 +666,22 @@ __global__ void __launch_bounds__(512, 3)
       for (int p = 0; p < V; ++p) {
         const NodeRec n = ld_node(nr + p);
         if (n.meta & META_INPUT) continue;
-        float ag[1];
-        node_agg<1>(n, er, a, ag);
-        b[p * 32] = act_apply(meta_act(n.meta), fmaf(n.resp, ag[0], n.bias));
+        float ag[SPL];
+        node_agg<SPL>(n, er, a, ag);
+#pragma unroll
+        for (int j = 0; j < SPL; ++j) ag[j] = fmaf(n.resp, ag[j], n.bias);
+        act_apply_n<SPL>(meta_act(n.meta), ag);
+#pragma unroll
+        for (int j = 0; j < SPL; ++j) b[(p * SPL + j) * 32] = ag[j];
       }
       float *tmp = a;
       a = b;
       b = tmp;
     }
-    if (active)
-      for (int o = 0; o < O; ++o) orow[o] = a[io[I + o] * 32];
+#pragma unroll
+    for (int j = 0; j < SPL; ++j)
+      if (sj[j] < S)
+        for (int o = 0; o < O; ++o) out[(size_t(g) * S + sj[j]) * O + o] = a[(io[I + o] * SPL + j) * 32];
   }
   grid_done_reset(w.counters + CTR_REC_ITEM, w.counters + CTR_REC_DONE);
 }
@@ -982,19 +1001,23 @@ cudaError_t launch_forward_plain(const Ws &w, const float *inputs, int64_t strid
 }
 
 cudaError_t launch_forward_recurrent(const Ws &w, const float *inputs, int64_t stride, int S,
-                                     int T, float *outputs, int warps, int grid, cudaStream_t st) {
+                                     int T, float *outputs, int spl, int warps, int grid,
+                                     cudaStream_t st) {
   if (w.P == 0 || S == 0) return cudaSuccess;
-  const int tiles = (S + 31) / 32;
-  k_forward_rec<<<grid, warps * 32, 0, st>>>(w, inputs, stride, S, T, outputs, tiles);
+  const int tiles = (S + 32 * spl - 1) / (32 * spl);
+  if (spl == 2)
+    k_forward_rec<2><<<grid, warps * 32, 0, st>>>(w, inputs, stride, S, T, outputs, tiles);
+  else
+    k_forward_rec<1><<<grid, warps * 32, 0, st>>>(w, inputs, stride, S, T, outputs, tiles);
   return cudaGetLastError();
 }
 
-int forward_rec_occupancy(int warps) {
+int forward_rec_occupancy(int warps, int spl) {
   int n = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_forward_rec, warps * 32, 0) !=
-      cudaSuccess)
-    return 0;
-  return n;
+  const cudaError_t e =
+      spl == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_forward_rec<2>, warps * 32, 0)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_forward_rec<1>, warps * 32, 0);
+  return e == cudaSuccess ? n : 0;
 }
 
 cudaError_t launch_hyperneat(const Ws &w, int G, float thresh, float *weights, int spl,

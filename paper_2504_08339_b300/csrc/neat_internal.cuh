@@ -483,11 +483,13 @@ inline int sp_scratch_slots(const Ws &w, int spl) {  // slots of N + 2 rows
 }
 cudaError_t launch_forward_plain(const Ws &w, const float *inputs, int64_t stride, int S,
                                  float *outputs, cudaStream_t st);
-// recurrent calculation: T synchronous iterations, `warps` per CTA, `grid`
-// CTAs (grid * warps <= sp_scratch_slots(w, 2): two value buffers per warp)
+// recurrent calculation: T synchronous iterations, spl (1 or 2) samples per
+// lane, `warps` per CTA, `grid` CTAs (grid * warps <= sp_scratch_slots(w,
+// 2 * spl): two value buffers per warp)
 cudaError_t launch_forward_recurrent(const Ws &w, const float *inputs, int64_t stride, int S,
-                                     int T, float *outputs, int warps, int grid, cudaStream_t st);
-int forward_rec_occupancy(int warps);
+                                     int T, float *outputs, int spl, int warps, int grid,
+                                     cudaStream_t st);
+int forward_rec_occupancy(int warps, int spl);
 // HyperNEAT two-sheet substrate: y = act(x W) per genome
 cudaError_t launch_substrate(const float *w, int P, int K, const float *x, int64_t stride, int S,
                              int act, float *y, cudaStream_t st);

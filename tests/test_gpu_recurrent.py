@@ -38,6 +38,22 @@ def test_recurrent_parity(T, shared):
     compare_outputs(out, ref, bnd, what=f"T={T}")
 
 
+@pytest.mark.parametrize("spl", [1, 2])
+def test_recurrent_samples_per_lane(spl):
+    """One or two samples per lane (the tuning's samples_per_lane): the same
+    outputs, against the oracle; S = 77 leaves a ragged last tile for both."""
+    P, S, T = 200, 77, 5
+    nodes, conns, spec = population_for("recurrent", seed=9, P=P)
+    x = np.random.default_rng(3).standard_normal((P, S, spec.I)).astype(np.float32)
+    plan = _plan(spec, P)
+    plan.set_tuning(samples_per_lane=spl)
+    plan.transform_recurrent(_dev(nodes), _dev(conns))
+    out = plan.forward_recurrent(_dev(x), T).cpu().numpy()
+    plan.check()
+    ref, bnd = oracle.forward_recurrent(nodes, conns, x, spec.I, spec.O, T, with_bound=True)
+    compare_outputs(out, ref, bnd, what=f"spl={spl}")
+
+
 def test_recurrent_status_bits_match_the_oracle():
     nodes, conns, spec = population_for("recurrent", seed=6, P=8)
     live = np.flatnonzero(~np.isnan(conns[0, :, 0]) & (conns[0, :, 3] != 0))
