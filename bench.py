@@ -47,11 +47,12 @@ PEAKS_FALLBACK = {"hbm_gbs": 6400.0, "source": "fallback"}
 
 # DRAM bytes (read + write) per launch of the timed kernel from one ncu
 # capture (summaries under profiles/), keyed by workload and kernel: (bytes,
-# population of the capture, hash prefixes of the kernel sources it was taken
-# on).  A capture on a smaller population is scaled by population (the
-# traffic grows with the genomes processed); the figure is reported only
-# while those sources are unchanged.
-_INTERNAL = ("paper_2504_08339_b300/csrc/neat_internal.cuh", "07bc367562034a61")
+# population of the capture, hash prefixes of the sources it was taken on:
+# the kernel's, and the library's where that picks the kernel's instantiation
+# and launch shape).  A capture on a smaller population is scaled by
+# population (the traffic grows with the genomes processed); the figure is
+# reported only while those sources are unchanged.
+_INTERNAL = ("paper_2504_08339_b300/csrc/neat_internal.cuh", "8d74f295807cc9cb")
 TRAFFIC = {
     ("locomotion", "k_forward_lvl"): (32797440, 10000, dict([
         ("paper_2504_08339_b300/csrc/level.cu", "9c35aa382f0efee0"), _INTERNAL])),
@@ -122,6 +123,10 @@ def parse_args():
     ap.add_argument("--tune", default="auto", choices=["auto", "default"],
                     help="auto: run the autotuner on the workload before timing "
                          "(the chosen tuning is recorded in config.tuning)")
+    ap.add_argument("--tuning", default=None,
+                    help="a given tuning, as JSON (e.g. '{\"samples_per_lane\": 2}'), "
+                         "instead of the autotuner (profiling captures of a small case in the "
+                         "full-size launch shape); recorded in config.tuning")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
@@ -580,11 +585,15 @@ def bench_ours(args, rank, world, local, pg):
     launches_per_step = 4  # transform, rank, offsets, pack
     extra = {}
     tuning = {"mode": args.tune, "chosen": {}}
+    if args.tuning is not None:
+        given = json.loads(args.tuning)
+        plan.set_tuning(**given, **({"prune_dead": 1} if args.prune else {}))
+        tuning = {"mode": "given", "chosen": given}
 
     def autotune_on(x_dev):
         """Run the autotuner on this population and one step's inputs (no
         cache: every run measures), keeping the prune setting."""
-        if args.tune != "auto":
+        if args.tune != "auto" or args.tuning is not None:
             return
         from paper_2504_08339_b300.autotune import autotune
         d_n = torch.from_numpy(nodes).to(dev)

@@ -48,11 +48,21 @@ neat_status cuda_status(cudaError_t e) { return neat::cuda_error_status(e); }
 // whole multiples of the SM count.
 neat::SpShape sp_shape(const neat_plan *p, int S) {
   neat::SpShape sh{};
-  sh.spl = p->tune.samples_per_lane > 0 ? p->tune.samples_per_lane : 1;
   // 8 warps; 4 for large genomes, whose most expensive members are evaluated
   // CTA-wide (smaller CTAs: more of them work on the big genomes at once,
   // measured 8 % faster on the uneven population)
   sh.warps = p->tune.warps_per_cta > 0 ? p->tune.warps_per_cta : (p->N > 256 ? 4 : 8);
+  // two samples a lane when the 64-sample tiles still fill every warp the
+  // GPU keeps resident at that width (the autotuner's choice on the uneven
+  // and differentiation workloads: 16,384 uneven genomes at S = 64, 1,065 ->
+  // 977 us), else one: with fewer tiles the warps are what is short (2,048
+  // of those genomes: 385 us with one, 485 us with two)
+  sh.spl = p->tune.samples_per_lane;
+  if (sh.spl <= 0) {
+    const int64_t tiles2 = int64_t(p->P) * ((int64_t(S) + 63) / 64);
+    const int occ2 = std::max(1, neat::forward_sp_occupancy(sh.warps, 0, 2));
+    sh.spl = S >= 64 && tiles2 >= int64_t(p->sm_count) * occ2 * sh.warps ? 2 : 1;
+  }
   sh.vcap = 0;
   sh.coop = 1;
   const int slots = neat::sp_scratch_slots(p->w, sh.spl);
@@ -233,7 +243,7 @@ neat_status neat_plan_get_tuning(const neat_plan *plan, neat_tuning *t) {
   *t = plan->tune;
   const neat::SpShape sh = sp_shape(plan, 32);
   if (t->warps_per_cta == 0) t->warps_per_cta = sh.warps;
-  if (t->samples_per_lane == 0) t->samples_per_lane = sh.spl;
+  // (samples_per_lane 0 stays 0: each forward picks it from its S)
   if (t->lvl_threads == 0) t->lvl_threads = 32 * lvl_warps(plan, 1, nullptr);
   if (t->small_s_max == 0) t->small_s_max = small_s_max(plan);
   // (lvl_budget_kb 0 stays 0: the transform picks the budget per population)

@@ -405,8 +405,14 @@ __device__ __forceinline__ void cwalk(const CNode *__restrict__ nodes, int nn,
 // reads another's value) with a barrier between frontiers, in the slot of the
 // CTA's first warp.  One warp walking such a genome alone would finish long
 // after the rest of the grid.  The remaining items are claimed per warp.
+//
+// One sample a lane fits 42 registers (three 512-thread CTAs an SM); two or
+// four a lane take up to 64 (two CTAs), which cuts their spills to a few
+// bytes: on the uneven population (16,384 genomes, S = 64) 1,050 -> 982 us
+// with two a lane, while one a lane at 64 registers loses more warps than it
+// gains (1,065 -> 1,250).
 template <int SPL, bool COMP>
-__global__ void __launch_bounds__(512, 3)
+__global__ void __launch_bounds__(512, SPL == 1 ? 3 : 2)
     k_forward_sp(Ws w, const float *__restrict__ inputs, int64_t stride, int S,
                              float *__restrict__ out, float *__restrict__ saved, int tiles,
                              int vcap, int coop) {
