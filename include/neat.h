@@ -130,9 +130,8 @@ neat_status neat_plan_destroy(neat_plan *plan);
  *   warps_per_cta    warps of a sample-parallel or HyperNEAT-query CTA (1..16)
  *   samples_per_lane samples one lane evaluates in the sample-parallel forward,
  *                    queries one lane evaluates in the HyperNEAT query (1, 2, 4);
- *                    0 (default, reported as 0): two for S >= 64 when the
- *                    population's 64-sample tiles fill every resident warp,
- *                    else one;
+ *                    0 (default, reported as 0): two for S >= 64 in calls
+ *                    without saved aggregates, else one;
  *                    the HyperNEAT query two; the recurrent forward one (it
  *                    takes 1 or 2, larger values as 2)
  *   lvl_threads      threads of a level-synchronous (small-sample) CTA: 32..256,

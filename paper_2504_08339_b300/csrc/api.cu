@@ -46,23 +46,20 @@ neat_status cuda_status(cudaError_t e) { return neat::cuda_error_status(e); }
 // than shared-memory value arrays on every workload: the L1 caches them and
 // many more warps fit on an SM); the slots bound the grid, which is kept to
 // whole multiples of the SM count.
-neat::SpShape sp_shape(const neat_plan *p, int S) {
+neat::SpShape sp_shape(const neat_plan *p, int S, bool compiled = true) {
   neat::SpShape sh{};
   // 8 warps; 4 for large genomes, whose most expensive members are evaluated
   // CTA-wide (smaller CTAs: more of them work on the big genomes at once,
   // measured 8 % faster on the uneven population)
   sh.warps = p->tune.warps_per_cta > 0 ? p->tune.warps_per_cta : (p->N > 256 ? 4 : 8);
-  // two samples a lane when the 64-sample tiles still fill every warp the
-  // GPU keeps resident at that width (the autotuner's choice on the uneven
-  // and differentiation workloads: 16,384 uneven genomes at S = 64, 1,065 ->
-  // 977 us), else one: with fewer tiles the warps are what is short (2,048
-  // of those genomes: 385 us with one, 485 us with two)
-  sh.spl = p->tune.samples_per_lane;
-  if (sh.spl <= 0) {
-    const int64_t tiles2 = int64_t(p->P) * ((int64_t(S) + 63) / 64);
-    const int occ2 = std::max(1, neat::forward_sp_occupancy(sh.warps, 0, 2));
-    sh.spl = S >= 64 && tiles2 >= int64_t(p->sm_count) * occ2 * sh.warps ? 2 : 1;
-  }
+  // the compiled walk (outputs only) takes two samples a lane from S = 64 (a
+  // tile of 64 samples; uneven genomes at S = 64, us per launch, one / two a
+  // lane: 266 / 204 for 256 genomes, 385 / 318 for 2,048, 1,067 / 886 for
+  // 16,384); the position walk (saved aggregates) and smaller S one
+  // (differentiation forward with saved aggregates, 2,048 genomes at S =
+  // 4096: 1,065 us with one, 1,137 with two)
+  sh.spl = p->tune.samples_per_lane > 0 ? p->tune.samples_per_lane
+                                        : (compiled && S >= 64 ? 2 : 1);
   sh.vcap = 0;
   sh.coop = 1;
   const int slots = neat::sp_scratch_slots(p->w, sh.spl);
@@ -333,7 +330,7 @@ neat_status neat_forward(neat_plan *plan, const float *inputs, int64_t in_pop_st
     return cuda_status(neat::launch_forward_lvl(plan->w, inputs, in_pop_stride, S, outputs, warps,
                                                 grid, wait_polls(plan), pdl, stream));
   }
-  const neat::SpShape sh = sp_shape(plan, S);
+  const neat::SpShape sh = sp_shape(plan, S, saved == nullptr && plan->w.cnode != nullptr);
   if (int64_t(sh.grid) * sh.warps > neat::sp_scratch_slots(plan->w, sh.spl))
     return NEAT_ERR_UNSUPPORTED;
   return cuda_status(neat::launch_forward_sp(plan->w, inputs, in_pop_stride, S, outputs, saved, sh,

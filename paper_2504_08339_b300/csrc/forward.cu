@@ -301,9 +301,20 @@ __device__ __forceinline__ void w_stv(waddr_t<GLOBAL> a, const float (&x)[SPL]) 
   }
 }
 
-// One compiled node (its 16-byte record nraw) for this lane's SPL samples.
+// whether a walk loads its records ahead of the evaluation (see cwalk)
 template <int SPL, bool GLOBAL>
-__device__ __forceinline__ void cnode_eval(const uint4 nraw, const waddr_t<GLOBAL> pairs,
+constexpr bool kCnPrefetch = SPL > 1 && GLOBAL;
+// the first edge pair of a compiled node (zeros when it has none)
+template <int SPL, bool GLOBAL>
+__device__ __forceinline__ uint4 cnode_first_pair(const uint4 nraw, const waddr_t<GLOBAL> pairs) {
+  const waddr_t<GLOBAL> pp = pairs + 16u * (nraw.z & ((1u << CN_PAIR_BITS) - 1u));
+  return (nraw.z >> CN_PAIR_BITS) != 0u ? w_ld16<GLOBAL>(pp) : make_uint4(0u, 0u, 0u, 0u);
+}
+// One compiled node (its 16-byte record nraw) for this lane's SPL samples;
+// e0 its first edge pair when the walk loads records ahead (kCnPrefetch),
+// else unused (the pair is loaded here).
+template <int SPL, bool GLOBAL>
+__device__ __forceinline__ void cnode_eval(const uint4 nraw, const uint4 e0, const waddr_t<GLOBAL> pairs,
                                            const waddr_t<GLOBAL> vb) {
   constexpr int SH = 7 + (SPL == 4 ? 2 : (SPL == 2 ? 1 : 0));
   const float bias = __uint_as_float(nraw.x), resp = __uint_as_float(nraw.y);
@@ -311,6 +322,7 @@ __device__ __forceinline__ void cnode_eval(const uint4 nraw, const waddr_t<GLOBA
   const int np = int(nraw.z >> CN_PAIR_BITS);
   const waddr_t<GLOBAL> pp = pairs + 16u * (nraw.z & ((1u << CN_PAIR_BITS) - 1u));
   const int agg = int(meta >> (CN_ROW_BITS + 3)) & 3;
+  constexpr bool PF = kCnPrefetch<SPL, GLOBAL>;  // e0: the first pair, when np > 0
   float a[SPL];
   if (agg == NEAT_AGG_SUM || agg == NEAT_AGG_MEAN) {
     float a0[SPL], a1[SPL];
@@ -318,7 +330,7 @@ __device__ __forceinline__ void cnode_eval(const uint4 nraw, const waddr_t<GLOBA
     for (int j = 0; j < SPL; ++j) a0[j] = a1[j] = 0.0f;
 #pragma unroll 2
     for (int k = 0; k < np; ++k) {
-      const uint4 e = w_ld16<GLOBAL>(pp + 16u * uint32_t(k));
+      const uint4 e = PF && k == 0 ? e0 : w_ld16<GLOBAL>(pp + 16u * uint32_t(k));
       float x0[SPL], x1[SPL];
       w_ldv<SPL, GLOBAL>(vb + (e.x << SH), x0);
       w_ldv<SPL, GLOBAL>(vb + (e.z << SH), x1);
@@ -336,7 +348,7 @@ __device__ __forceinline__ void cnode_eval(const uint4 nraw, const waddr_t<GLOBA
 #pragma unroll
     for (int j = 0; j < SPL; ++j) a[j] = 0.0f;
   } else if (agg == NEAT_AGG_MAX) {
-    const uint4 e = w_ld16<GLOBAL>(pp);
+    const uint4 e = PF ? e0 : w_ld16<GLOBAL>(pp);
     float x0[SPL], x1[SPL];
     w_ldv<SPL, GLOBAL>(vb + (e.x << SH), x0);
     w_ldv<SPL, GLOBAL>(vb + (e.z << SH), x1);
@@ -357,7 +369,7 @@ __device__ __forceinline__ void cnode_eval(const uint4 nraw, const waddr_t<GLOBA
 #pragma unroll
     for (int j = 0; j < SPL; ++j) a[j] = 1.0f;
     for (int k = 0; k < np; ++k) {
-      const uint4 f = w_ld16<GLOBAL>(pp + 16u * uint32_t(k));
+      const uint4 f = PF && k == 0 ? e0 : w_ld16<GLOBAL>(pp + 16u * uint32_t(k));
       float x0[SPL], x1[SPL];
       w_ldv<SPL, GLOBAL>(vb + (f.x << SH), x0);
       w_ldv<SPL, GLOBAL>(vb + (f.z << SH), x1);
@@ -374,6 +386,14 @@ __device__ __forceinline__ void cnode_eval(const uint4 nraw, const waddr_t<GLOBA
   w_stv<SPL, GLOBAL>(vb + ((meta & ((1u << CN_ROW_BITS) - 1u)) << SH), a);
 }
 
+template <int SPL, bool GLOBAL>
+__device__ __forceinline__ void cnode_eval(const uint4 nraw, const waddr_t<GLOBAL> pairs,
+                                           const waddr_t<GLOBAL> vb) {
+  const uint4 e0 = kCnPrefetch<SPL, GLOBAL> ? cnode_first_pair<SPL, GLOBAL>(nraw, pairs)
+                                               : make_uint4(0u, 0u, 0u, 0u);
+  cnode_eval<SPL, GLOBAL>(nraw, e0, pairs, vb);
+}
+
 // Walk of a compiled program (CNode records and edge pairs; see
 // neat_internal.cuh) for this lane's SPL samples.  vb = the warp's value array
 // + lane * SPL floats (bytes); value row r of it at vb + r * 128 * SPL
@@ -382,13 +402,38 @@ __device__ __forceinline__ void cnode_eval(const uint4 nraw, const waddr_t<GLOBA
 // 16-byte record; per two edges: one 16-byte pair; per edge and sample: one
 // value and one FMA.  Sum and mean keep even edges in a0 and odd edges in a1,
 // the rounding order of the position walk.
+//
+// With two or four samples a lane and the records in global memory (the
+// workspace-slot walk), the records run ahead of the evaluation:
+// node c + 1's first pair and node c + 2's record are loaded before node c
+// is evaluated (records only: values are read when their node runs), which
+// takes two dependent L2 loads off every node's chain (16,384 uneven
+// genomes, two samples a lane at 64 registers: 981 -> 916 us).  One sample a
+// lane keeps the plain loop (the extra records spill under its 42-register
+// bound), and so does a walk of records staged in shared memory (short
+// latency).
 template <int SPL, bool GLOBAL>
 __device__ __forceinline__ void cwalk(const CNode *__restrict__ nodes, int nn,
                                       const uint4 *__restrict__ pairs, char *vb) {
   const waddr_t<GLOBAL> na = waddr<GLOBAL>(nodes), pa = waddr<GLOBAL>(pairs),
                         va = waddr<GLOBAL>(vb);
-  for (int c = 0; c < nn; ++c)
-    cnode_eval<SPL, GLOBAL>(w_ld16<GLOBAL>(na + 16u * uint32_t(c)), pa, va);
+  if constexpr (!kCnPrefetch<SPL, GLOBAL>) {
+    for (int c = 0; c < nn; ++c)
+      cnode_eval<SPL, GLOBAL>(w_ld16<GLOBAL>(na + 16u * uint32_t(c)), pa, va);
+  } else {
+    if (nn <= 0) return;
+    uint4 r0 = w_ld16<GLOBAL>(na);
+    uint4 r1 = w_ld16<GLOBAL>(na + 16u * uint32_t(min(1, nn - 1)));
+    uint4 p0 = cnode_first_pair<SPL, GLOBAL>(r0, pa);
+    for (int c = 0; c < nn; ++c) {
+      const uint4 p1 = cnode_first_pair<SPL, GLOBAL>(r1, pa);
+      const uint4 r2 = w_ld16<GLOBAL>(na + 16u * uint32_t(min(c + 2, nn - 1)));
+      cnode_eval<SPL, GLOBAL>(r0, p0, pa, va);
+      r0 = r1;
+      r1 = r2;
+      p0 = p1;
+    }
+  }
 }
 
 // Item = (genome in queue order, tile of 32 * SPL samples); lane l evaluates
@@ -406,13 +451,14 @@ __device__ __forceinline__ void cwalk(const CNode *__restrict__ nodes, int nn,
 // CTA's first warp.  One warp walking such a genome alone would finish long
 // after the rest of the grid.  The remaining items are claimed per warp.
 //
-// One sample a lane fits 42 registers (three 512-thread CTAs an SM); two or
-// four a lane take up to 64 (two CTAs), which cuts their spills to a few
-// bytes: on the uneven population (16,384 genomes, S = 64) 1,050 -> 982 us
-// with two a lane, while one a lane at 64 registers loses more warps than it
-// gains (1,065 -> 1,250).
+// Registers: one sample a lane fits 42 (three 512-thread CTAs an SM); two or
+// four a lane take up to 80 (six 4-warp CTAs), with the records loaded ahead
+// (cwalk) without spilling.  On the uneven population (16,384 genomes, S =
+// 64, 4-warp CTAs, us per launch): two a lane 1,050 at a 42-register bound,
+// 982 at 64, 916 at 64 with the records ahead, 897 at 72, 886 at 80; one a
+// lane at 64 registers loses more warps than it gains (1,065 -> 1,250).
 template <int SPL, bool COMP>
-__global__ void __launch_bounds__(512, SPL == 1 ? 3 : 2)
+__global__ void __launch_bounds__(512, SPL == 1 ? 3 : 1) __maxnreg__(SPL == 1 ? 255 : 80)
     k_forward_sp(Ws w, const float *__restrict__ inputs, int64_t stride, int S,
                              float *__restrict__ out, float *__restrict__ saved, int tiles,
                              int vcap, int coop) {
@@ -475,10 +521,24 @@ __global__ void __launch_bounds__(512, SPL == 1 ? 3 : 2)
         __syncthreads();
         char *vb = reinterpret_cast<char *>(vc + lane * SPL);
         for (int k = 0; k < h.clayers; ++k) {
-          const int c1 = cl[k + 1];
-          for (int c = cl[k] + wid; c < c1; c += nw)
-            cnode_eval<SPL, true>(__ldg(reinterpret_cast<const uint4 *>(cn + c)),
-                                  waddr<true>(cp), waddr<true>(vb));
+          // (each warp's next node record and first pair loaded ahead, as in
+          // cwalk, with two or more samples a lane)
+          const int c0 = cl[k] + wid, c1 = cl[k + 1];
+          if constexpr (!kCnPrefetch<SPL, true>) {
+            for (int c = c0; c < c1; c += nw)
+              cnode_eval<SPL, true>(__ldg(reinterpret_cast<const uint4 *>(cn + c)),
+                                    waddr<true>(cp), waddr<true>(vb));
+          } else if (c0 < c1) {
+            uint4 r0 = __ldg(reinterpret_cast<const uint4 *>(cn + c0));
+            uint4 p0 = cnode_first_pair<SPL, true>(r0, waddr<true>(cp));
+            for (int c = c0; c < c1; c += nw) {
+              const uint4 r1 = __ldg(reinterpret_cast<const uint4 *>(cn + min(c + nw, c1 - 1)));
+              const uint4 p1 = cnode_first_pair<SPL, true>(r1, waddr<true>(cp));
+              cnode_eval<SPL, true>(r0, p0, waddr<true>(cp), waddr<true>(vb));
+              r0 = r1;
+              p0 = p1;
+            }
+          }
           __syncthreads();
         }
         const int32_t *orow = w.cout + size_t(g) * O;
@@ -669,16 +729,21 @@ __global__ void __launch_bounds__(256, 4)
     const NodeRec *nr = w.knode + h.node_off;
     const EdgeRec *er = w.kedge + h.edge_off;
     for (int t = 0; t < T; ++t) {
+      // each node's record loaded one node ahead (10,000 cyclic genomes, S =
+      // 64, T = 8: 2.36 -> 2.12 ms)
+      NodeRec n = ld_node(nr);
       for (int p = 0; p < V; ++p) {
-        const NodeRec n = ld_node(nr + p);
-        if (n.meta & META_INPUT) continue;
-        float ag[SPL];
-        node_agg<SPL>(n, er, a, ag);
+        const NodeRec nx = ld_node(nr + min(p + 1, V - 1));
+        if (!(n.meta & META_INPUT)) {
+          float ag[SPL];
+          node_agg<SPL>(n, er, a, ag);
 #pragma unroll
-        for (int j = 0; j < SPL; ++j) ag[j] = fmaf(n.resp, ag[j], n.bias);
-        act_apply_n<SPL>(meta_act(n.meta), ag);
+          for (int j = 0; j < SPL; ++j) ag[j] = fmaf(n.resp, ag[j], n.bias);
+          act_apply_n<SPL>(meta_act(n.meta), ag);
 #pragma unroll
-        for (int j = 0; j < SPL; ++j) b[(p * SPL + j) * 32] = ag[j];
+          for (int j = 0; j < SPL; ++j) b[(p * SPL + j) * 32] = ag[j];
+        }
+        n = nx;
       }
       float *tmp = a;
       a = b;
