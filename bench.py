@@ -591,16 +591,17 @@ def bench_ours(args, rank, world, local, pg):
         plan.set_tuning(**given, **({"prune_dead": 1} if args.prune else {}))
         tuning = {"mode": "given", "chosen": given}
 
-    def autotune_on(x_dev):
+    def autotune_on(x_dev, saved=False):
         """Run the autotuner on this population and one step's inputs (no
-        cache: every run measures), keeping the prune setting."""
+        cache: every run measures), keeping the prune setting; `saved`: on
+        the forward that writes the aggregates (the one a training step runs)."""
         if args.tune != "auto" or args.tuning is not None:
             return
         from paper_2504_08339_b300.autotune import autotune
         d_n = torch.from_numpy(nodes).to(dev)
         d_c = torch.from_numpy(conns).to(dev)
         base = {"prune_dead": 1} if args.prune else {}
-        r = autotune(plan, d_n, d_c, x_dev, use_cache=False, base=base)
+        r = autotune(plan, d_n, d_c, x_dev, use_cache=False, base=base, saved=saved)
         tuning["chosen"] = r["tuning"]
         tuning["trials_us"] = {json.dumps(t["tuning"], sort_keys=True): round(1e3 * t["ms"], 2)
                                for t in r["trials"]}
@@ -654,7 +655,7 @@ def bench_ours(args, rank, world, local, pg):
         saved = None if cfg.get("recompute") else torch.empty((P, spec.N, S), device=dev)
         out = torch.empty((P, S, spec.O), device=dev)
         go = torch.empty((P, S, spec.O), device=dev)
-        autotune_on(d_x)
+        autotune_on(d_x, saved=saved is not None)
         tr = plan.transform(d_nodes, d_conns)
         # ev[0]: the backward (the dominant kernel, the roofline's); ev_f: the forward
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))]

@@ -46,31 +46,34 @@ def candidates(plan: Plan, S: int):
     return out
 
 
-def _time_forward(plan: Plan, inputs, out, reps: int) -> float:
+def _time_forward(plan: Plan, inputs, out, reps: int, saved=None) -> float:
     for _ in range(3):
-        plan.forward(inputs, out=out)
+        plan.forward(inputs, out=out, saved=saved)
     torch.cuda.synchronize()
     a = torch.cuda.Event(enable_timing=True)
     b = torch.cuda.Event(enable_timing=True)
     a.record()
     for _ in range(reps):
-        plan.forward(inputs, out=out)
+        plan.forward(inputs, out=out, saved=saved)
     b.record()
     torch.cuda.synchronize()
     return a.elapsed_time(b) / reps
 
 
 def autotune(plan: Plan, nodes, conns, inputs, reps: int = 20, use_cache: bool = True,
-             verbose: bool = False, base: dict | None = None) -> dict:
+             verbose: bool = False, base: dict | None = None, saved: bool = False) -> dict:
     """Pick and apply the fastest tuning for this population and input shape.
-    `base` holds knobs every candidate keeps (e.g. prune_dead=1).
+    `base` holds knobs every candidate keeps (e.g. prune_dead=1); `saved`
+    times the forward that also writes the aggregates a backward reads (the
+    position walk) instead of the outputs-only forward (the compiled walk).
     Returns {"tuning": {...}, "ms": best forward time, "trials": [...]}."""
     base = dict(base or {})
     S = inputs.shape[1]
     en = (~torch.isnan(conns[..., 0])) & (conns[..., 3] != 0) & ~torch.isnan(conns[..., 3])
     n_edges = float(en.sum(dim=1).float().mean())
     n_nodes = float((~torch.isnan(nodes[..., 0])).sum(dim=1).float().mean())
-    sig = _signature(plan, S, n_edges, n_nodes) + "|" + json.dumps(base, sort_keys=True)
+    sig = (_signature(plan, S, n_edges, n_nodes) + "|" + json.dumps(base, sort_keys=True) +
+           ("|saved" if saved else ""))
     path = _cache_path()
     cache = {}
     if use_cache and os.path.exists(path):
@@ -85,12 +88,14 @@ def autotune(plan: Plan, nodes, conns, inputs, reps: int = 20, use_cache: bool =
         plan.transform(nodes, conns)
         return best
     out = torch.empty((plan.P, S, plan.O), dtype=torch.float32, device=inputs.device)
+    sv = (torch.empty((plan.P, plan.N, S), dtype=torch.float32, device=inputs.device)
+          if saved else None)
     trials = []
     for cand in candidates(plan, S):
         cand = {**base, **cand}
         plan.set_tuning(**cand)
         plan.transform(nodes, conns)
-        ms = _time_forward(plan, inputs, out, reps)
+        ms = _time_forward(plan, inputs, out, reps, sv)
         trials.append({"tuning": cand, "ms": ms})
         if verbose:
             print(f"autotune {cand} -> {ms * 1e3:.2f} us")

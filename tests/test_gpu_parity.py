@@ -800,3 +800,27 @@ def test_tuning_knobs_and_autotuner(tmp_path, monkeypatch):
     # the cache answers the second call
     res2 = autotune(plan, dn, dc, dx, reps=3)
     assert res2["tuning"] == res["tuning"]
+
+
+def test_autotuner_on_the_saved_aggregates_forward(tmp_path, monkeypatch):
+    """With saved=True the autotuner times the forward that writes the
+    aggregates (S = 64: one and two samples a lane among the candidates);
+    its choice gives the oracle's outputs and aggregates, and the cache keeps
+    the two kinds of timing apart."""
+    from paper_2504_08339_b300.autotune import autotune
+    P, S = 96, 64
+    nodes, conns, spec = population_for("differentiation", seed=3, P=P)
+    plan = _plan(spec, P)
+    x = np.random.default_rng(2).standard_normal((P, S, spec.I)).astype(np.float32)
+    monkeypatch.setenv("NEAT_TUNE_CACHE", str(tmp_path / "tune.json"))
+    dn, dc, dx = _dev(nodes), _dev(conns), _dev(x)
+    res = autotune(plan, dn, dc, dx, reps=2, saved=True)
+    assert {t["tuning"].get("samples_per_lane") for t in res["trials"]} >= {1, 2}
+    saved = torch.empty((P, spec.N, S), device="cuda")
+    out = plan.forward(dx, saved=saved).cpu().numpy()
+    ref, bnd = oracle.forward(nodes, conns, x, spec.I, spec.O, with_bound=True)
+    compare_outputs(out, ref, bnd)
+    autotune(plan, dn, dc, dx, reps=2)  # outputs only: its own cache entry
+    import json
+    with open(tmp_path / "tune.json") as f:
+        assert len(json.load(f)) == 2
