@@ -81,8 +81,13 @@ class Plan:
         return {k: getattr(t, k) for k, _ in t._fields_}
 
     def set_tuning(self, **kw):
+        """Set the tuning knobs (neat_tuning); knobs not named are 0, the
+        library's default.  An unknown knob name is an error."""
         t = _lib.neat_tuning()
+        names = {k for k, _ in t._fields_}
         for k, v in kw.items():
+            if k not in names:
+                raise _lib.NeatError(f"set_tuning: unknown knob {k!r} (knobs: {sorted(names)})")
             setattr(t, k, int(v))
         _lib.check(self._lib.neat_plan_set_tuning(self._h, ctypes.byref(t)), "set_tuning")
 

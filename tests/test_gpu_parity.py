@@ -785,6 +785,8 @@ def test_tuning_knobs_and_autotuner(tmp_path, monkeypatch):
         plan.set_tuning(samples_per_lane=3)
     with pytest.raises(NeatError):
         plan.set_tuning(wait_polls=-2)
+    with pytest.raises(NeatError):
+        plan.set_tuning(samples_per_lanes=2)  # a misspelt knob is not ignored
     x = np.random.default_rng(0).standard_normal((600, 1, spec.I)).astype(np.float32)
     ref, bnd = oracle.forward(nodes, conns, x, spec.I, spec.O, with_bound=True)
     monkeypatch.setenv("NEAT_TUNE_CACHE", str(tmp_path / "tune.json"))
