@@ -57,7 +57,7 @@ TRAFFIC = {
     ("locomotion", "k_forward_lvl"): (32797440, 10000, dict([
         ("paper_2504_08339_b300/csrc/level.cu", "9c35aa382f0efee0"), _INTERNAL])),
     ("uneven", "k_forward_sp"): (106514944, 2048, dict([
-        ("paper_2504_08339_b300/csrc/forward.cu", "8b7d48f7094536e0"),
+        ("paper_2504_08339_b300/csrc/forward.cu", "400cb012c35e8c09"),
         ("paper_2504_08339_b300/csrc/api.cu", "cc8693b9f802b05f"), _INTERNAL])),
     ("differentiation", "k_backward"): (359663104, 512, dict([
         ("paper_2504_08339_b300/csrc/backward.cu", "ae1c59197d133899"), _INTERNAL])),

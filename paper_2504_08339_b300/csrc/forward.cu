@@ -730,7 +730,7 @@ __global__ void __launch_bounds__(256, 4)
     const EdgeRec *er = w.kedge + h.edge_off;
     for (int t = 0; t < T; ++t) {
       // each node's record loaded one node ahead (10,000 cyclic genomes, S =
-      // 64, T = 8: 2.36 -> 2.12 ms)
+      // 64, T = 8: 2.36 -> 2.12 ms); V >= I + O >= 2 for a valid genome
       NodeRec n = ld_node(nr);
       for (int p = 0; p < V; ++p) {
         const NodeRec nx = ld_node(nr + min(p + 1, V - 1));
