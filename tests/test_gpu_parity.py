@@ -665,6 +665,23 @@ def test_maximum_sizes():
     out = plan.forward(_dev(x)).cpu().numpy()
     r, bnd = oracle.forward(nodes, conns, x, 9, 3, with_bound=True)
     compare_outputs(out, r, bnd)
+    # one sample per genome (the rollout step's call) and the saved aggregates
+    x1 = np.ascontiguousarray(x[:, :1])
+    r1, b1 = oracle.forward(nodes, conns, x1, 9, 3, with_bound=True)
+    compare_outputs(plan.forward(_dev(x1)).cpu().numpy(), r1, b1)
+    saved = torch.empty((6, spec.N, 40), device="cuda")
+    compare_outputs(plan.forward(_dev(x), saved=saved).cpu().numpy(), r, bnd)
+    plan.check()
+    # the backward at the maxima (per-warp arrays in workspace slots), both modes
+    go = np.random.default_rng(1).standard_normal((6, 40, 3)).astype(np.float32)
+    rw, rb, rr, ri = oracle.backward(nodes, conns, x, 9, 3, go)
+    for sv in (saved, None):
+        gw, gb, gr, gi = plan.backward(_dev(x), _dev(go), saved=sv)
+        plan.check()
+        compare_grads(gw.cpu().numpy(), rw, "grad_weight")
+        compare_grads(gb.cpu().numpy(), rb, "grad_bias")
+        compare_grads(gr.cpu().numpy(), rr, "grad_response")
+        compare_grads(gi.cpu().numpy(), ri, "grad_inputs")
 
 
 def test_abi_argument_errors():
