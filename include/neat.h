@@ -190,6 +190,28 @@ neat_status neat_plan_device_errors(neat_plan *plan, uint32_t *errors, int clear
  * NEAT_DEV_NO_SCRATCH was, NEAT_OK otherwise.  Not during a stream capture. */
 neat_status neat_plan_check(neat_plan *plan, cudaStream_t stream);
 
+/* Structure check of the plan's transformed population (no counterpart in
+ * the paper; the range checks a debugging build would make, run as kernels
+ * over the structures instead of inside the evaluation kernels).  Checks
+ * every index the forward, backward and HyperNEAT kernels read from the
+ * structures the last transform wrote -- queue entries, genome headers,
+ * packed position programs (records, edge ranges, sources earlier than their
+ * node in a feed-forward transform), input / output positions, compiled
+ * programs (pair ranges, value rows, layer starts, output rows) and level
+ * batch programs (arena place, staged head size, header offsets, genome
+ * table, round table, task and edge slots) -- against the arrays they
+ * address, reading only inside the workspace whatever its contents.
+ *   bits   device u32, caller-owned, 4-byte aligned: set to the OR of
+ *          NEAT_BAD_* bits (0: every structure in range), asynchronously on
+ *          `stream`
+ * NEAT_ERR_STATE before any transform, NEAT_ERR_ARG for a NULL or misaligned
+ * `bits`. */
+#define NEAT_BAD_QUEUE 1u    /* a queue entry is not a genome id */
+#define NEAT_BAD_PACKED 2u   /* a header or packed position program out of range */
+#define NEAT_BAD_COMPILED 4u /* a compiled program out of range */
+#define NEAT_BAD_BATCHES 8u  /* a level batch program out of range */
+neat_status neat_plan_validate(const neat_plan *plan, uint32_t *bits, cudaStream_t stream);
+
 /* Transformation stage (Sec. 3.3) for all P genomes.
  *   nodes   [P, N, 5] f32, conns [P, C, 4] f32 (read only)
  *   order   [P, N] i32 out: node ROWS in topological order -- Kahn by frontier,

@@ -17,6 +17,8 @@ LIB_PATH = os.path.join(_HERE, "libneat.so")
 (NEAT_OK, NEAT_ERR_ARG, NEAT_ERR_CUDA, NEAT_ERR_WORKSPACE, NEAT_ERR_UNSUPPORTED, NEAT_ERR_STATE,
  NEAT_ERR_TIMEOUT) = (0, -1, -2, -3, -4, -5, -6)
 DEV_TIMEOUT, DEV_NO_SCRATCH = 1, 2
+# neat_plan_validate bits (NEAT_BAD_*)
+BAD_QUEUE, BAD_PACKED, BAD_COMPILED, BAD_BATCHES = 1, 2, 4, 8
 G_CYCLE, G_DANGLING_KEY, G_DUP_KEY, G_DUP_EDGE, G_EDGE_INTO_INPUT, G_BAD_ATTR, G_IO_ROW_INVALID = (
     1, 2, 4, 8, 16, 32, 64)
 
@@ -24,7 +26,7 @@ G_CYCLE, G_DANGLING_KEY, G_DUP_KEY, G_DUP_EDGE, G_EDGE_INTO_INPUT, G_BAD_ATTR, G
 SYMBOLS = ("neat_version", "neat_status_string", "neat_last_cuda_error",
            "neat_workspace_bytes", "neat_plan_create",
            "neat_plan_destroy", "neat_plan_set_tuning", "neat_plan_get_tuning",
-           "neat_plan_device_errors", "neat_plan_check", "neat_transform",
+           "neat_plan_device_errors", "neat_plan_check", "neat_plan_validate", "neat_transform",
            "neat_forward", "neat_forward_plain", "neat_backward", "neat_sum_genomes",
            "neat_hyperneat_query",
            "neat_forward_noalloc", "neat_probe_smem_read", "neat_transform_recurrent",
@@ -72,6 +74,7 @@ def load(path: str = LIB_PATH):
             "neat_plan_get_tuning": (i32, [vp, ctypes.POINTER(neat_tuning)]),
             "neat_plan_device_errors": (i32, [vp, vp, i32, vp]),
             "neat_plan_check": (i32, [vp, vp]),
+            "neat_plan_validate": (i32, [vp, vp, vp]),
             "neat_transform": (i32, [vp, vp, vp, vp, vp, vp, vp, vp]),
             "neat_forward": (i32, [vp, vp, i64, i32, vp, vp, vp]),
             "neat_forward_plain": (i32, [vp, vp, i64, i32, vp, vp]),

@@ -105,6 +105,15 @@ class Plan:
         (their outputs are NaN) since the last check or transform."""
         _lib.check(self._lib.neat_plan_check(self._h, _stream(stream)), "neat_plan_check")
 
+    def validate(self, stream=None) -> int:
+        """neat_plan_validate: the NEAT_BAD_* bits (_lib.BAD_*) of the
+        structures the last transform wrote, 0 when every index they hold is
+        in range (synchronises with the stream)."""
+        bits = torch.zeros((1,), dtype=torch.int32, device=self.device)
+        _lib.check(self._lib.neat_plan_validate(self._h, _ptr(bits), _stream(stream)),
+                   "neat_plan_validate")
+        return int(bits.item()) & 0xffffffff
+
     # -- transformation stage -----------------------------------------------------
     def transform(self, nodes, conns, out: Transformed | None = None, stream=None) -> Transformed:
         P, N, C = self.P, self.N, self.C

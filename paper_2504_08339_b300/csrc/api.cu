@@ -270,6 +270,13 @@ neat_status neat_plan_check(neat_plan *plan, cudaStream_t stream) {
   return NEAT_OK;
 }
 
+neat_status neat_plan_validate(const neat_plan *plan, uint32_t *bits, cudaStream_t stream) {
+  if (plan == nullptr || bits == nullptr || !aligned(bits, 4)) return NEAT_ERR_ARG;
+  if (plan->transformed == 0) return NEAT_ERR_STATE;
+  return cuda_status(neat::launch_validate(plan->w, plan->L, plan->transformed == 1 ? 1 : 0, bits,
+                                           plan->sm_count, stream));
+}
+
 neat_status neat_transform(neat_plan *plan, const float *nodes, const float *conns, int32_t *order,
                            int32_t *layer, int32_t *n_layers, uint32_t *gstatus,
                            cudaStream_t stream) {

@@ -483,6 +483,11 @@ inline int sp_scratch_slots(const Ws &w, int spl) {  // slots of N + 2 rows
 }
 cudaError_t launch_forward_plain(const Ws &w, const float *inputs, int64_t stride, int S,
                                  float *outputs, cudaStream_t st);
+// structure check (neat_plan_validate): NEAT_BAD_* bits OR-ed into *bits
+// (zeroed first); feedforward = 1 after neat_transform, 0 after the
+// recurrent transform (no compiled programs or batches)
+cudaError_t launch_validate(const Ws &w, const Layout &L, int feedforward, uint32_t *bits,
+                            int sm_count, cudaStream_t st);
 // recurrent calculation: T synchronous iterations, spl (1 or 2) samples per
 // lane, `warps` per CTA, `grid` CTAs (grid * warps <= sp_scratch_slots(w,
 // 2 * spl): two value buffers per warp)
