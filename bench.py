@@ -57,7 +57,7 @@ TRAFFIC = {
     ("locomotion", "k_forward_lvl"): (32806656, 10000, dict([
         ("paper_2504_08339_b300/csrc/level.cu", "9c35aa382f0efee0"), _INTERNAL])),
     ("uneven", "k_forward_sp"): (106514944, 2048, dict([
-        ("paper_2504_08339_b300/csrc/forward.cu", "400cb012c35e8c09"),
+        ("paper_2504_08339_b300/csrc/forward.cu", "197eb47a40b84b5d"),
         ("paper_2504_08339_b300/csrc/api.cu", "b0d1b94ec2fb1a85"), _INTERNAL])),
     ("differentiation", "k_backward"): (359663104, 512, dict([
         ("paper_2504_08339_b300/csrc/backward.cu", "ae1c59197d133899"), _INTERNAL])),

@@ -313,7 +313,7 @@ __device__ __forceinline__ uint4 cnode_first_pair(const uint4 nraw, const waddr_
 // One compiled node (its 16-byte record nraw) for this lane's SPL samples;
 // e0 its first edge pair when the walk loads records ahead (kCnPrefetch),
 // else unused (the pair is loaded here).
-template <int SPL, bool GLOBAL>
+template <int SPL, bool GLOBAL, bool PF = kCnPrefetch<SPL, GLOBAL>>
 __device__ __forceinline__ void cnode_eval(const uint4 nraw, const uint4 e0, const waddr_t<GLOBAL> pairs,
                                            const waddr_t<GLOBAL> vb) {
   constexpr int SH = 7 + (SPL == 4 ? 2 : (SPL == 2 ? 1 : 0));
@@ -322,7 +322,7 @@ __device__ __forceinline__ void cnode_eval(const uint4 nraw, const uint4 e0, con
   const int np = int(nraw.z >> CN_PAIR_BITS);
   const waddr_t<GLOBAL> pp = pairs + 16u * (nraw.z & ((1u << CN_PAIR_BITS) - 1u));
   const int agg = int(meta >> (CN_ROW_BITS + 3)) & 3;
-  constexpr bool PF = kCnPrefetch<SPL, GLOBAL>;  // e0: the first pair, when np > 0
+  // PF: e0 holds the first pair (when np > 0), loaded ahead by the walk
   float a[SPL];
   if (agg == NEAT_AGG_SUM || agg == NEAT_AGG_MEAN) {
     float a0[SPL], a1[SPL];
@@ -386,12 +386,11 @@ __device__ __forceinline__ void cnode_eval(const uint4 nraw, const uint4 e0, con
   w_stv<SPL, GLOBAL>(vb + ((meta & ((1u << CN_ROW_BITS) - 1u)) << SH), a);
 }
 
-template <int SPL, bool GLOBAL>
+template <int SPL, bool GLOBAL, bool PF = kCnPrefetch<SPL, GLOBAL>>
 __device__ __forceinline__ void cnode_eval(const uint4 nraw, const waddr_t<GLOBAL> pairs,
                                            const waddr_t<GLOBAL> vb) {
-  const uint4 e0 = kCnPrefetch<SPL, GLOBAL> ? cnode_first_pair<SPL, GLOBAL>(nraw, pairs)
-                                               : make_uint4(0u, 0u, 0u, 0u);
-  cnode_eval<SPL, GLOBAL>(nraw, e0, pairs, vb);
+  const uint4 e0 = PF ? cnode_first_pair<SPL, GLOBAL>(nraw, pairs) : make_uint4(0u, 0u, 0u, 0u);
+  cnode_eval<SPL, GLOBAL, PF>(nraw, e0, pairs, vb);
 }
 
 // Walk of a compiled program (CNode records and edge pairs; see
@@ -412,14 +411,14 @@ __device__ __forceinline__ void cnode_eval(const uint4 nraw, const waddr_t<GLOBA
 // lane keeps the plain loop (the extra records spill under its 42-register
 // bound), and so does a walk of records staged in shared memory (short
 // latency).
-template <int SPL, bool GLOBAL>
+template <int SPL, bool GLOBAL, bool PF = kCnPrefetch<SPL, GLOBAL>>
 __device__ __forceinline__ void cwalk(const CNode *__restrict__ nodes, int nn,
                                       const uint4 *__restrict__ pairs, char *vb) {
   const waddr_t<GLOBAL> na = waddr<GLOBAL>(nodes), pa = waddr<GLOBAL>(pairs),
                         va = waddr<GLOBAL>(vb);
-  if constexpr (!kCnPrefetch<SPL, GLOBAL>) {
+  if constexpr (!PF) {
     for (int c = 0; c < nn; ++c)
-      cnode_eval<SPL, GLOBAL>(w_ld16<GLOBAL>(na + 16u * uint32_t(c)), pa, va);
+      cnode_eval<SPL, GLOBAL, false>(w_ld16<GLOBAL>(na + 16u * uint32_t(c)), pa, va);
   } else {
     if (nn <= 0) return;
     uint4 r0 = w_ld16<GLOBAL>(na);
@@ -428,7 +427,7 @@ __device__ __forceinline__ void cwalk(const CNode *__restrict__ nodes, int nn,
     for (int c = 0; c < nn; ++c) {
       const uint4 p1 = cnode_first_pair<SPL, GLOBAL>(r1, pa);
       const uint4 r2 = w_ld16<GLOBAL>(na + 16u * uint32_t(min(c + 2, nn - 1)));
-      cnode_eval<SPL, GLOBAL>(r0, p0, pa, va);
+      cnode_eval<SPL, GLOBAL, true>(r0, p0, pa, va);
       r0 = r1;
       r1 = r2;
       p0 = p1;
@@ -901,14 +900,14 @@ struct HnTile {
   float *wg;                   // the genome's weights
 };
 
-// Tiles tile0, tile0 + stride, ... < tile1 of one warp: coordinates into the
-// input rows of the warp's value array v, walk(), thresholded outputs.  Value
-// (row, query k of this lane) sits at v[(row * 32 + lane) * SPL + k] when
-// LANE_MAJOR (the staged walk: one vector access per row), else at
-// v[(row * SPL + k) * 32 + lane] (the sample-parallel walk).
-template <int SPL, bool LANE_MAJOR, class Walk>
-__device__ __forceinline__ void hn_tiles(const HnTile &t, float *v, int tile0, int tile1,
-                                         int stride, Walk walk) {
+// The tiles next() hands one warp (warp-uniform, -1 when done): coordinates
+// into the input rows of the warp's value array v, walk(), thresholded
+// outputs.  Value (row, query k of this lane) sits at
+// v[(row * 32 + lane) * SPL + k] when LANE_MAJOR (the compiled walks: one
+// vector access per row), else at v[(row * SPL + k) * 32 + lane] (the
+// sample-parallel position walk).
+template <int SPL, bool LANE_MAJOR, class Next, class Walk>
+__device__ __forceinline__ void hn_tiles(const HnTile &t, float *v, Next next, Walk walk) {
   constexpr int RS = 32 * SPL;
   const int lane = threadIdx.x & 31;
   auto at = [&](int row, int k) -> float & {
@@ -916,7 +915,7 @@ __device__ __forceinline__ void hn_tiles(const HnTile &t, float *v, int tile0, i
   };
 #pragma unroll
   for (int k = 0; k < SPL; ++k) at(t.pb, k) = 1.0f;
-  for (int tile = tile0; tile < tile1; tile += stride) {
+  for (int tile = next(); tile >= 0; tile = next()) {
     const int q0 = tile * RS;
     const int sc0 = q0 / t.G2, tc0 = q0 - sc0 * t.G2 + lane;
 #pragma unroll
@@ -944,6 +943,30 @@ __device__ __forceinline__ void hn_tiles(const HnTile &t, float *v, int tile0, i
   }
 }
 
+// The tiles of one item for a warp whose value array is its workspace slot
+// (tiles claimed from the CTA's counter *s_tile below t1; the compiled
+// program read from global memory).  Out of line: its registers do not add
+// to those of the staged walk it runs beside.
+template <int SPL>
+__device__ __noinline__ void hn_slot_tiles(const HnTile t, float *v, int *s_tile, int t1,
+                                           const CNode *gcn, int nlive, const uint4 *cp, int I) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int k = 0; k < SPL; ++k) {
+    v[(I * 32 + lane) * SPL + k] = 0.0f;
+    v[((I + 1) * 32 + lane) * SPL + k] = 1.0f;
+  }
+  char *vb = reinterpret_cast<char *>(v + lane * SPL);
+  auto claim = [&]() {
+    int x = 0;
+    if (lane == 0) x = atomicAdd(s_tile, 1);
+    x = __shfl_sync(0xffffffffu, x, 0);
+    return x < t1 ? x : -1;
+  };
+  // (the plain loop: the records loaded ahead would spill)
+  hn_tiles<SPL, true>(t, v, claim, [&]() { cwalk<SPL, true, false>(gcn, nlive, cp, vb); });
+}
+
 template <int SPL>
 __global__ void __launch_bounds__(512, 2) k_hyperneat(Ws w, int G, float thresh,
                                                    float *__restrict__ weights,
@@ -951,17 +974,18 @@ __global__ void __launch_bounds__(512, 2) k_hyperneat(Ws w, int G, float thresh,
                                                    int smem_bytes) {
   constexpr int RS = 32 * SPL;
   extern __shared__ __align__(16) unsigned char hsm[];
-  __shared__ int s_item;
+  __shared__ int s_item, s_tile;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int N = w.N, I = w.I;
   const int prog_bytes = hn_prog_bytes(N, w.C);
   uint4 *s_nodes = reinterpret_cast<uint4 *>(hsm);  // CNode records
   uint4 *s_pairs = reinterpret_cast<uint4 *>(hsm + size_t(N) * sizeof(CNode));
   float *s_vals = reinterpret_cast<float *>(hsm + prog_bytes);
-  // workspace slots of every warp of this CTA (the fallback walk), or none
+  // workspace slots of every warp of this CTA (N + 2 rows each), or none
+  const size_t SLOT = size_t(N + 2) * RS;
   const bool slots_ok = w.sp_scratch != nullptr &&
-                        size_t(blockIdx.x + 1) * nw * N * RS <= w.sp_scratch_floats;
-  float *vg = slots_ok ? w.sp_scratch + (size_t(blockIdx.x) * nw + wid) * N * RS : nullptr;
+                        size_t(blockIdx.x + 1) * nw * SLOT <= w.sp_scratch_floats;
+  float *vg = slots_ok ? w.sp_scratch + (size_t(blockIdx.x) * nw + wid) * SLOT : nullptr;
   const int G2 = G * G, G4 = G2 * G2;
   const int tiles = (G4 + RS - 1) / RS;
   const int total = w.P * chunks_per_genome;
@@ -992,14 +1016,28 @@ __global__ void __launch_bounds__(512, 2) k_hyperneat(Ws w, int G, float thresh,
     }
     if (vwarps >= 1) {
       // the compiled program to shared memory
-      const uint4 *cn = reinterpret_cast<const uint4 *>(w.cnode + size_t(g) * N);
+      const CNode *gcn = w.cnode + size_t(g) * N;
+      const uint4 *cn = reinterpret_cast<const uint4 *>(gcn);
       const uint4 *cp = w.cpair + size_t(g) * cpair_cap(N, w.C);
       for (int i = threadIdx.x; i < h.nlive; i += blockDim.x) s_nodes[i] = __ldg(cn + i);
       for (int i = threadIdx.x; i < h.cpairs; i += blockDim.x) s_pairs[i] = __ldg(cp + i);
+      if (threadIdx.x == 0) s_tile = t0;
       __syncthreads();
+      // tiles claimed one at a time: the warps with a value array in shared
+      // memory walk the staged program; the others (the CPPN's arrays fill the
+      // shared memory before every warp has one) walk the same compiled
+      // program from global memory with their arrays in their workspace slots
+      // (the same arithmetic: the same bits), instead of waiting for the next
+      // item
+      auto claim = [&]() {
+        int x = 0;
+        if (lane == 0) x = atomicAdd(&s_tile, 1);
+        x = __shfl_sync(0xffffffffu, x, 0);
+        return x < t1 ? x : -1;
+      };
+      // inputs in rows 0..4, constants 0 and 1 in rows I and I + 1
+      const HnTile t{G, G2, G4, step, inv_g, thresh, 0, 1, 2, 3, 4, w.cout[g], wg};
       if (wid < vwarps) {
-        // inputs in rows 0..4, constants 0 and 1 in rows I and I + 1
-        const HnTile t{G, G2, G4, step, inv_g, thresh, 0, 1, 2, 3, 4, w.cout[g], wg};
         float *v = s_vals + size_t(wid) * h.crows * RS;  // shared memory
 #pragma unroll
         for (int k = 0; k < SPL; ++k) {
@@ -1008,15 +1046,21 @@ __global__ void __launch_bounds__(512, 2) k_hyperneat(Ws w, int G, float thresh,
         }
         char *vb = reinterpret_cast<char *>(v + lane * SPL);
         const CNode *sn = reinterpret_cast<const CNode *>(s_nodes);
-        hn_tiles<SPL, true>(t, v, t0 + wid, t1, vwarps,
-                            [&]() { cwalk<SPL, false>(sn, h.nlive, s_pairs, vb); });
+        hn_tiles<SPL, true>(t, v, claim, [&]() { cwalk<SPL, false>(sn, h.nlive, s_pairs, vb); });
+      } else if (vg != nullptr) {
+        hn_slot_tiles<SPL>(t, vg, &s_tile, t1, gcn, h.nlive, cp, I);
       }
     } else {
       const HnTile t{G, G2, G4, step, inv_g, thresh, io[0], io[1], io[2], io[3], io[4], io[5], wg};
       const NodeRec *nr = w.knode + h.node_off;
       const EdgeRec *er = w.kedge + h.edge_off;
       float *vl = vg + lane;
-      hn_tiles<SPL, false>(t, vg, t0 + wid, t1, nw, [&]() {
+      int cur = t0 + wid - nw;
+      auto next = [&]() {
+        cur += nw;
+        return cur < t1 ? cur : -1;
+      };
+      hn_tiles<SPL, false>(t, vg, next, [&]() {
         float *const scol[SPL] = {};
         walk_program<false, SPL>(nr, er, h.V, vl, scol, 0);
       });
