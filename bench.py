@@ -52,12 +52,12 @@ PEAKS_FALLBACK = {"hbm_gbs": 6400.0, "source": "fallback"}
 # and launch shape).  A capture on a smaller population is scaled by
 # population (the traffic grows with the genomes processed); the figure is
 # reported only while those sources are unchanged.
-_INTERNAL = ("paper_2504_08339_b300/csrc/neat_internal.cuh", "487c0beb96677286")
+_INTERNAL = ("paper_2504_08339_b300/csrc/neat_internal.cuh", "0d5d940c51250188")
 TRAFFIC = {
     ("locomotion", "k_forward_lvl"): (32806656, 10000, dict([
         ("paper_2504_08339_b300/csrc/level.cu", "9c35aa382f0efee0"), _INTERNAL])),
     ("uneven", "k_forward_sp"): (106514944, 2048, dict([
-        ("paper_2504_08339_b300/csrc/forward.cu", "197eb47a40b84b5d"),
+        ("paper_2504_08339_b300/csrc/forward.cu", "b4b5082dcc2f7747"),
         ("paper_2504_08339_b300/csrc/api.cu", "b0d1b94ec2fb1a85"), _INTERNAL])),
     ("differentiation", "k_backward"): (359663104, 512, dict([
         ("paper_2504_08339_b300/csrc/backward.cu", "ae1c59197d133899"), _INTERNAL])),

@@ -674,7 +674,7 @@ __global__ void __launch_bounds__(512, SPL == 1 ? 3 : 1) __maxnreg__(SPL == 1 ? 
 // j * 32 + l, j < SPL (every record load serves SPL samples).  The warp's
 // workspace slot holds two [N][SPL][32] value buffers, v^{t-1} (read) and
 // v^t (written), swapped after every iteration.
-// (launch bound: the workspace slots keep the grid near 24 warps per SM)
+// (launch bound: 64 registers, four 8-warp CTAs an SM)
 template <int SPL>
 __global__ void __launch_bounds__(256, 4)
     k_forward_rec(Ws w, const float *__restrict__ inputs, int64_t stride, int S, int T,
