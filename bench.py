@@ -57,8 +57,8 @@ TRAFFIC = {
     ("locomotion", "k_forward_lvl"): (32806656, 10000, dict([
         ("paper_2504_08339_b300/csrc/level.cu", "9c35aa382f0efee0"), _INTERNAL])),
     ("uneven", "k_forward_sp"): (106514944, 2048, dict([
-        ("paper_2504_08339_b300/csrc/forward.cu", "b4b5082dcc2f7747"),
-        ("paper_2504_08339_b300/csrc/api.cu", "b0d1b94ec2fb1a85"), _INTERNAL])),
+        ("paper_2504_08339_b300/csrc/forward.cu", "5829aa1bc16b8561"),
+        ("paper_2504_08339_b300/csrc/api.cu", "a5479abbfff12c07"), _INTERNAL])),
     ("differentiation", "k_backward"): (359663104, 512, dict([
         ("paper_2504_08339_b300/csrc/backward.cu", "ae1c59197d133899"), _INTERNAL])),
 }

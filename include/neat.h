@@ -132,7 +132,7 @@ neat_status neat_plan_destroy(neat_plan *plan);
  *                    queries one lane evaluates in the HyperNEAT query (1, 2, 4);
  *                    0 (default, reported as 0): two for S >= 64 in calls
  *                    without saved aggregates, else one;
- *                    the HyperNEAT query two; the recurrent forward one (it
+ *                    the HyperNEAT query four; the recurrent forward one (it
  *                    takes 1 or 2, larger values as 2)
  *   lvl_threads      threads of a level-synchronous (small-sample) CTA: 32..256,
  *                    a multiple of 32; each warp of it evaluates its own batches
